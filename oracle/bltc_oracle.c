@@ -1,0 +1,693 @@
+/*
+ * bltc_oracle.c -- plain FP64 CPU oracle of the barycentric Lagrange treecode (BLTC)
+ * of Vaughn, Wilson and Krasny, "A GPU-Accelerated Barycentric Lagrange Treecode".
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct reference that the
+ * CUDA library is checked against.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * CPU-baseline leg may load it.  It shares no code, header, table or helper with the
+ * library; both receive the same input arrays from the seeded generators and nothing else.
+ *
+ * Everything is IEEE FP64, compiled with -ffp-contract=off so that a*b+c is never fused.
+ * OpenMP is used only across independent units (targets of the direct sum, clusters of the
+ * upward pass, target batches of the treecode), as the paper's CPU code did (Sec. IV,
+ * "Single GPU vs. Single 6-Core CPU").  The order of every floating-point sum is fixed.
+ *
+ * Readings of the paper taken where it is silent (each is restated where it is used):
+ *   R1  a pair with r^2 == 0 exactly is skipped (targets equal sources, Eq. 1);
+ *   R2  cluster and batch boxes are the minimal axis-aligned boxes of their particles;
+ *       min/max order -0.0 before +0.0;
+ *   R3  centre c = 0.5*(lo+hi), half extent h = 0.5*(hi-lo), radius sqrt(hx*hx+hy*hy+hz*hz),
+ *       R = sqrt(dx*dx+dy*dy+dz*dz) between centres, all left to right;
+ *   R4  the geometric MAC test is (rB+rC)/R < theta (IEEE division); a NaN ratio fails it;
+ *   R5  Algorithm 1's branch order, a size-rejected cluster is summed directly whole;
+ *   R6  split rule: dimension d is split iff (hi_d-lo_d)*sqrt(2) >= max extent; a particle
+ *       goes low iff coord < 0.5*(lo_d+hi_d); octant bit0/1/2 = x/y/z high; children in
+ *       increasing octant order, empty ones dropped; stable partition; leaf iff count <=
+ *       max_leaf, or zero extent, or the split leaves one non-empty child; DFS pre-order ids;
+ *   R7  Chebyshev points s_k = lo + 0.5*(t_k+1)*(hi-lo), t_k = cos(pi*k/n), with s_0 = hi
+ *       and s_n = lo forced;
+ *   R8  exact hit in dimension l iff |y - s_k| < DBL_MIN, smallest such k wins.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "bltc_oracle.h"
+
+/* ------------------------------------------------------------------------------------ */
+/* Kernels G(x, y), Eq. 2, plus a polynomial test kernel.                                 */
+/* ------------------------------------------------------------------------------------ */
+
+/* Polynomial test kernel (not in the paper): G(x, y) = prod_l (1 + x_l*y_l/2)^n.  Its degree
+ * in every source coordinate y_l is n, so the tensor-product interpolant of Eq. 8 reproduces
+ * it exactly and the treecode must equal the direct sum up to rounding. */
+static double poly_kernel(int degree, double tx, double ty, double tz,
+                          double sx, double sy, double sz)
+{
+    double fx = 1.0 + 0.5 * tx * sx;
+    double fy = 1.0 + 0.5 * ty * sy;
+    double fz = 1.0 + 0.5 * tz * sz;
+    double g = 1.0;
+    for (int m = 0; m < degree; ++m) g = g * fx;
+    for (int m = 0; m < degree; ++m) g = g * fy;
+    for (int m = 0; m < degree; ++m) g = g * fz;
+    return g;
+}
+
+/* G(x_i, y_j) of Eq. 2.  Returns 0 (pair skipped, reading R1) when r^2 == 0, else 1. */
+static int kernel_G(int kernel, double kappa, int degree,
+                    double tx, double ty, double tz, double sx, double sy, double sz,
+                    double* g)
+{
+    double dx = tx - sx;
+    double dy = ty - sy;
+    double dz = tz - sz;
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 == 0.0) return 0;
+    if (kernel == ORACLE_KERNEL_POLY) {
+        *g = poly_kernel(degree, tx, ty, tz, sx, sy, sz);
+        return 1;
+    }
+    double r = sqrt(r2);
+    if (kernel == ORACLE_KERNEL_YUKAWA)
+        *g = exp(-kappa * r) / r;       /* Yukawa, Eq. 2 right */
+    else
+        *g = 1.0 / r;                   /* Coulomb, Eq. 2 left */
+    return 1;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Direct summation, Eq. 1.                                                              */
+/* ------------------------------------------------------------------------------------ */
+
+int oracle_direct_sum(const double* tx, const double* ty, const double* tz, int64_t nt,
+                      const double* sx, const double* sy, const double* sz, const double* sq,
+                      int64_t ns, int32_t kernel, double kappa, int32_t degree,
+                      int32_t threads, double* phi, double* phi_abs)
+{
+    if (nt < 0 || ns < 0) return -1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+    /* phi(x_i) = sum_j G(x_i, y_j) q_j, j ascending. */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < nt; ++i) {
+        double acc = 0.0, acc_abs = 0.0;
+        for (int64_t j = 0; j < ns; ++j) {
+            double g;
+            if (!kernel_G(kernel, kappa, degree, tx[i], ty[i], tz[i], sx[j], sy[j], sz[j], &g))
+                continue;
+            acc = acc + g * sq[j];
+            acc_abs = acc_abs + fabs(g * sq[j]);
+        }
+        phi[i] = acc;
+        if (phi_abs) phi_abs[i] = acc_abs;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Tree of source clusters / target batches, Sec. II-D "Source Clusters and Target        */
+/* Batches" and the aspect-ratio rule of Sec. III-A (readings R2, R3, R6).                */
+/* ------------------------------------------------------------------------------------ */
+
+struct oracle_tree {
+    int64_t n;            /* particles */
+    int64_t n_nodes, cap;
+    int64_t* perm;        /* perm[i] = original index of the i-th particle in tree order */
+    int64_t* begin;       /* node's first position in tree order */
+    int64_t* count;       /* node's particle count */
+    int32_t* parent;      /* -1 for the root */
+    int32_t* level;       /* root = 0 */
+    int32_t* n_children;  /* 0 for a leaf */
+    int32_t* children;    /* 8 per node, in increasing octant order, -1 padded */
+    double* lo;           /* 3 per node: minimal box */
+    double* hi;
+    double* center;       /* 3 per node */
+    double* radius;
+};
+
+static int tree_grow(oracle_tree* t)
+{
+    if (t->n_nodes < t->cap) return 0;
+    int64_t cap = t->cap ? 2 * t->cap : 64;
+#define GROW(field, type, per)                                                      \
+    do {                                                                            \
+        type* p = (type*)realloc(t->field, (size_t)(cap * (per)) * sizeof(type));   \
+        if (!p) return -1;                                                          \
+        t->field = p;                                                               \
+    } while (0)
+    GROW(begin, int64_t, 1);
+    GROW(count, int64_t, 1);
+    GROW(parent, int32_t, 1);
+    GROW(level, int32_t, 1);
+    GROW(n_children, int32_t, 1);
+    GROW(children, int32_t, 8);
+    GROW(lo, double, 3);
+    GROW(hi, double, 3);
+    GROW(center, double, 3);
+    GROW(radius, double, 1);
+#undef GROW
+    t->cap = cap;
+    return 0;
+}
+
+/* Total order on the box coordinates: -0.0 sorts before +0.0 (reading R2). */
+static int less_total(double a, double b)
+{
+    return a < b || (a == b && signbit(a) && !signbit(b));
+}
+
+typedef struct {
+    const double* c[3];   /* x, y, z in original order */
+    int32_t max_leaf;
+    uint8_t* oct;         /* scratch: octant code per tree position */
+    int64_t* tmp;         /* scratch: partition buffer */
+} build_ctx;
+
+/* Builds the node covering tree positions [begin, begin+count) and its subtree.
+ * Returns the node id (DFS pre-order), or -1 on allocation failure. */
+static int64_t build_node(oracle_tree* t, build_ctx* b, int64_t begin, int64_t count,
+                          int32_t parent, int32_t level)
+{
+    if (tree_grow(t)) return -1;
+    int64_t id = t->n_nodes++;
+    t->begin[id] = begin;
+    t->count[id] = count;
+    t->parent[id] = parent;
+    t->level[id] = level;
+    t->n_children[id] = 0;
+    for (int c = 0; c < 8; ++c) t->children[8 * id + c] = -1;
+
+    /* Minimal bounding box of the node's own particles (R2). */
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = b->c[d][t->perm[begin]];
+        hi[d] = lo[d];
+        for (int64_t i = begin + 1; i < begin + count; ++i) {
+            double v = b->c[d][t->perm[i]];
+            if (less_total(v, lo[d])) lo[d] = v;
+            if (less_total(hi[d], v)) hi[d] = v;
+        }
+    }
+    /* Centre and radius (R3). */
+    double h[3];
+    for (int d = 0; d < 3; ++d) {
+        t->lo[3 * id + d] = lo[d];
+        t->hi[3 * id + d] = hi[d];
+        t->center[3 * id + d] = 0.5 * (lo[d] + hi[d]);
+        h[d] = 0.5 * (hi[d] - lo[d]);
+    }
+    t->radius[id] = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+
+    /* Recursion stops at max_leaf particles or fewer (Sec. II-D). */
+    if (count <= b->max_leaf) return id;
+    double L[3], Lmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        L[d] = hi[d] - lo[d];
+        if (L[d] > Lmax) Lmax = L[d];
+    }
+    if (Lmax == 0.0) return id;
+
+    /* Aspect-ratio rule (Sec. III-A): split only the dimensions whose extent is within a
+     * factor sqrt(2) of the longest; the longest always splits. */
+    int split[3];
+    double mid[3];
+    for (int d = 0; d < 3; ++d) {
+        split[d] = (L[d] * 1.4142135623730951 >= Lmax);
+        mid[d] = 0.5 * (lo[d] + hi[d]);
+    }
+
+    /* Octant of each particle: bit d set iff dimension d is split and coord >= midpoint. */
+    int64_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = begin; i < begin + count; ++i) {
+        int o = 0;
+        for (int d = 0; d < 3; ++d)
+            if (split[d] && !(b->c[d][t->perm[i]] < mid[d])) o |= (1 << d);
+        b->oct[i] = (uint8_t)o;
+        cnt[o]++;
+    }
+    int nonempty = 0;
+    for (int o = 0; o < 8; ++o) nonempty += (cnt[o] > 0);
+    if (nonempty <= 1) return id;   /* the split makes no progress: keep as a leaf (R6) */
+
+    /* Stable partition of perm[begin, begin+count) by octant. */
+    int64_t k = 0;
+    for (int o = 0; o < 8; ++o)
+        for (int64_t i = begin; i < begin + count; ++i)
+            if (b->oct[i] == o) b->tmp[k++] = t->perm[i];
+    memcpy(t->perm + begin, b->tmp, (size_t)count * sizeof(int64_t));
+
+    /* Children in increasing octant order; ids are assigned on entry (DFS pre-order). */
+    int64_t sub = begin;
+    int nc = 0;
+    for (int o = 0; o < 8; ++o) {
+        if (cnt[o] == 0) continue;
+        int64_t child = build_node(t, b, sub, cnt[o], (int32_t)id, level + 1);
+        if (child < 0) return -1;
+        t->children[8 * id + nc] = (int32_t)child;
+        nc++;
+        sub += cnt[o];
+    }
+    t->n_children[id] = nc;
+    return id;
+}
+
+void oracle_tree_free(oracle_tree* t)
+{
+    if (!t) return;
+    free(t->perm);
+    free(t->begin);
+    free(t->count);
+    free(t->parent);
+    free(t->level);
+    free(t->n_children);
+    free(t->children);
+    free(t->lo);
+    free(t->hi);
+    free(t->center);
+    free(t->radius);
+    free(t);
+}
+
+int oracle_tree_build(const double* x, const double* y, const double* z, int64_t n,
+                      int32_t max_leaf, oracle_tree** out)
+{
+    *out = NULL;
+    if (n < 1 || max_leaf < 1) return -1;
+    oracle_tree* t = (oracle_tree*)calloc(1, sizeof(oracle_tree));
+    if (!t) return -2;
+    t->n = n;
+    t->perm = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    build_ctx b;
+    b.c[0] = x;
+    b.c[1] = y;
+    b.c[2] = z;
+    b.max_leaf = max_leaf;
+    b.oct = (uint8_t*)malloc((size_t)n);
+    b.tmp = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    if (!t->perm || !b.oct || !b.tmp) {
+        free(b.oct);
+        free(b.tmp);
+        oracle_tree_free(t);
+        return -2;
+    }
+    for (int64_t i = 0; i < n; ++i) t->perm[i] = i;
+    int64_t root = build_node(t, &b, 0, n, -1, 0);
+    free(b.oct);
+    free(b.tmp);
+    if (root != 0) {
+        oracle_tree_free(t);
+        return -2;
+    }
+    *out = t;
+    return 0;
+}
+
+int64_t oracle_tree_num_nodes(const oracle_tree* t) { return t->n_nodes; }
+
+void oracle_tree_export(const oracle_tree* t, int64_t* perm, int64_t* begin, int64_t* count,
+                        int32_t* parent, int32_t* level, int32_t* n_children,
+                        int32_t* children, double* lo, double* hi, double* center,
+                        double* radius)
+{
+    int64_t m = t->n_nodes;
+    if (perm) memcpy(perm, t->perm, (size_t)t->n * sizeof(int64_t));
+    if (begin) memcpy(begin, t->begin, (size_t)m * sizeof(int64_t));
+    if (count) memcpy(count, t->count, (size_t)m * sizeof(int64_t));
+    if (parent) memcpy(parent, t->parent, (size_t)m * sizeof(int32_t));
+    if (level) memcpy(level, t->level, (size_t)m * sizeof(int32_t));
+    if (n_children) memcpy(n_children, t->n_children, (size_t)m * sizeof(int32_t));
+    if (children) memcpy(children, t->children, (size_t)(8 * m) * sizeof(int32_t));
+    if (lo) memcpy(lo, t->lo, (size_t)(3 * m) * sizeof(double));
+    if (hi) memcpy(hi, t->hi, (size_t)(3 * m) * sizeof(double));
+    if (center) memcpy(center, t->center, (size_t)(3 * m) * sizeof(double));
+    if (radius) memcpy(radius, t->radius, (size_t)m * sizeof(double));
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Barycentric Lagrange interpolation, Sec. II-A and II-C.                               */
+/* ------------------------------------------------------------------------------------ */
+
+/* Chebyshev points of the second kind mapped to [lo, hi] (Eq. 6, reading R7) and their
+ * barycentric weights (Eq. 7), which the linear map leaves unchanged. */
+void oracle_cheb(int32_t degree, double lo, double hi, double* s, double* w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k <= degree; ++k) {
+        double tk = cos(pi * (double)k / (double)degree);
+        s[k] = lo + 0.5 * (tk + 1.0) * (hi - lo);
+        double delta = (k == 0 || k == degree) ? 0.5 : 1.0;
+        w[k] = ((k % 2) ? -1.0 : 1.0) * delta;
+    }
+    s[0] = hi;
+    s[degree] = lo;
+}
+
+/* The n+1 values L_k(y), k = 0..n, of Eq. 4 on the Chebyshev points of [lo, hi].  When y
+ * coincides with a point s_k' (|y - s_k'| below the smallest positive normal double,
+ * Sec. II-C), L_k(y) = delta_{k k'} is enforced instead (reading R8: smallest k'). */
+void oracle_lagrange(int32_t degree, double lo, double hi, double y, double* a)
+{
+    double s[ORACLE_MAX_DEGREE + 1], w[ORACLE_MAX_DEGREE + 1];
+    oracle_cheb(degree, lo, hi, s, w);
+    for (int k = 0; k <= degree; ++k) {
+        if (fabs(y - s[k]) < DBL_MIN) {
+            for (int m = 0; m <= degree; ++m) a[m] = (m == k) ? 1.0 : 0.0;
+            return;
+        }
+    }
+    double denom = 0.0;
+    for (int k = 0; k <= degree; ++k) denom = denom + w[k] / (y - s[k]);
+    for (int k = 0; k <= degree; ++k) a[k] = (w[k] / (y - s[k])) / denom;
+}
+
+/* Modified charges of every cluster, Eq. 12 (Algorithm 1, the loop over source clusters):
+ * qhat_k = sum_{y_j in C} L_k1(y_j1) L_k2(y_j2) L_k3(y_j3) q_j, j in tree order,
+ * k = (k1*(n+1) + k2)*(n+1) + k3.  qhat has n_nodes*(n+1)^3 entries. */
+int oracle_modified_charges(const oracle_tree* t, const double* x, const double* y,
+                            const double* z, const double* q, int32_t degree,
+                            int32_t threads, double* qhat)
+{
+    if (degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
+    const int n1 = degree + 1;
+    const int64_t P = (int64_t)n1 * n1 * n1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < t->n_nodes; ++c) {
+        double* qh = qhat + c * P;
+        for (int64_t k = 0; k < P; ++k) qh[k] = 0.0;
+        const double* lo = t->lo + 3 * c;
+        const double* hi = t->hi + 3 * c;
+        double a1[ORACLE_MAX_DEGREE + 1], a2[ORACLE_MAX_DEGREE + 1], a3[ORACLE_MAX_DEGREE + 1];
+        for (int64_t i = t->begin[c]; i < t->begin[c] + t->count[c]; ++i) {
+            int64_t j = t->perm[i];
+            oracle_lagrange(degree, lo[0], hi[0], x[j], a1);
+            oracle_lagrange(degree, lo[1], hi[1], y[j], a2);
+            oracle_lagrange(degree, lo[2], hi[2], z[j], a3);
+            for (int k1 = 0; k1 < n1; ++k1)
+                for (int k2 = 0; k2 < n1; ++k2)
+                    for (int k3 = 0; k3 < n1; ++k3)
+                        qh[(k1 * n1 + k2) * n1 + k3] += a1[k1] * a2[k2] * a3[k3] * q[j];
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Treecode, Algorithm 1 with the MAC of Eq. 13 (readings R3-R5).                         */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+    const oracle_tree* bt;   /* target batches */
+    const oracle_tree* st;   /* source clusters */
+    const double *tx, *ty, *tz;              /* targets, original order */
+    const double *sx, *sy, *sz, *sq;         /* sources, original order */
+    const double* qhat;                      /* n_nodes(st) * P, or NULL when only listing */
+    double theta, kappa;
+    int32_t kernel, degree;
+    int64_t P;
+    double* phi;             /* original target order, or NULL when only listing */
+    double* phi_abs;
+    /* list recording (may be NULL) */
+    int64_t *app, *dir;
+    int64_t n_app, n_dir, cap_app, cap_dir;
+    int fail;
+} cp_ctx;
+
+static void list_push(int64_t** a, int64_t* n, int64_t* cap, int64_t v, int* fail)
+{
+    if (*n == *cap) {
+        int64_t nc = *cap ? 2 * *cap : 256;
+        int64_t* p = (int64_t*)realloc(*a, (size_t)nc * sizeof(int64_t));
+        if (!p) {
+            *fail = 1;
+            return;
+        }
+        *a = p;
+        *cap = nc;
+    }
+    (*a)[(*n)++] = v;
+}
+
+/* Batch-cluster approximation, Eq. 11: phi_i += sum_k G(x_i, s_k) qhat_k. */
+static void approx_interaction(cp_ctx* c, int64_t B, int64_t C)
+{
+    const int n1 = c->degree + 1;
+    double s1[ORACLE_MAX_DEGREE + 1], s2[ORACLE_MAX_DEGREE + 1], s3[ORACLE_MAX_DEGREE + 1];
+    double w[ORACLE_MAX_DEGREE + 1];
+    const double* lo = c->st->lo + 3 * C;
+    const double* hi = c->st->hi + 3 * C;
+    oracle_cheb(c->degree, lo[0], hi[0], s1, w);
+    oracle_cheb(c->degree, lo[1], hi[1], s2, w);
+    oracle_cheb(c->degree, lo[2], hi[2], s3, w);
+    const double* qh = c->qhat + C * c->P;
+    for (int64_t i = c->bt->begin[B]; i < c->bt->begin[B] + c->bt->count[B]; ++i) {
+        int64_t t = c->bt->perm[i];
+        double acc = c->phi[t], acc_abs = c->phi_abs ? c->phi_abs[t] : 0.0;
+        for (int k1 = 0; k1 < n1; ++k1)
+            for (int k2 = 0; k2 < n1; ++k2)
+                for (int k3 = 0; k3 < n1; ++k3) {
+                    double g;
+                    if (!kernel_G(c->kernel, c->kappa, c->degree, c->tx[t], c->ty[t], c->tz[t],
+                                  s1[k1], s2[k2], s3[k3], &g))
+                        continue;
+                    double term = g * qh[(k1 * n1 + k2) * n1 + k3];
+                    acc = acc + term;
+                    acc_abs = acc_abs + fabs(term);
+                }
+        c->phi[t] = acc;
+        if (c->phi_abs) c->phi_abs[t] = acc_abs;
+    }
+}
+
+/* Batch-cluster direct sum, Eq. 9: phi_i += sum_{y_j in C} G(x_i, y_j) q_j. */
+static void direct_interaction(cp_ctx* c, int64_t B, int64_t C)
+{
+    for (int64_t i = c->bt->begin[B]; i < c->bt->begin[B] + c->bt->count[B]; ++i) {
+        int64_t t = c->bt->perm[i];
+        double acc = c->phi[t], acc_abs = c->phi_abs ? c->phi_abs[t] : 0.0;
+        for (int64_t m = c->st->begin[C]; m < c->st->begin[C] + c->st->count[C]; ++m) {
+            int64_t j = c->st->perm[m];
+            double g;
+            if (!kernel_G(c->kernel, c->kappa, c->degree, c->tx[t], c->ty[t], c->tz[t],
+                          c->sx[j], c->sy[j], c->sz[j], &g))
+                continue;
+            double term = g * c->sq[j];
+            acc = acc + term;
+            acc_abs = acc_abs + fabs(term);
+        }
+        c->phi[t] = acc;
+        if (c->phi_abs) c->phi_abs[t] = acc_abs;
+    }
+}
+
+/* ComputePotential(batch, cluster) of Algorithm 1. */
+static void compute_potential(cp_ctx* c, int64_t B, int64_t C)
+{
+    const double* cb = c->bt->center + 3 * B;
+    const double* cc = c->st->center + 3 * C;
+    double dx = cb[0] - cc[0];
+    double dy = cb[1] - cc[1];
+    double dz = cb[2] - cc[2];
+    double R = sqrt(dx * dx + dy * dy + dz * dz);
+    double ratio = (c->bt->radius[B] + c->st->radius[C]) / R;
+    int geometric_ok = ratio < c->theta;      /* Eq. 13, first condition (R4) */
+    int size_ok = c->P < c->st->count[C];      /* Eq. 13, second condition */
+    if (geometric_ok && size_ok) {
+        if (c->app) list_push(&c->app, &c->n_app, &c->cap_app, C, &c->fail);
+        if (c->phi) approx_interaction(c, B, C);
+    } else if (!geometric_ok) {
+        if (c->st->n_children[C] == 0) {
+            if (c->dir) list_push(&c->dir, &c->n_dir, &c->cap_dir, C, &c->fail);
+            if (c->phi) direct_interaction(c, B, C);
+        } else {
+            for (int k = 0; k < c->st->n_children[C]; ++k)
+                compute_potential(c, B, c->st->children[8 * C + k]);
+        }
+    } else {
+        /* (n+1)^3 >= N_C: the whole cluster is summed directly (R5). */
+        if (c->dir) list_push(&c->dir, &c->n_dir, &c->cap_dir, C, &c->fail);
+        if (c->phi) direct_interaction(c, B, C);
+    }
+}
+
+/* Leaves of a tree in DFS order (these are the target batches of a batch tree). */
+static int64_t collect_leaves(const oracle_tree* t, int64_t* out)
+{
+    int64_t m = 0;
+    for (int64_t v = 0; v < t->n_nodes; ++v)
+        if (t->n_children[v] == 0) {
+            if (out) out[m] = v;
+            m++;
+        }
+    return m;
+}
+
+int64_t oracle_num_leaves(const oracle_tree* t) { return collect_leaves(t, NULL); }
+
+void oracle_leaves(const oracle_tree* t, int64_t* out) { collect_leaves(t, out); }
+
+/* Interaction lists of every batch (leaf of bt, in DFS order), as CSR arrays.  The caller
+ * passes arrays sized by a first call with NULL outputs, which only returns the totals. */
+int oracle_lists(const oracle_tree* bt, const oracle_tree* st, double theta, int32_t degree,
+                 int64_t* app_off, int64_t* app_ids, int64_t* dir_off, int64_t* dir_ids,
+                 int64_t* n_app_total, int64_t* n_dir_total)
+{
+    int64_t nb = collect_leaves(bt, NULL);
+    int64_t* leaves = (int64_t*)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(int64_t));
+    if (!leaves) return -2;
+    collect_leaves(bt, leaves);
+    const int64_t n1 = degree + 1;
+    int64_t ta = 0, td = 0;
+    if (app_off) app_off[0] = 0;
+    if (dir_off) dir_off[0] = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        cp_ctx c;
+        memset(&c, 0, sizeof(c));
+        c.bt = bt;
+        c.st = st;
+        c.theta = theta;
+        c.degree = degree;
+        c.P = n1 * n1 * n1;
+        c.app = (int64_t*)malloc(256 * sizeof(int64_t));
+        c.dir = (int64_t*)malloc(256 * sizeof(int64_t));
+        c.cap_app = c.cap_dir = 256;
+        if (!c.app || !c.dir) {
+            free(c.app);
+            free(c.dir);
+            free(leaves);
+            return -2;
+        }
+        compute_potential(&c, leaves[b], 0);
+        if (c.fail) {
+            free(c.app);
+            free(c.dir);
+            free(leaves);
+            return -2;
+        }
+        if (app_ids) memcpy(app_ids + ta, c.app, (size_t)c.n_app * sizeof(int64_t));
+        if (dir_ids) memcpy(dir_ids + td, c.dir, (size_t)c.n_dir * sizeof(int64_t));
+        ta += c.n_app;
+        td += c.n_dir;
+        if (app_off) app_off[b + 1] = ta;
+        if (dir_off) dir_off[b + 1] = td;
+        free(c.app);
+        free(c.dir);
+    }
+    free(leaves);
+    *n_app_total = ta;
+    *n_dir_total = td;
+    return 0;
+}
+
+static double now_seconds(void)
+{
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    return 0.0;
+#endif
+}
+
+/* Algorithm 1.  Targets and sources are the same particles (x, y, z, q), as in all of the
+ * paper's runs.  The source tree uses leaf_size (N_L) and the batch tree batch_size (N_B).
+ * If batch_subset is non-NULL, only those batches (indices into the DFS-ordered leaves of
+ * the batch tree) are evaluated; phi of the other targets is left at 0.  timings receives
+ * setup (trees), precompute (modified charges) and compute seconds. */
+int oracle_bltc(const double* x, const double* y, const double* z, const double* q, int64_t n,
+                double theta, int32_t degree, int32_t leaf_size, int32_t batch_size,
+                int32_t kernel, double kappa, int32_t threads, const int64_t* batch_subset,
+                int64_t n_subset, double* phi, double* phi_abs, double* timings)
+{
+    if (n < 1 || degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    double t0 = now_seconds();
+    oracle_tree *st = NULL, *bt = NULL;
+    if (oracle_tree_build(x, y, z, n, leaf_size, &st)) return -2;
+    if (oracle_tree_build(x, y, z, n, batch_size, &bt)) {
+        oracle_tree_free(st);
+        return -2;
+    }
+    double t1 = now_seconds();
+    const int64_t n1 = degree + 1, P = n1 * n1 * n1;
+    double* qhat = (double*)malloc((size_t)(st->n_nodes * P) * sizeof(double));
+    if (!qhat) {
+        oracle_tree_free(st);
+        oracle_tree_free(bt);
+        return -2;
+    }
+    oracle_modified_charges(st, x, y, z, q, degree, threads, qhat);
+    double t2 = now_seconds();
+
+    int64_t nb = collect_leaves(bt, NULL);
+    int64_t* leaves = (int64_t*)malloc((size_t)nb * sizeof(int64_t));
+    collect_leaves(bt, leaves);
+    for (int64_t i = 0; i < n; ++i) {
+        phi[i] = 0.0;
+        if (phi_abs) phi_abs[i] = 0.0;
+    }
+    int64_t todo = batch_subset ? n_subset : nb;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t u = 0; u < todo; ++u) {
+        int64_t b = batch_subset ? batch_subset[u] : u;
+        if (b < 0 || b >= nb) {
+            bad = 1;
+            continue;
+        }
+        cp_ctx c;
+        memset(&c, 0, sizeof(c));
+        c.bt = bt;
+        c.st = st;
+        c.tx = x;
+        c.ty = y;
+        c.tz = z;
+        c.sx = x;
+        c.sy = y;
+        c.sz = z;
+        c.sq = q;
+        c.qhat = qhat;
+        c.theta = theta;
+        c.kappa = kappa;
+        c.kernel = kernel;
+        c.degree = degree;
+        c.P = P;
+        c.phi = phi;
+        c.phi_abs = phi_abs;
+        compute_potential(&c, leaves[b], 0);
+    }
+    double t3 = now_seconds();
+    if (timings) {
+        timings[0] = t1 - t0;
+        timings[1] = t2 - t1;
+        timings[2] = t3 - t2;
+    }
+    free(leaves);
+    free(qhat);
+    oracle_tree_free(st);
+    oracle_tree_free(bt);
+    return bad ? -1 : 0;
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,65 @@
+/*
+ * bltc_oracle.h -- declarations of the FP64 CPU oracle (test infrastructure only).
+ *
+ * This header belongs to oracle/ alone.  The CUDA library neither includes it nor shares
+ * any of its definitions; tests reach both through their own Python bindings.
+ */
+#ifndef BLTC_ORACLE_H
+#define BLTC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORACLE_MAX_DEGREE 32
+
+enum { ORACLE_KERNEL_COULOMB = 0, ORACLE_KERNEL_YUKAWA = 1, ORACLE_KERNEL_POLY = 2 };
+
+typedef struct oracle_tree oracle_tree;
+
+/* Eq. 1 with the kernels of Eq. 2; pairs with r^2 == 0 are skipped. */
+int oracle_direct_sum(const double* tx, const double* ty, const double* tz, int64_t nt,
+                      const double* sx, const double* sy, const double* sz, const double* sq,
+                      int64_t ns, int32_t kernel, double kappa, int32_t degree,
+                      int32_t threads, double* phi, double* phi_abs);
+
+/* Sec. II-D tree of clusters (or batches) with the Sec. III-A aspect-ratio rule. */
+int oracle_tree_build(const double* x, const double* y, const double* z, int64_t n,
+                      int32_t max_leaf, oracle_tree** out);
+void oracle_tree_free(oracle_tree* t);
+int64_t oracle_tree_num_nodes(const oracle_tree* t);
+void oracle_tree_export(const oracle_tree* t, int64_t* perm, int64_t* begin, int64_t* count,
+                        int32_t* parent, int32_t* level, int32_t* n_children,
+                        int32_t* children, double* lo, double* hi, double* center,
+                        double* radius);
+int64_t oracle_num_leaves(const oracle_tree* t);
+void oracle_leaves(const oracle_tree* t, int64_t* out);
+
+/* Eq. 6-7 and Eq. 4-5 with the Sec. II-C exact-hit rule. */
+void oracle_cheb(int32_t degree, double lo, double hi, double* s, double* w);
+void oracle_lagrange(int32_t degree, double lo, double hi, double y, double* a);
+
+/* Eq. 12 for every node of the tree. */
+int oracle_modified_charges(const oracle_tree* t, const double* x, const double* y,
+                            const double* z, const double* q, int32_t degree,
+                            int32_t threads, double* qhat);
+
+/* Algorithm 1's ComputePotential recursion, recording the lists only. */
+int oracle_lists(const oracle_tree* bt, const oracle_tree* st, double theta, int32_t degree,
+                 int64_t* app_off, int64_t* app_ids, int64_t* dir_off, int64_t* dir_ids,
+                 int64_t* n_app_total, int64_t* n_dir_total);
+
+/* Algorithm 1 end to end (targets = sources). */
+int oracle_bltc(const double* x, const double* y, const double* z, const double* q, int64_t n,
+                double theta, int32_t degree, int32_t leaf_size, int32_t batch_size,
+                int32_t kernel, double kappa, int32_t threads, const int64_t* batch_subset,
+                int64_t n_subset, double* phi, double* phi_abs, double* timings);
+
+int oracle_max_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,61 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a temporary copy of ``oracle/bltc_oracle.c`` (never in the
+committed file), builds it with the same flags, and runs the fast oracle pins against it in
+a subprocess.  The pins must fail for every mutant, and pass for the unmodified copy.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "bltc_oracle.c")
+
+# (name, text in the source, replacement): one mistake each.
+MUTANTS = [
+    ("dropped_dz_term", "double r2 = dx * dx + dy * dy + dz * dz;", "double r2 = dx * dx + dy * dy;"),
+    ("yukawa_sign", "exp(-kappa * r) / r", "exp(kappa * r) / r"),
+    ("split_on_midpoint_low", "!(b->c[d][t->perm[i]] < mid[d])", "!(b->c[d][t->perm[i]] <= mid[d])"),
+    ("aspect_factor_two", "L[d] * 1.4142135623730951 >= Lmax", "L[d] * 2.0 >= Lmax"),
+    ("unstable_partition", "for (int64_t i = begin; i < begin + count; ++i)\n            if (b->oct[i] == o)",
+     "for (int64_t i = begin + count - 1; i >= begin; --i)\n            if (b->oct[i] == o)"),
+    ("radius_full_extent", "h[d] = 0.5 * (hi[d] - lo[d]);", "h[d] = (hi[d] - lo[d]);"),
+    ("cheb_endpoints_swapped", "s[0] = hi;\n    s[degree] = lo;", "s[0] = lo;\n    s[degree] = hi;"),
+    ("weight_sign", "w[k] = ((k % 2) ? -1.0 : 1.0) * delta;", "w[k] = delta;"),
+    ("no_exact_hit", "if (fabs(y - s[k]) < DBL_MIN) {", "if (0) {"),
+    ("qhat_transposed", "qh[(k1 * n1 + k2) * n1 + k3] += a1[k1]", "qh[(k3 * n1 + k2) * n1 + k1] += a1[k1]"),
+    ("far_field_uses_wrong_axis", "s1[k1], s2[k2], s3[k3], &g))", "s1[k1], s2[k3], s3[k2], &g))"),
+    ("self_pair_not_skipped", "if (r2 == 0.0) return 0;", "if (r2 < 0.0) return 0;"),
+    ("mac_ignores_size", "int size_ok = c->P < c->st->count[C];", "int size_ok = 1;"),
+]
+
+FAST = "not decays and not band and not degenerates"
+
+
+def _run_pins(tmp_path, text):
+    src = tmp_path / "m.c"
+    src.write_text(text)
+    lib = tmp_path / "libm.so"
+    subprocess.run(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                    "-I", os.path.join(ROOT, "oracle"), "-o", str(lib), str(src), "-lm"],
+                   check=True, capture_output=True)
+    env = dict(os.environ, BLTC_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", FAST],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode
+
+
+def test_unmodified_copy_passes(tmp_path):
+    with open(SRC) as f:
+        assert _run_pins(tmp_path, f.read()) == 0
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new):
+    with open(SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    assert _run_pins(tmp_path, text.replace(old, new)) != 0, f"pins missed mutant {name}"

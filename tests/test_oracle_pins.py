@@ -1,0 +1,408 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these checks re-types the oracle's own formulas: they use closed forms, hand-derived
+trees (tests/golden/trees_small.json), invariants of interpolation (partition of unity,
+moment reproduction, exactness for polynomial kernels), special cases that reduce to the
+direct sum, and brute-force coverage on small inputs.  A dropped term, a wrong sign or index,
+or a transposed operand anywhere in the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_01836_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------
+# Direct sum, Eq. 1-2
+# ---------------------------------------------------------------------------------------
+
+def _direct(pts, q, kernel=oracle.KERNEL_COULOMB, kappa=0.0):
+    pts = np.asarray(pts, dtype=np.float64).T
+    return oracle.direct_sum(pts, pts, np.asarray(q, dtype=np.float64), kernel, kappa)
+
+
+def test_direct_two_charges_closed_form():
+    # phi at each of two charges is the other charge over their distance (Eq. 1-2).
+    phi = _direct([[0.0, 0.0, 0.0], [0.0, 0.0, 0.5]], [0.75, -0.25])
+    assert phi[0] == -0.5 and phi[1] == 1.5
+    kappa = 0.5
+    phi = _direct([[0.0, 0.0, 0.0], [0.0, 0.5, 0.0]], [0.75, -0.25], oracle.KERNEL_YUKAWA, kappa)
+    assert phi[0] == pytest.approx(-0.25 * math.exp(-kappa * 0.5) / 0.5, rel=1e-15)
+    assert phi[1] == pytest.approx(0.75 * math.exp(-kappa * 0.5) / 0.5, rel=1e-15)
+
+
+def test_direct_pythagorean_triangle_exact():
+    # Distances 5, 12, 13 are integers, so every potential is an exact rational.
+    pts = [[0, 0, 0], [3, 4, 0], [3, 4, 12]]
+    q = [1.0, 2.0, 3.0]
+    phi = _direct(pts, q)
+    want = [Fraction(2, 5) + Fraction(3, 13), Fraction(1, 5) + Fraction(3, 12),
+            Fraction(1, 13) + Fraction(2, 12)]
+    for p, w in zip(phi, want):
+        assert abs(Fraction(p) - w) <= Fraction(1, 2 ** 50)
+
+
+def test_direct_cube_corners_symmetric():
+    # Eight unit charges on the corners of a cube of side a: by symmetry every corner sees
+    # 3 neighbours at a, 3 at a*sqrt2 and 1 at a*sqrt3.
+    a = 0.75
+    pts = [[a * i, a * j, a * k] for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+    phi = _direct(pts, [1.0] * 8)
+    want = 3 / a + 3 / (a * math.sqrt(2)) + 1 / (a * math.sqrt(3))
+    np.testing.assert_allclose(phi, want, rtol=2e-16 * 8)
+
+
+def test_direct_self_pairs_skipped():
+    # Targets are the sources: the r = 0 pair is skipped, also for duplicated particles.
+    assert _direct([[0.1, 0.2, 0.3]], [1.0])[0] == 0.0
+    phi = _direct([[0.5, 0.5, 0.5], [0.5, 0.5, 0.5], [0.5, 0.5, 1.0]], [1.0, 2.0, 4.0])
+    assert phi[0] == 8.0 and phi[1] == 8.0 and phi[2] == 6.0
+
+
+def test_direct_yukawa_kappa0_is_coulomb_bitwise():
+    x, y, z, q = inputs.uniform_cube(300, 11)
+    pts = np.stack([x, y, z])
+    c = oracle.direct_sum(pts, pts, q, oracle.KERNEL_COULOMB)
+    yk = oracle.direct_sum(pts, pts, q, oracle.KERNEL_YUKAWA, 0.0)
+    assert np.array_equal(c, yk)
+
+
+# ---------------------------------------------------------------------------------------
+# Trees, Sec. II-D and Sec. III-A
+# ---------------------------------------------------------------------------------------
+
+def _golden_trees():
+    with open(os.path.join(GOLDEN, "trees_small.json")) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_trees(), ids=lambda c: c["name"])
+def test_tree_hand_derived(case):
+    t = oracle.Tree(case["x"], case["y"], case["z"], case["max_leaf"])
+    assert t.perm.tolist() == case["perm"]
+    assert t.n_nodes == len(case["nodes"])
+    for i, nd in enumerate(case["nodes"]):
+        assert t.begin[i] == nd["begin"] and t.count[i] == nd["count"]
+        assert t.parent[i] == nd["parent"] and t.level[i] == nd["level"]
+        assert t.n_children[i] == len(nd["children"])
+        assert t.children[i, :len(nd["children"])].tolist() == nd["children"]
+        assert (t.children[i, len(nd["children"]):] == -1).all()
+        assert t.lo[i].tolist() == nd["lo"] and t.hi[i].tolist() == nd["hi"]
+        assert t.center[i].tolist() == nd["center"]
+        assert t.radius[i] == math.sqrt(nd["radius_sq"])
+
+
+def test_tree_signed_zero_box():
+    t = oracle.Tree([0.0, -0.0, 1.0], [1.0, 0.0, 0.5], [1.0, 0.0, 0.5], 3)
+    assert math.copysign(1.0, t.lo[0, 0]) == -1.0 and t.lo[0, 0] == 0.0
+
+
+def check_tree_invariants(t, x, y, z, max_leaf):
+    n = len(x)
+    assert sorted(t.perm.tolist()) == list(range(n))
+    assert t.begin[0] == 0 and t.count[0] == n and t.parent[0] == -1
+    coords = np.stack([x, y, z], axis=1)
+    sub = np.ones(t.n_nodes, np.int64)
+    for v in range(t.n_nodes - 1, -1, -1):
+        ch = t.children[v, :t.n_children[v]]
+        sub[v] = 1 + sub[ch].sum()
+    for v in range(t.n_nodes):
+        b, c = t.begin[v], t.count[v]
+        pts = coords[t.perm[b:b + c]]
+        assert (t.lo[v] == pts.min(axis=0)).all() and (t.hi[v] == pts.max(axis=0)).all()
+        ch = t.children[v, :t.n_children[v]]
+        if len(ch) == 0:
+            continue
+        assert len(ch) >= 2
+        # children partition the parent's range, in order, and are DFS pre-order numbered
+        assert t.begin[ch[0]] == b and ch[0] == v + 1
+        for a, bb in zip(ch[:-1], ch[1:]):
+            assert t.begin[bb] == t.begin[a] + t.count[a] and bb == a + sub[a]
+        assert t.begin[ch[-1]] + t.count[ch[-1]] == b + c
+        assert (t.parent[ch] == v).all() and (t.level[ch] == t.level[v] + 1).all()
+        assert c > max_leaf
+        # every child's particles lie on one side of every split midpoint
+        mid = 0.5 * (t.lo[v] + t.hi[v])
+        L = t.hi[v] - t.lo[v]
+        split = L * 1.4142135623730951 >= L.max()
+        for k in ch:
+            kp = coords[t.perm[t.begin[k]:t.begin[k] + t.count[k]]]
+            for d in range(3):
+                if split[d]:
+                    side = kp[:, d] < mid[d]
+                    assert side.all() or (~side).all()
+    # stable partitions of the identity leave every leaf's segment in increasing order
+    for v in range(t.n_nodes):
+        if t.n_children[v] == 0:
+            seg = t.perm[t.begin[v]:t.begin[v] + t.count[v]]
+            assert (np.diff(seg) > 0).all()
+
+
+@pytest.mark.parametrize("kind,n,leaf", [("cube", 5000, 100), ("plummer", 6000, 64),
+                                          ("cube", 3000, 1)])
+def test_tree_invariants(kind, n, leaf):
+    x, y, z, _ = inputs.system(kind, n, 123)
+    t = oracle.Tree(x, y, z, leaf)
+    check_tree_invariants(t, x, y, z, leaf)
+    leaves = t.leaves
+    assert (t.count[leaves] <= leaf).all() or kind == "plummer"
+    assert t.count[leaves].sum() == n
+
+
+def test_tree_scale_by_two_identical():
+    x, y, z, _ = inputs.uniform_cube(4000, 9)
+    a = oracle.Tree(x, y, z, 150)
+    b = oracle.Tree(2 * x, 2 * y, 2 * z, 150)
+    for k in ("perm", "begin", "count", "parent", "level", "n_children", "children"):
+        assert np.array_equal(getattr(a, k), getattr(b, k))
+    for k in ("lo", "hi", "center", "radius"):
+        assert np.array_equal(2 * getattr(a, k), getattr(b, k))
+
+
+# ---------------------------------------------------------------------------------------
+# Barycentric Lagrange interpolation, Sec. II-A and II-C
+# ---------------------------------------------------------------------------------------
+
+def test_cheb_points_closed_form():
+    s, w = oracle.cheb(4, -1.0, 1.0)
+    np.testing.assert_allclose(s, [1, math.sqrt(0.5), 0, -math.sqrt(0.5), -1], atol=1e-16)
+    assert s[0] == 1.0 and s[4] == -1.0
+    assert w.tolist() == [0.5, -1.0, 1.0, -1.0, 0.5]
+    s, w = oracle.cheb(3, 2.0, 6.0)          # [2, 6]: points 6, 5, 3, 2
+    np.testing.assert_allclose(s, [6, 5, 3, 2], rtol=1e-15)
+    assert s[0] == 6.0 and s[3] == 2.0
+    assert w.tolist() == [0.5, -1.0, 1.0, -0.5]
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8, 13])
+def test_cheb_weights_match_definition(n):
+    # Eq. 4 defines w_k = 1 / prod_{j != k} (s_k - s_j); Eq. 7 is that up to a common factor.
+    s, w = oracle.cheb(n, -1.0, 1.0)
+    true_w = np.array([1.0 / np.prod([s[k] - s[j] for j in range(n + 1) if j != k])
+                       for k in range(n + 1)])
+    ratio = true_w / w
+    np.testing.assert_allclose(ratio, ratio[0], rtol=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 4, 8, 13])
+def test_lagrange_kronecker_at_nodes(n):
+    lo, hi = -0.3, 0.7
+    s, _ = oracle.cheb(n, lo, hi)
+    for k in range(n + 1):
+        a = oracle.lagrange(n, lo, hi, s[k])
+        e = np.zeros(n + 1)
+        e[k] = 1.0
+        assert a.tolist() == e.tolist()      # exact hit, Eq. 5 enforced (Sec. II-C)
+
+
+@pytest.mark.parametrize("n", [1, 3, 8, 13])
+def test_lagrange_reproduces_polynomials(n):
+    # sum_k L_k(y) p(s_k) = p(y) for deg p <= n; partition of unity is m = 0.
+    lo, hi = -1.25, 0.5
+    s, _ = oracle.cheb(n, lo, hi)
+    rng = np.random.default_rng(n)
+    for yv in rng.uniform(lo, hi, 20):
+        a = oracle.lagrange(n, lo, hi, yv)
+        for m in range(n + 1):
+            assert abs(a @ (s ** m) - yv ** m) <= 1e-12 * max(1.0, abs(yv) ** m)
+        # degree n+1 is generally not reproduced (the rule is not trivially exact)
+    yv = 0.1234
+    a = oracle.lagrange(n, lo, hi, yv)
+    assert abs(a @ (s ** (n + 1)) - yv ** (n + 1)) > 1e-10
+
+
+def test_lagrange_matches_scipy_barycentric():
+    scipy_interp = pytest.importorskip("scipy.interpolate")
+    n, lo, hi = 9, 0.2, 1.7
+    s, _ = oracle.cheb(n, lo, hi)
+    f = np.cos(3 * s) + s ** 2
+    P = scipy_interp.BarycentricInterpolator(s, f)
+    for yv in np.linspace(lo, hi, 37):
+        assert oracle.lagrange(n, lo, hi, yv) @ f == pytest.approx(float(P(yv)), abs=1e-12)
+
+
+def test_lagrange_zero_extent_is_e0():
+    a = oracle.lagrange(6, 0.25, 0.25, 0.25)
+    assert a.tolist() == [1.0] + [0.0] * 6
+
+
+# ---------------------------------------------------------------------------------------
+# Modified charges, Eq. 12
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_modified_charges_moments(n):
+    # qhat reproduces every moment sum_j q_j y1^a y2^b y3^c with a, b, c <= n.
+    x, y, z, q = inputs.uniform_cube(3000, 21)
+    t = oracle.Tree(x, y, z, 400)
+    qh = oracle.modified_charges(t, q, n)
+    n1 = n + 1
+    for v in [0] + list(range(1, t.n_nodes, max(1, t.n_nodes // 6))):
+        idx = t.perm[t.begin[v]:t.begin[v] + t.count[v]]
+        s = [oracle.cheb(n, t.lo[v, d], t.hi[v, d])[0] for d in range(3)]
+        Q = qh[v].reshape(n1, n1, n1)
+        assert Q.sum() == pytest.approx(q[idx].sum(), abs=1e-12 * np.abs(q[idx]).sum())
+        for (a, b, c) in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (n, 0, 0), (0, n, n), (n, n, n),
+                          (1, 2 % n1, 0)]:
+            lhs = np.einsum("ijk,i,j,k->", Q, s[0] ** a, s[1] ** b, s[2] ** c)
+            rhs = np.sum(q[idx] * x[idx] ** a * y[idx] ** b * z[idx] ** c)
+            scale = np.sum(np.abs(q[idx]))
+            assert abs(lhs - rhs) <= 1e-11 * scale, (v, a, b, c)
+
+
+def test_modified_charges_single_corner_particle():
+    # A lone particle at a box corner takes the exact-hit path: qhat = q at that corner.
+    x = np.array([0.0, 1.0, 0.25])
+    y = np.array([0.0, 1.0, 0.5])
+    z = np.array([0.0, 1.0, 0.75])
+    q = np.array([2.0, 0.0, 0.0])
+    t = oracle.Tree(x, y, z, 8)
+    qh = oracle.modified_charges(t, q, 3).reshape(4, 4, 4)
+    expect = np.zeros((4, 4, 4))
+    expect[3, 3, 3] = 2.0     # s_n = lo on every axis
+    assert np.array_equal(qh, expect)
+
+
+# ---------------------------------------------------------------------------------------
+# Treecode, Algorithm 1 + Eq. 11, 13
+# ---------------------------------------------------------------------------------------
+
+def _system(n, seed=20031837):
+    return inputs.uniform_cube(n, seed)
+
+
+def test_lists_cover_every_pair_exactly_once():
+    x, y, z, _ = _system(6000, 77)
+    for theta, n in [(0.7, 4), (0.5, 2), (0.9, 6)]:
+        st = oracle.Tree(x, y, z, 200)
+        bt = oracle.Tree(x, y, z, 150)
+        L = oracle.lists(bt, st, theta, n)
+        N = len(x)
+        for b_i, B in enumerate(bt.leaves):
+            cover = np.zeros(N, np.int64)
+            for key in ("approx", "direct"):
+                ids = L[key + "_ids"][L[key + "_off"][b_i]:L[key + "_off"][b_i + 1]]
+                for C in ids:
+                    cover[st.begin[C]:st.begin[C] + st.count[C]] += 1
+            assert (cover == 1).all(), (theta, n, b_i)
+        P = (n + 1) ** 3
+        app = L["approx_ids"]
+        assert (st.count[app] > P).all()
+        assert len(app) > 0
+
+
+def test_theta_zero_equals_direct_sum():
+    x, y, z, q = _system(4000)
+    phi, _, _ = oracle.bltc(x, y, z, q, 0.0, 4, 300, 300)
+    ref = oracle.direct_sum(np.stack([x, y, z]), np.stack([x, y, z]), q)
+    assert oracle.rel_err(ref, phi) < 1e-14
+
+
+def test_size_check_routes_everything_direct():
+    # With (n+1)^3 >= every cluster size no cluster is approximated (Eq. 13, 2nd condition).
+    x, y, z, q = _system(3000)
+    phi, _, _ = oracle.bltc(x, y, z, q, 0.9, 13, 100, 100)  # (14)^3 = 2744 < 3000 only at root
+    ref = oracle.direct_sum(np.stack([x, y, z]), np.stack([x, y, z]), q)
+    assert oracle.rel_err(ref, phi) < 1e-14
+
+
+def test_yukawa_kappa0_equals_coulomb_bitwise():
+    x, y, z, q = _system(3000)
+    a, _, _ = oracle.bltc(x, y, z, q, 0.7, 4, 200, 200, oracle.KERNEL_COULOMB)
+    b, _, _ = oracle.bltc(x, y, z, q, 0.7, 4, 200, 200, oracle.KERNEL_YUKAWA, 0.0)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_polynomial_kernel_is_exact(n):
+    # G(x, y) of degree n in every source coordinate is interpolated exactly (Eq. 8), so the
+    # treecode equals the direct sum for any theta.
+    x, y, z, q = _system(4000, 3)
+    phi, _, _ = oracle.bltc(x, y, z, q, 0.7, n, 150, 150, oracle.KERNEL_POLY)
+    pts = np.stack([x, y, z])
+    ref, ref_abs = oracle.direct_sum(pts, pts, q, oracle.KERNEL_POLY, 0.0, n, with_abs=True)
+    assert np.max(np.abs(phi - ref) / ref_abs) < 1e-12
+    # and the approximation is actually used
+    st = oracle.Tree(x, y, z, 150)
+    assert len(oracle.lists(st, st, 0.7, n)["approx_ids"]) > 0
+
+
+_SAMPLED = {}
+
+
+def _sampled_system():
+    # Sec. IV samples the error at a subset of targets for large N; here three batches of a
+    # 2e5-particle cube with N_L = N_B = 2000, large enough that clusters of (n+1)^3 = 2744
+    # points (n = 13) still pass the size check of Eq. 13.
+    if not _SAMPLED:
+        x, y, z, q = inputs.uniform_cube(200000, 5)
+        bt = oracle.Tree(x, y, z, 2000)
+        pick = np.array([0, len(bt.leaves) // 2, len(bt.leaves) - 1])
+        idx = np.concatenate([bt.perm[bt.begin[bt.leaves[b]]:
+                                      bt.begin[bt.leaves[b]] + bt.count[bt.leaves[b]]]
+                              for b in pick])
+        pts = np.stack([x, y, z])
+        _SAMPLED.update(x=x, y=y, z=z, q=q, pick=pick, idx=idx,
+                        ref=oracle.direct_sum(pts[:, idx], pts, q))
+    return _SAMPLED
+
+
+def _sampled_err(theta, n, kernel=oracle.KERNEL_COULOMB, kappa=0.0, ref=None):
+    S = _sampled_system()
+    phi, _, _ = oracle.bltc(S["x"], S["y"], S["z"], S["q"], theta, n, 2000, 2000, kernel, kappa,
+                            batches=S["pick"])
+    return oracle.rel_err(S["ref"] if ref is None else ref, phi[S["idx"]])
+
+
+def test_error_decays_with_degree():
+    # Sec. IV (Fig. 5): for fixed theta the error falls towards machine precision as n grows,
+    # and a smaller theta is more accurate at the same n.
+    table = {th: [_sampled_err(th, n) for n in (1, 3, 5, 7, 9, 11, 13)] for th in (0.5, 0.7, 0.9)}
+    for th, errs in table.items():
+        assert all(b < a for a, b in zip(errs, errs[1:])), (th, errs)
+        assert errs[0] > 1e-3
+    for i in range(7):
+        assert table[0.5][i] < table[0.7][i] < table[0.9][i]
+    assert table[0.5][-1] < 1e-12
+
+
+def test_paper_accuracy_band():
+    # theta = 0.8, n = 8 gives 5-6 digit accuracy in the paper (Sec. IV, weak and strong
+    # scaling: errors 3e-6 .. 1.5e-5 with N_L = N_B = 4000); same broad band here.
+    S = _sampled_system()
+    assert 1e-8 < _sampled_err(0.8, 8) < 1e-4
+    pts = np.stack([S["x"], S["y"], S["z"]])
+    ref = oracle.direct_sum(pts[:, S["idx"]], pts, S["q"], oracle.KERNEL_YUKAWA, 0.5)
+    assert 1e-8 < _sampled_err(0.8, 8, oracle.KERNEL_YUKAWA, 0.5, ref) < 1e-4
+
+
+def test_small_n_degenerates_to_direct_sum():
+    # With N = 1e4 and N_L = 500 the leaves hold ~156 particles: for n >= 5 every candidate
+    # fails the size check (n+1)^3 < N_C at theta = 0.5, so Algorithm 1 is the direct sum.
+    x, y, z, q = _system(10000)
+    pts = np.stack([x, y, z])
+    ref = oracle.direct_sum(pts, pts, q)
+    phi, _, _ = oracle.bltc(x, y, z, q, 0.5, 5, 500, 500)
+    assert oracle.rel_err(ref, phi) < 1e-14
+    phi, _, _ = oracle.bltc(x, y, z, q, 0.7, 4, 500, 500)
+    assert 1e-8 < oracle.rel_err(ref, phi) < 1e-4
+
+
+def test_batch_subset_matches_full_run():
+    x, y, z, q = _system(5000)
+    full, _, _ = oracle.bltc(x, y, z, q, 0.7, 4, 300, 300)
+    bt = oracle.Tree(x, y, z, 300)
+    pick = np.array([0, 3, len(bt.leaves) - 1])
+    sub, _, _ = oracle.bltc(x, y, z, q, 0.7, 4, 300, 300, batches=pick)
+    for b in pick:
+        B = bt.leaves[b]
+        idx = bt.perm[bt.begin[B]:bt.begin[B] + bt.count[B]]
+        assert np.array_equal(sub[idx], full[idx])
