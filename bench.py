@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Time-to-solution of the GB300 barycentric Lagrange treecode on its headline workload.
+
+Workload: 1e6 particles uniform in [-1,1]^3 with charges uniform in [-1,1] (Sec. IV test
+systems), Coulomb kernel, theta = 0.7, degree n = 8, N_L = N_B = 2000, mixed precision.
+A step is one pass of the whole path on resident device inputs: source tree (= target
+batches), MAC lists, modified charges, far- and near-field sweep, finalize.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own independent system
+on its own GPU (replicas: the treecode of one system needs no exchange); the value is the
+whole job's targets per second over the slowest rank.  ``--impl reference`` times the FP64
+CPU oracle (Algorithm 1 as written, on the host cores) on a bounded sample of the same
+workload, extrapolated to the whole system by target count.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("targets/sec and effective interactions/sec at rel. err ≤1e-6 vs FP64 GPU BLTC; "
+          "p50/p99")
+WORKLOAD = dict(kind="cube", n=1_000_000, theta=0.7, degree=8, leaf=2000, batch=2000,
+                kernel=0, kappa=0.0, seed=20031838)
+WORKLOAD_NAME = ("uniform cube N=1e6 (q in [-1,1]), Coulomb, theta=0.7, n=8, N_L=N_B=2000, "
+                 "mixed FP32 evaluation / FP64 accumulation")
+# Roofline of the sweep: one interaction of the Coulomb kernel costs one MUFU.RSQ; the SFU
+# (XU) pipe issues 16 per clock per SM, so the peak interaction rate is SMs * 16 * f_max.
+XU_PER_CLK_PER_SM = 16
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 256 << 20
+SWEEP_SOURCE = os.path.join(ROOT, "paper_2003_01836_gb300", "csrc", "sweep.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_sweep_mixed_traffic.txt")
+
+
+# ---- distributed helpers (one process per GPU, replicas) --------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local_rank)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(per_rank_ms: float, n_per_rank: int, dist: Dist) -> dict:
+    """Whole-job throughput over the slowest rank (weak scaling: fixed work per GPU)."""
+    slowest = dist.max(per_rank_ms)
+    total_targets = dist.sum(n_per_rank)
+    return {"ms_per_step": slowest, "targets_per_s": total_targets / (slowest / 1e3),
+            "total_targets": total_targets}
+
+
+# ---- clocks sampled during the timed region ----------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)], stdout=self.out,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ---- the CPU oracle on a bounded sample ----------------------------------------------------
+
+def oracle_sample(x, y, z, q, w, budget_batches=None):
+    """Algorithm 1 on the host cores: full trees and modified charges, ComputePotential on a
+    sample of batches; time-to-solution extrapolated by target count."""
+    import oracle
+    cores = os.cpu_count() or 1
+    st = oracle.Tree(x, y, z, w["leaf"])
+    nl = len(st.leaves)
+    k = budget_batches or max(2, min(nl, cores))
+    pick = np.unique(np.linspace(0, nl - 1, k).astype(np.int64))
+    targets = int(st.count[st.leaves[pick]].sum())
+    t0 = time.perf_counter()
+    _, _, tm = oracle.bltc(x, y, z, q, w["theta"], w["degree"], w["leaf"], w["batch"],
+                           w["kernel"], w["kappa"], threads=cores, batches=pick)
+    wall = time.perf_counter() - t0
+    n = len(x)
+    t_est = tm["setup"] + tm["precompute"] + tm["compute"] * (n / targets)
+    return {"targets_per_s": n / t_est, "t_est_s": t_est, "wall_s": wall, "cores": cores,
+            "sample": (f"full source/batch trees and modified charges of the {n}-particle "
+                       f"system, ComputePotential on {len(pick)} of {nl} batches "
+                       f"({targets} targets); time extrapolated by target count"),
+            "phases_s": tm}
+
+
+# ---- our arm -----------------------------------------------------------------------------
+
+def traffic_for_current_kernel():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on the
+    current sweep source (matching SHA-256), else None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            kv = dict(line.strip().split(": ", 1) for line in f if ": " in line)
+        with open(SWEEP_SOURCE, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if kv.get("sweep_source_sha256") != sha:
+            return None
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_ours(args, dist: Dist):
+    import torch
+
+    import paper_2003_01836_gb300 as b
+    from paper_2003_01836_gb300 import build, inputs
+    build.build()
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+    x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"] + dist.rank)
+    X = [torch.from_numpy(a).to(f"cuda:{dev}") for a in (x, y, z, q)]
+    phi = torch.empty_like(X[0])
+    ctx = b.Context(dev)
+    p = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
+                 b.BLTC_PRECISION_MIXED)
+    b.bltc_context_set_timing(ctx.h, True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    for _ in range(args.warmup):
+        ctx.solve(*X, p, phi)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev)
+    step_ms, phases = [], []
+    launches0 = b.bltc_context_launch_count(ctx.h)
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.solve(*X, p, phi)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        phases.append(b.bltc_last_timings(ctx.h))
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    launches = b.bltc_context_launch_count(ctx.h) - launches0
+    mean_ms = sum(step_ms) / len(step_ms)
+    agg = aggregate(mean_ms, w["n"], dist)
+
+    # evaluated interactions of one step (same lists every step)
+    st = b.bltc_tree_build(ctx.h, X[0], X[1], X[2], X[3], w["leaf"])
+    L = b.bltc_lists_build(ctx.h, st, st, p)
+    counts = b.bltc_stats(ctx.h, L)
+    n_batches = b.bltc_lists_info(L)["n_batches"]
+    b.bltc_lists_destroy(L)
+    b.bltc_tree_destroy(st)
+    evaluated = counts["direct"] + counts["approx"]
+
+    ph = {k: statistics.mean(d[k] for d in phases) for k in phases[0]}
+    sweep_s = ph["sweep"] / 1e3
+    achieved = evaluated / sweep_s / 1e9
+    peak = ctx.sm_count * XU_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+    roofline = {"bound": "alu", "pipe": "XU (MUFU rsqrt), 1 per Coulomb interaction",
+                "kernel": "k_sweep_mixed<Coulomb>", "achieved": achieved, "peak": peak,
+                "unit": "G interactions/s", "frac": achieved / peak,
+                "traffic": traffic_for_current_kernel(),
+                "peak_basis": f"{ctx.sm_count} SMs x {XU_PER_CLK_PER_SM}/clk x "
+                              f"{SM_MAX_MHZ:.0f} MHz (recipe max SM clock)",
+                "units_per_launch": evaluated}
+
+    out = {"metric": METRIC, "value": agg["targets_per_s"], "unit": "targets/s",
+           "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": agg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 (f64 accumulation)", "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAME, "n_particles": w["n"], "theta": w["theta"],
+                      "degree": w["degree"], "leaf_size": w["leaf"], "batch_size": w["batch"],
+                      "kernel": "coulomb", "precision": "mixed", "batches": n_batches,
+                      "parallelism": f"replicas x{dist.world}",
+                      "l2": "flushed before every timed step (256 MiB device write)"},
+           "effective_interactions_per_s": w["n"] * w["n"] * dist.world / (agg["ms_per_step"] / 1e3),
+           "evaluated_interactions_per_step": evaluated,
+           "evaluated_interactions_per_s": evaluated * dist.world / (agg["ms_per_step"] / 1e3),
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                          "p99": float(np.percentile(step_ms, 99)),
+                          "min": min(step_ms), "max": max(step_ms)},
+           "phases_ms": ph, "clocks": clocks, "gpu_launches": int(launches),
+           "roofline": roofline}
+
+    if not args.no_check:
+        out["error"] = check_errors(ctx, b, X, p, w, phi)
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(ctx, b, x, y, z, q, p, args, dist, w)
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(x, y, z, q, w)
+        out["cpu_baseline"] = {"value": cb["targets_per_s"], "unit": "targets/s",
+                               "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"],
+                               "t_est_s": cb["t_est_s"], "wall_s": cb["wall_s"]}
+    ctx.close()
+    return out
+
+
+def check_errors(ctx, b, X, p, w, phi_mixed):
+    """Relative 2-norm errors (Eq. 16): mixed vs FP64 GPU treecode (the metric's condition),
+    and both vs the FP64 GPU direct sum on a seeded sample of targets."""
+    import torch
+    import oracle
+    phi_mx = phi_mixed.clone()
+    p64 = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
+                   b.BLTC_PRECISION_FP64)
+    phi64 = torch.empty_like(phi_mx)
+    t0 = time.perf_counter()
+    ctx.solve(*X, p64, phi64)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    rng = np.random.default_rng(20031836)
+    idx = torch.from_numpy(np.sort(rng.choice(w["n"], size=min(w["n"], 4096), replace=False))).cuda()
+    T = [a.index_select(0, idx).contiguous() for a in X[:3]]
+    ref = torch.empty_like(T[0])
+    b.bltc_direct_sum(ctx.h, *T, *X[:3], X[3], p64, ref)
+    torch.cuda.synchronize()
+    h = lambda t: t.cpu().numpy()
+    e_mx_64 = oracle.rel_err(h(phi64), h(phi_mx))
+    return {"mixed_vs_fp64_gpu_bltc": e_mx_64, "meets_1e-6": bool(e_mx_64 <= 1e-6),
+            "fp64_bltc_vs_direct_sampled": oracle.rel_err(h(ref), h(phi64.index_select(0, idx))),
+            "mixed_bltc_vs_direct_sampled": oracle.rel_err(h(ref), h(phi_mx.index_select(0, idx))),
+            "fp64_gpu_bltc_seconds": t64, "direct_sample_targets": int(idx.numel())}
+
+
+def run_e2e(ctx, b, x, y, z, q, p, args, dist, w):
+    """The same metric through bltc_solve_host: pinned host inputs copied in and phi copied
+    back inside every timed step."""
+    import torch
+    H = [torch.from_numpy(a).pin_memory() for a in (x, y, z, q)]
+    out = torch.empty(w["n"], dtype=torch.float64).pin_memory()
+    Hn = [t.numpy() for t in H]
+    on = out.numpy()
+    for _ in range(max(1, min(args.warmup, 2))):
+        b.bltc_solve_host(ctx.h, *Hn, p, on)
+    k = max(1, min(args.steps, 5))
+    dist.barrier()
+    times = []
+    for _ in range(k):
+        t0 = time.perf_counter()
+        b.bltc_solve_host(ctx.h, *Hn, p, on)   # synchronizes
+        times.append(time.perf_counter() - t0)
+    dist.barrier()
+    t = dist.max(sum(times) / len(times))
+    total = dist.sum(w["n"])
+    return {"value": total / t, "unit": "targets/s", "h2d_bytes_per_step": 4 * 8 * w["n"],
+            "d2h_bytes_per_step": 8 * w["n"], "steps": k, "ms_per_step": t * 1e3}
+
+
+# ---- reference arm: the oracle --------------------------------------------------------------
+
+def run_reference(args, dist: Dist):
+    if dist.rank != 0:
+        return None
+    from paper_2003_01836_gb300 import inputs
+    import oracle
+    oracle.build()
+    w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+    x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"])
+    cores = os.cpu_count() or 1
+    k = max(2, cores // 2)
+    for _ in range(args.warmup):
+        oracle_sample(x, y, z, q, w, budget_batches=2)
+    runs = [oracle_sample(x, y, z, q, w, budget_batches=k) for _ in range(args.steps)]
+    t = statistics.mean(r["t_est_s"] for r in runs)
+    v = w["n"] / t
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "targets/s",
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME.replace("mixed FP32 evaluation / FP64 accumulation",
+                                                         "FP64 CPU oracle"),
+                       "n_particles": w["n"], "theta": w["theta"], "degree": w["degree"],
+                       "leaf_size": w["leaf"], "batch_size": w["batch"]},
+            "cpu_baseline": {"value": v, "unit": "targets/s", "cores": runs[0]["cores"],
+                             "kind": "oracle", "sample": runs[0]["sample"]},
+            "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=0, help="override the particle count (smoke runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    dist = Dist()
+    try:
+        out = run_reference(args, dist) if args.impl == "reference" else run_ours(args, dist)
+        if out is not None and dist.rank == 0:
+            print(json.dumps(out), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * bltc.h -- C ABI of the GB300 barycentric Lagrange treecode (BLTC) library.
+ *
+ * The library evaluates the potentials
+ *     phi(x_i) = sum_j G(x_i, y_j) q_j,   G = 1/r (Coulomb) or exp(-kappa r)/r (Yukawa)
+ * of Eq. 1-2 of Vaughn, Wilson and Krasny, "A GPU-Accelerated Barycentric Lagrange
+ * Treecode" (2020), with the treecode of Algorithm 1: a tree of source clusters and target
+ * batches (Sec. II-D), interaction lists from the multipole acceptance criterion (MAC,
+ * Eq. 13), modified charges at tensor-product Chebyshev points (Eq. 12, Sec. II-C), and the
+ * batch-cluster approximation (Eq. 11) and direct (Eq. 9) sums.  Every step runs on the GPU.
+ *
+ * Conventions, for every entry point unless its comment says otherwise:
+ *   - Pointers named x, y, z, q, phi, tx, ... are DEVICE pointers owned by the caller
+ *     (for example torch tensors' data_ptr()), FP64, contiguous, one value per particle in
+ *     the caller's order.  The library never frees or keeps them past the call.
+ *   - Work is enqueued on the context's stream (bltc_context_set_stream) and may still be
+ *     running when the call returns.  Calls whose comment says "synchronizes" wait for the
+ *     stream before returning.  A call that needs a count computed on the device (tree
+ *     build, list build, evaluate, solve) synchronizes the stream internally.
+ *   - Handles (bltc_tree, bltc_lists) own their device memory, allocated through the
+ *     context's allocator; only the matching *_destroy frees it.  A handle must not
+ *     outlive its context.
+ *   - Every call returns a bltc_status; on failure nothing observable was written to the
+ *     caller's output buffers, and bltc_last_error() describes the failure.  No C++
+ *     exception crosses this boundary.
+ *   - A context is not thread-safe: use one per host thread.
+ *
+ * Readings of the paper that the library implements exactly (shared with the test oracle,
+ * which is a separate implementation):
+ *   - a pair with r^2 == 0 is skipped (targets are the sources, Eq. 1);
+ *   - boxes are the minimal axis-aligned boxes of their particles (Sec. II-D), -0.0 < +0.0;
+ *   - centre c = 0.5*(lo+hi), radius = |0.5*(hi-lo)|, R = |c_B - c_C|, all FP64, no fused
+ *     multiply-add; the MAC's geometric part is (r_B + r_C)/R < theta (a NaN ratio fails);
+ *   - dimension d is split iff (hi_d-lo_d)*sqrt(2) >= longest extent (Sec. III-A); a
+ *     particle goes low iff coord < 0.5*(lo_d+hi_d); children in increasing octant order
+ *     (bit0/1/2 = x/y/z high), empty ones dropped, stable partition; a node is a leaf iff
+ *     count <= max_leaf, its extent is zero, or the split leaves one non-empty child; node
+ *     ids are DFS pre-order;
+ *   - Chebyshev points s_k = lo + 0.5*(cos(pi k/n)+1)*(hi-lo) with s_0 = hi, s_n = lo;
+ *     a source coordinate within DBL_MIN of s_k takes L_k = 1 exactly (Sec. II-C).
+ */
+#ifndef BLTC_H
+#define BLTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BLTC_VERSION 1
+#define BLTC_MAX_DEGREE 16
+
+typedef enum bltc_status {
+    BLTC_OK = 0,
+    BLTC_ERR_ARG = -1,      /* an argument is out of range or non-finite; nothing was run */
+    BLTC_ERR_OOM = -2,      /* the allocator returned no memory */
+    BLTC_ERR_CUDA = -3,     /* a CUDA call failed; the message names it */
+    BLTC_ERR_TIMEOUT = -4,  /* reserved for bounded device-side waits (none in this version) */
+    BLTC_ERR_STATE = -5     /* handles that do not belong together, or a step missing */
+} bltc_status;
+
+enum { BLTC_KERNEL_COULOMB = 0, BLTC_KERNEL_YUKAWA = 1 };
+
+/* FP64: every step in FP64 (the reference path; Sec. IV computes in double precision).
+ * MIXED: kernel evaluations in FP32 on coordinates relative to the batch centre with FP32
+ * sums over one cluster; cross-cluster sums, boxes, MAC, Chebyshev points and the
+ * source-minus-point differences of the modified charges stay FP64. */
+enum { BLTC_PRECISION_FP64 = 0, BLTC_PRECISION_MIXED = 1 };
+
+/* Treecode parameters of Algorithm 1 ("input: theta, n, N_L, N_B") plus the kernel. */
+typedef struct bltc_params {
+    int32_t degree;      /* n, interpolation degree, 1..BLTC_MAX_DEGREE; (n+1)^3 points */
+    int32_t leaf_size;   /* N_L >= 1, source clusters hold at most N_L particles */
+    int32_t batch_size;  /* N_B >= 1, target batches hold at most N_B particles */
+    int32_t kernel;      /* BLTC_KERNEL_COULOMB or BLTC_KERNEL_YUKAWA */
+    int32_t precision;   /* BLTC_PRECISION_FP64 or BLTC_PRECISION_MIXED */
+    int32_t reserved;    /* must be 0 */
+    double theta;        /* MAC parameter, 0 <= theta < 1 (theta = 0: all direct) */
+    double kappa;        /* Yukawa inverse Debye length, >= 0 (ignored for Coulomb) */
+} bltc_params;
+
+typedef struct bltc_context bltc_context;
+typedef struct bltc_tree bltc_tree;
+typedef struct bltc_lists bltc_lists;
+
+/* Optional allocator hooks.  alloc returns device memory of >= bytes usable in stream order
+ * on `stream`, or NULL; free releases it in stream order.  Default: a CUDA memory pool of
+ * the context's device (cudaMallocFromPoolAsync / cudaFreeAsync). */
+typedef void* (*bltc_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*bltc_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* ---- context ---------------------------------------------------------------------- */
+
+/* Creates a context on CUDA `device` enqueuing on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  *out receives the handle.  Errors: ARG (out NULL, bad device),
+ * CUDA. */
+bltc_status bltc_context_create(int device, void* stream, bltc_context** out);
+void bltc_context_destroy(bltc_context* ctx);
+bltc_status bltc_context_set_stream(bltc_context* ctx, void* stream);
+bltc_status bltc_context_set_allocator(bltc_context* ctx, bltc_alloc_fn alloc,
+                                       bltc_free_fn free_fn, void* user);
+/* Waits for the context's stream.  Errors: CUDA. */
+bltc_status bltc_synchronize(bltc_context* ctx);
+/* The message of the last failed call on ctx ("" if none); valid until the next call. */
+const char* bltc_last_error(const bltc_context* ctx);
+int bltc_version(void);
+/* Multiprocessor count of the context's device (the persistent sweep's grid unit). */
+int bltc_device_sm_count(const bltc_context* ctx);
+/* Number of CUDA kernels this context has launched so far (a diagnostic counter). */
+int64_t bltc_context_launch_count(const bltc_context* ctx);
+/* Enables (1) or disables (0) phase timing: CUDA events recorded on the context's stream
+ * at the phase boundaries of bltc_solve / bltc_evaluate.  Errors: ARG, CUDA. */
+bltc_status bltc_context_set_timing(bltc_context* ctx, int enable);
+/* Milliseconds of the last timed bltc_solve (or bltc_evaluate), ms[7] = {trees, lists,
+ * modified charges, work plan, sweep kernel, finalize, total}; -1 for a phase that was not
+ * recorded.  Waits for the last recorded event.  Errors: ARG, CUDA. */
+bltc_status bltc_last_timings(bltc_context* ctx, float* ms);
+
+/* ---- A0: tree of source clusters / target batches (Sec. II-D, Sec. III-A) ---------- */
+
+/* Builds the tree over the n particles (x, y, z, and charges q, or q = NULL for a target
+ * tree), splitting every node holding more than max_leaf particles by the rules above.
+ * The tree keeps its own permuted FP64 copy of the particles.  Synchronizes once per tree
+ * level.  Errors: ARG (n < 1, n >= 2^31, max_leaf < 1, NULL pointer, non-finite
+ * coordinate or charge), OOM, CUDA. */
+bltc_status bltc_tree_build(bltc_context* ctx, const double* x, const double* y,
+                            const double* z, const double* q, int64_t n, int32_t max_leaf,
+                            bltc_tree** out);
+void bltc_tree_destroy(bltc_tree* tree);
+/* Sizes of a built tree: particles, nodes, leaves, levels (root only = 1).  Host out
+ * pointers, each may be NULL. */
+bltc_status bltc_tree_info(const bltc_tree* tree, int64_t* n_particles, int64_t* n_nodes,
+                           int64_t* n_leaves, int32_t* n_levels);
+/* Copies the tree to HOST arrays (each may be NULL), nodes in DFS pre-order:
+ * perm[n] (original index of the i-th particle in tree order), begin/count[m],
+ * parent[m] (-1 at the root), level[m], n_children[m], children[8*m] (-1 padded, in
+ * increasing octant order), lo/hi/center[3*m] (x, y, z per node), radius[m].
+ * Synchronizes.  Errors: ARG, CUDA. */
+bltc_status bltc_tree_export(bltc_context* ctx, const bltc_tree* tree, int64_t* perm,
+                             int64_t* begin, int64_t* count, int32_t* parent, int32_t* level,
+                             int32_t* n_children, int32_t* children, double* lo, double* hi,
+                             double* center, double* radius);
+
+/* ---- A1: interaction lists (MAC of Eq. 13, ComputePotential of Algorithm 1) -------- */
+
+/* For every target batch (leaf of `batches`, DFS order) walks Algorithm 1's
+ * ComputePotential from the root of `sources` and records the clusters approximated
+ * (MAC passes) and summed directly (leaf with a failed geometric test, or a cluster with
+ * (n+1)^3 >= N_C), each list in the recursion's visit order.  Uses params->theta and
+ * params->degree.  batches may equal sources.  Synchronizes.  Errors: ARG, OOM, CUDA. */
+bltc_status bltc_lists_build(bltc_context* ctx, const bltc_tree* batches,
+                             const bltc_tree* sources, const bltc_params* params,
+                             bltc_lists** out);
+void bltc_lists_destroy(bltc_lists* lists);
+bltc_status bltc_lists_info(const bltc_lists* lists, int64_t* n_batches, int64_t* n_approx,
+                            int64_t* n_direct);
+/* Copies the lists to HOST CSR arrays (each may be NULL): approx_off/direct_off
+ * [n_batches+1] and approx_ids[n_approx]/direct_ids[n_direct] (source node ids, DFS
+ * pre-order numbering).  Synchronizes.  Errors: ARG, CUDA. */
+bltc_status bltc_lists_export(bltc_context* ctx, const bltc_lists* lists, int64_t* approx_off,
+                              int64_t* approx_ids, int64_t* direct_off, int64_t* direct_ids);
+/* Evaluated kernel interactions of one evaluation: sum over batches of N_B * N_C for the
+ * direct list and N_B * (n+1)^3 for the approximation list.  Synchronizes. */
+bltc_status bltc_stats(bltc_context* ctx, const bltc_lists* lists,
+                       int64_t* n_direct_interactions, int64_t* n_approx_interactions);
+
+/* ---- A2: modified charges (Eq. 12; Eq. 14-15; exact hits, Sec. II-C) --------------- */
+
+/* Computes qhat_k = sum_{y_j in C} L_k1(y_j1) L_k2(y_j2) L_k3(y_j3) q_j for every cluster
+ * C of `sources` with more than (n+1)^3 particles that appears in an approximation list of
+ * `lists` (every such cluster if lists is NULL).  The source tree must carry charges.
+ * Stored in the tree for params->degree and params->precision.  Errors: ARG, STATE, OOM,
+ * CUDA. */
+bltc_status bltc_modified_charges(bltc_context* ctx, bltc_tree* sources,
+                                  const bltc_lists* lists, const bltc_params* params);
+/* Copies the modified charges to a HOST array qhat[n_nodes * (n+1)^3] (node in DFS order,
+ * k = (k1*(n+1) + k2)*(n+1) + k3); clusters without modified charges get NaN.
+ * Synchronizes.  Errors: ARG, STATE, CUDA. */
+bltc_status bltc_modified_charges_export(bltc_context* ctx, const bltc_tree* sources,
+                                         double* qhat);
+
+/* ---- A3-A5: far-field and near-field sweeps and the per-target finalize ------------ */
+
+/* phi[i] = sum over the approximation list of batch(i) of Eq. 11 plus sum over its direct
+ * list of Eq. 9, for every target i of `batches`, written to the caller's device buffer
+ * phi[n_targets] in the caller's original target order.  Needs bltc_modified_charges for
+ * the same degree and precision.  Runs the far/near sweep as one persistent launch over a
+ * work queue of (batch, list range) items, then sums each target's per-item partials in a
+ * fixed order (deterministic).  Errors: ARG, STATE, OOM, CUDA. */
+bltc_status bltc_evaluate(bltc_context* ctx, const bltc_lists* lists, const bltc_tree* batches,
+                          const bltc_tree* sources, const bltc_params* params, double* phi);
+
+/* The whole of Algorithm 1 with targets = sources: builds the source tree (leaf_size) and
+ * the batch tree (batch_size; shared when equal), the lists, the modified charges, and
+ * evaluates phi[n] (device, original order).  Errors: as the steps above. */
+bltc_status bltc_solve(bltc_context* ctx, const double* x, const double* y, const double* z,
+                       const double* q, int64_t n, const bltc_params* params, double* phi);
+
+/* bltc_solve for HOST buffers x, y, z, q, phi (pinned memory recommended): copies the
+ * inputs to the device, solves, copies phi back.  Synchronizes.  Errors: as bltc_solve. */
+bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,
+                            const double* z, const double* q, int64_t n,
+                            const bltc_params* params, double* phi);
+
+/* ---- direct summation, Eq. 1 (the GPU baseline) ----------------------------------- */
+
+/* phi[i] = sum_j G(x_i, y_j) q_j over all nt targets (tx, ty, tz) and ns sources
+ * (sx, sy, sz, sq), pairs with r^2 == 0 skipped; params->kernel, kappa and precision are
+ * used (MIXED: FP32 evaluation on absolute coordinates, FP32 sums over tiles of sources,
+ * FP64 across tiles).  Device pointers.  Errors: ARG, OOM, CUDA. */
+bltc_status bltc_direct_sum(bltc_context* ctx, const double* tx, const double* ty,
+                            const double* tz, int64_t nt, const double* sx, const double* sy,
+                            const double* sz, const double* sq, int64_t ns,
+                            const bltc_params* params, double* phi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLTC_H */

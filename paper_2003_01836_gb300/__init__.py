@@ -1,1 +1,387 @@
-"""GB300-native barycentric Lagrange treecode (placeholder until the binding lands)."""
+"""GB300-native barycentric Lagrange treecode (BLTC), Python binding of include/bltc.h.
+
+The functions below carry the C ABI's names and only marshal arguments: torch tensors become
+device pointers, torch's current CUDA stream becomes the context's stream, and a non-zero
+status becomes a ``BltcError``.  Every step of the treecode runs in the CUDA library
+``_build/libbltc.so`` (built by ``build.build()``); there is no CPU path, and importing a
+function that needs the library raises if it has not been built.
+
+The paper: Vaughn, Wilson and Krasny, "A GPU-Accelerated Barycentric Lagrange Treecode"
+(2020) -- Eq. 1-2 (potentials), Eq. 4-8 (barycentric Lagrange interpolation), Eq. 11-13
+(approximation, modified charges, MAC), Algorithm 1 (the treecode).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbltc.so")
+
+BLTC_OK = 0
+BLTC_ERR_ARG = -1
+BLTC_ERR_OOM = -2
+BLTC_ERR_CUDA = -3
+BLTC_ERR_TIMEOUT = -4
+BLTC_ERR_STATE = -5
+BLTC_KERNEL_COULOMB = 0
+BLTC_KERNEL_YUKAWA = 1
+BLTC_PRECISION_FP64 = 0
+BLTC_PRECISION_MIXED = 1
+BLTC_MAX_DEGREE = 16
+
+_STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
+           -5: "ERR_STATE"}
+
+
+class BltcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class bltc_params(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("theta", ctypes.c_double), ("kappa", ctypes.c_double)]
+
+
+def params(degree=8, theta=0.7, leaf_size=2000, batch_size=None, kernel=BLTC_KERNEL_COULOMB,
+           kappa=0.0, precision=BLTC_PRECISION_MIXED) -> bltc_params:
+    """Treecode parameters (theta, n, N_L, N_B of Algorithm 1) plus kernel and precision."""
+    return bltc_params(int(degree), int(leaf_size),
+                       int(leaf_size if batch_size is None else batch_size), int(kernel),
+                       int(precision), 0, float(theta), float(kappa))
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                           ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_pp = ctypes.POINTER(ctypes.c_void_p)
+_P = ctypes.POINTER(bltc_params)
+
+_SIGNATURES = {
+    "bltc_version": ([], ctypes.c_int),
+    "bltc_context_create": ([ctypes.c_int, _vp, _pp], ctypes.c_int),
+    "bltc_context_destroy": ([_vp], None),
+    "bltc_context_set_stream": ([_vp, _vp], ctypes.c_int),
+    "bltc_context_set_allocator": ([_vp, ALLOC_FN, FREE_FN, _vp], ctypes.c_int),
+    "bltc_synchronize": ([_vp], ctypes.c_int),
+    "bltc_last_error": ([_vp], ctypes.c_char_p),
+    "bltc_device_sm_count": ([_vp], ctypes.c_int),
+    "bltc_context_launch_count": ([_vp], ctypes.c_int64),
+    "bltc_context_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
+    "bltc_last_timings": ([_vp, _vp], ctypes.c_int),
+    "bltc_tree_build": ([_vp, _vp, _vp, _vp, _vp, _i64, _i32, _pp], ctypes.c_int),
+    "bltc_tree_destroy": ([_vp], None),
+    "bltc_tree_info": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "bltc_tree_export": ([_vp] * 13, ctypes.c_int),
+    "bltc_lists_build": ([_vp, _vp, _vp, _P, _pp], ctypes.c_int),
+    "bltc_lists_destroy": ([_vp], None),
+    "bltc_lists_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "bltc_lists_export": ([_vp] * 6, ctypes.c_int),
+    "bltc_stats": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "bltc_modified_charges": ([_vp, _vp, _vp, _P], ctypes.c_int),
+    "bltc_modified_charges_export": ([_vp, _vp, _vp], ctypes.c_int),
+    "bltc_evaluate": ([_vp, _vp, _vp, _vp, _P, _vp], ctypes.c_int),
+    "bltc_solve": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
+    "bltc_solve_host": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
+    "bltc_direct_sum": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
+                        ctypes.c_int),
+}
+
+
+def library_built() -> bool:
+    return os.path.exists(LIB_PATH)
+
+
+def lib():
+    """The loaded libbltc.so.  Raises if it was not built: there is no fallback."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libbltc.so is not built ({LIB_PATH}); run "
+                                   "paper_2003_01836_gb300.build.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+        return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def _ptr(t):
+    """Device (or host) address of a contiguous float64 tensor/array, checked."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a contiguous float64 array")
+        return t.ctypes.data
+    if t.dtype.is_floating_point and t.dtype.itemsize != 8:
+        raise TypeError("expected float64 tensors")
+    if not t.is_contiguous():
+        raise TypeError("expected contiguous tensors")
+    return t.data_ptr()
+
+
+def _check(ctx, status):
+    if status != BLTC_OK:
+        msg = lib().bltc_last_error(ctx).decode() if ctx else ""
+        raise BltcError(status, msg)
+
+
+def _stream(ctx):
+    import torch
+    lib().bltc_context_set_stream(ctx, torch.cuda.current_stream().cuda_stream)
+
+
+# ---- torch's caching allocator as the library's device allocator ---------------------
+
+class _TorchAllocator:
+    def __init__(self, device):
+        import torch
+        self.device = device
+        self.torch = torch
+
+        def alloc(size, stream, user):
+            try:
+                return self.torch.cuda.caching_allocator_alloc(int(size), self.device,
+                                                               int(stream or 0))
+            except Exception:   # reported to the library as NULL -> BLTC_ERR_OOM
+                return None
+
+        def free(ptr, size, stream, user):
+            self.torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ALLOC_FN(alloc)
+        self.free = FREE_FN(free)
+
+
+# ---- the C ABI, same names -------------------------------------------------------------
+
+def bltc_version() -> int:
+    return lib().bltc_version()
+
+
+def bltc_context_create(device=0, stream=None):
+    h = ctypes.c_void_p()
+    st = lib().bltc_context_create(int(device), stream, ctypes.byref(h))
+    if st != BLTC_OK:
+        raise BltcError(st, "context creation failed")
+    return h.value
+
+
+def bltc_context_destroy(ctx):
+    lib().bltc_context_destroy(ctx)
+
+
+def bltc_context_set_stream(ctx, stream):
+    _check(ctx, lib().bltc_context_set_stream(ctx, stream))
+
+
+def bltc_context_set_allocator(ctx, alloc_fn, free_fn, user=None):
+    _check(ctx, lib().bltc_context_set_allocator(ctx, alloc_fn, free_fn, user))
+
+
+def bltc_synchronize(ctx):
+    _check(ctx, lib().bltc_synchronize(ctx))
+
+
+def bltc_last_error(ctx) -> str:
+    return lib().bltc_last_error(ctx).decode()
+
+
+def bltc_device_sm_count(ctx) -> int:
+    return lib().bltc_device_sm_count(ctx)
+
+
+def bltc_context_launch_count(ctx) -> int:
+    return lib().bltc_context_launch_count(ctx)
+
+
+def bltc_context_set_timing(ctx, enable=True):
+    _check(ctx, lib().bltc_context_set_timing(ctx, 1 if enable else 0))
+
+
+PHASES = ("trees", "lists", "modified_charges", "plan", "sweep", "finalize", "total")
+
+
+def bltc_last_timings(ctx):
+    ms = (ctypes.c_float * 7)()
+    _check(ctx, lib().bltc_last_timings(ctx, ctypes.addressof(ms)))
+    return {k: float(v) for k, v in zip(PHASES, ms)}
+
+
+def bltc_tree_build(ctx, x, y, z, q, max_leaf):
+    _stream(ctx)
+    h = ctypes.c_void_p()
+    _check(ctx, lib().bltc_tree_build(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.numel(),
+                                      int(max_leaf), ctypes.byref(h)))
+    return h.value
+
+
+def bltc_tree_destroy(tree):
+    lib().bltc_tree_destroy(tree)
+
+
+def bltc_tree_info(tree):
+    v = [ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()]
+    _check(None, lib().bltc_tree_info(tree, *[ctypes.byref(a) for a in v]))
+    return {"n_particles": v[0].value, "n_nodes": v[1].value, "n_leaves": v[2].value,
+            "n_levels": v[3].value}
+
+
+def bltc_tree_export(ctx, tree):
+    info = bltc_tree_info(tree)
+    n, m = info["n_particles"], info["n_nodes"]
+    out = {"perm": np.empty(n, np.int64), "begin": np.empty(m, np.int64),
+           "count": np.empty(m, np.int64), "parent": np.empty(m, np.int32),
+           "level": np.empty(m, np.int32), "n_children": np.empty(m, np.int32),
+           "children": np.empty((m, 8), np.int32), "lo": np.empty((m, 3)),
+           "hi": np.empty((m, 3)), "center": np.empty((m, 3)), "radius": np.empty(m)}
+    keys = ["perm", "begin", "count", "parent", "level", "n_children", "children", "lo", "hi",
+            "center", "radius"]
+    _check(ctx, lib().bltc_tree_export(ctx, tree, *[out[k].ctypes.data for k in keys]))
+    return out
+
+
+def bltc_lists_build(ctx, batches, sources, p: bltc_params):
+    _stream(ctx)
+    h = ctypes.c_void_p()
+    _check(ctx, lib().bltc_lists_build(ctx, batches, sources, ctypes.byref(p), ctypes.byref(h)))
+    return h.value
+
+
+def bltc_lists_destroy(lists):
+    lib().bltc_lists_destroy(lists)
+
+
+def bltc_lists_info(lists):
+    v = [ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()]
+    _check(None, lib().bltc_lists_info(lists, *[ctypes.byref(a) for a in v]))
+    return {"n_batches": v[0].value, "n_approx": v[1].value, "n_direct": v[2].value}
+
+
+def bltc_lists_export(ctx, lists):
+    info = bltc_lists_info(lists)
+    nb = info["n_batches"]
+    out = {"approx_off": np.empty(nb + 1, np.int64),
+           "approx_ids": np.empty(max(1, info["n_approx"]), np.int64),
+           "direct_off": np.empty(nb + 1, np.int64),
+           "direct_ids": np.empty(max(1, info["n_direct"]), np.int64)}
+    _check(ctx, lib().bltc_lists_export(ctx, lists, out["approx_off"].ctypes.data,
+                                        out["approx_ids"].ctypes.data,
+                                        out["direct_off"].ctypes.data,
+                                        out["direct_ids"].ctypes.data))
+    out["approx_ids"] = out["approx_ids"][:info["n_approx"]]
+    out["direct_ids"] = out["direct_ids"][:info["n_direct"]]
+    return out
+
+
+def bltc_stats(ctx, lists):
+    _stream(ctx)
+    d, a = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, lib().bltc_stats(ctx, lists, ctypes.byref(d), ctypes.byref(a)))
+    return {"direct": d.value, "approx": a.value}
+
+
+def bltc_modified_charges(ctx, sources, lists, p: bltc_params):
+    _stream(ctx)
+    _check(ctx, lib().bltc_modified_charges(ctx, sources, lists, ctypes.byref(p)))
+
+
+def bltc_modified_charges_export(ctx, sources, degree):
+    m = bltc_tree_info(sources)["n_nodes"]
+    P = (degree + 1) ** 3
+    out = np.empty(m * P)
+    _check(ctx, lib().bltc_modified_charges_export(ctx, sources, out.ctypes.data))
+    return out.reshape(m, P)
+
+
+def bltc_evaluate(ctx, lists, batches, sources, p: bltc_params, phi):
+    _stream(ctx)
+    _check(ctx, lib().bltc_evaluate(ctx, lists, batches, sources, ctypes.byref(p), _ptr(phi)))
+
+
+def bltc_solve(ctx, x, y, z, q, p: bltc_params, phi):
+    _stream(ctx)
+    _check(ctx, lib().bltc_solve(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.numel(),
+                                 ctypes.byref(p), _ptr(phi)))
+
+
+def bltc_solve_host(ctx, x, y, z, q, p: bltc_params, phi):
+    """Host buffers (numpy arrays or CPU tensors, pinned recommended)."""
+    _stream(ctx)
+    n = x.shape[0]
+    _check(ctx, lib().bltc_solve_host(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), n,
+                                      ctypes.byref(p), _ptr(phi)))
+
+
+def bltc_direct_sum(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):
+    _stream(ctx)
+    _check(ctx, lib().bltc_direct_sum(ctx, _ptr(tx), _ptr(ty), _ptr(tz), tx.numel(), _ptr(sx),
+                                      _ptr(sy), _ptr(sz), _ptr(sq), sx.numel(), ctypes.byref(p),
+                                      _ptr(phi)))
+
+
+# ---- convenience owner of a context ----------------------------------------------------
+
+class Context:
+    """Owns a bltc context on ``device``; by default the library allocates its working
+    memory through torch's caching allocator."""
+
+    def __init__(self, device=0, torch_allocator=True):
+        import torch
+        self.device = device
+        self.h = bltc_context_create(device, torch.cuda.current_stream(device).cuda_stream)
+        self._alloc = None
+        if torch_allocator:
+            self._alloc = _TorchAllocator(device)
+            bltc_context_set_allocator(self.h, self._alloc.alloc, self._alloc.free)
+
+    def close(self):
+        if self.h:
+            bltc_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def sm_count(self):
+        return bltc_device_sm_count(self.h)
+
+    def solve(self, x, y, z, q, p, phi=None):
+        import torch
+        if phi is None:
+            phi = torch.empty_like(x)
+        bltc_solve(self.h, x, y, z, q, p, phi)
+        return phi
+
+    def direct_sum(self, targets, sources, q, p, phi=None):
+        import torch
+        if phi is None:
+            phi = torch.empty_like(targets[0])
+        bltc_direct_sum(self.h, targets[0], targets[1], targets[2], sources[0], sources[1],
+                        sources[2], q, p, phi)
+        return phi

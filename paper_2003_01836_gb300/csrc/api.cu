@@ -1,0 +1,428 @@
+// api.cu -- the extern "C" boundary declared in include/bltc.h: argument checks, status
+// codes, the context (device, stream, allocator, Chebyshev tables) and the composition of
+// the steps into Algorithm 1 (bltc_solve).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "internal.cuh"
+
+struct bltc_context {
+    bltc::Context c;
+};
+struct bltc_tree {
+    bltc::Tree t;
+};
+struct bltc_lists {
+    bltc::Lists l;
+};
+
+namespace bltc {
+
+void* Context::dalloc(size_t bytes) {
+    void* p = nullptr;
+    if (alloc_fn) {
+        p = alloc_fn(bytes, stream, alloc_user);
+        if (!p) throw Error(BLTC_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+        return p;
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        throw Error(BLTC_ERR_OOM, "device pool out of memory for " + std::to_string(bytes) + " bytes");
+    }
+    if (e != cudaSuccess) throw Error(BLTC_ERR_CUDA, std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
+    return p;
+}
+
+void Context::dfree(void* p, size_t bytes) {
+    if (!p) return;
+    if (free_fn) {
+        free_fn(p, bytes, stream, alloc_user);
+        return;
+    }
+    cudaFreeAsync(p, stream);
+}
+
+const int64_t* Context::read_words(const void* dev, int words) {
+    if (words > kPinnedWords) throw Error(BLTC_ERR_ARG, "read_words: too many words");
+    BLTC_CUDA(cudaMemcpyAsync(pinned, dev, sizeof(int64_t) * words, cudaMemcpyDeviceToHost, stream));
+    BLTC_CUDA(cudaStreamSynchronize(stream));
+    return pinned;
+}
+
+// t_k = cos(pi k / n), k = 0..n (Eq. 6), generated on the host in FP64 and uploaded once.
+const double* Context::cheb_table(int degree) {
+    if (degree < 1 || degree > BLTC_MAX_DEGREE) throw Error(BLTC_ERR_ARG, "degree out of range");
+    if (!cheb_t[degree]) {
+        double h[BLTC_MAX_DEGREE + 1];
+        const double pi = 3.14159265358979323846;
+        for (int k = 0; k <= degree; ++k) h[k] = std::cos(pi * static_cast<double>(k) / static_cast<double>(degree));
+        double* d = nullptr;
+        BLTC_CUDA(cudaMalloc(&d, sizeof(double) * (degree + 1)));
+        BLTC_CUDA(cudaMemcpy(d, h, sizeof(double) * (degree + 1), cudaMemcpyHostToDevice));
+        cheb_t[degree] = d;
+    }
+    return cheb_t[degree];
+}
+
+static void check_params(const bltc_params* p) {
+    require(p != nullptr, "params is NULL");
+    require(p->degree >= 1 && p->degree <= BLTC_MAX_DEGREE, "degree must be in [1, 16]");
+    require(std::isfinite(p->theta) && p->theta >= 0.0 && p->theta < 1.0,
+            "theta must satisfy 0 <= theta < 1");
+    require(p->leaf_size >= 1 && p->batch_size >= 1, "leaf_size and batch_size must be >= 1");
+    require(p->kernel == BLTC_KERNEL_COULOMB || p->kernel == BLTC_KERNEL_YUKAWA, "unknown kernel");
+    require(p->kernel != BLTC_KERNEL_YUKAWA || (std::isfinite(p->kappa) && p->kappa >= 0.0),
+            "kappa must be finite and >= 0");
+    require(p->precision == BLTC_PRECISION_FP64 || p->precision == BLTC_PRECISION_MIXED,
+            "unknown precision");
+    require(p->reserved == 0, "params.reserved must be 0");
+}
+
+template <typename F>
+static bltc_status guarded(bltc_context* ctx, F&& f) {
+    try {
+        if (ctx) {
+            ctx->c.err.clear();
+            BLTC_CUDA(cudaSetDevice(ctx->c.device));
+        }
+        f();
+        return BLTC_OK;
+    } catch (const Error& e) {
+        if (ctx) ctx->c.err = e.what();
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        if (ctx) ctx->c.err = "host out of memory";
+        return BLTC_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (ctx) ctx->c.err = e.what();
+        return BLTC_ERR_CUDA;
+    }
+}
+
+static void solve_device(Context* c, const double* x, const double* y, const double* z,
+                         const double* q, int64_t n, const bltc_params& p, double* phi) {
+    c->mark(Context::kStart);
+    Tree st;
+    build_tree(c, x, y, z, q, n, p.leaf_size, &st);
+    std::unique_ptr<Tree> btp;
+    const Tree* bt = &st;
+    if (p.batch_size != p.leaf_size) {
+        btp.reset(new Tree());
+        build_tree(c, x, y, z, nullptr, n, p.batch_size, btp.get());
+        bt = btp.get();
+    }
+    c->mark(Context::kTrees);
+    Lists L;
+    build_lists(c, bt, &st, p.theta, p.degree, &L);
+    c->mark(Context::kLists);
+    compute_modified_charges(c, &st, &L, p.degree, p.precision);
+    c->mark(Context::kUpward);
+    evaluate(c, &L, bt, &st, p, phi);
+}
+
+}  // namespace bltc
+
+using namespace bltc;
+
+template <typename D, typename S>
+static void copy_out(Context* c, D* host, const S* dev, int64_t count) {
+    if (!host || count <= 0) return;
+    if (sizeof(D) == sizeof(S)) {
+        BLTC_CUDA(cudaMemcpyAsync(host, dev, sizeof(S) * count, cudaMemcpyDeviceToHost, c->stream));
+        BLTC_CUDA(cudaStreamSynchronize(c->stream));
+        return;
+    }
+    std::unique_ptr<S[]> tmp(new S[count]);
+    BLTC_CUDA(cudaMemcpyAsync(tmp.get(), dev, sizeof(S) * count, cudaMemcpyDeviceToHost, c->stream));
+    BLTC_CUDA(cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0; i < count; ++i) host[i] = static_cast<D>(tmp[i]);
+}
+
+extern "C" {
+
+int bltc_version(void) { return BLTC_VERSION; }
+
+bltc_status bltc_context_create(int device, void* stream, bltc_context** out) {
+    if (!out) return BLTC_ERR_ARG;
+    *out = nullptr;
+    std::unique_ptr<bltc_context> ctx(new (std::nothrow) bltc_context());
+    if (!ctx) return BLTC_ERR_OOM;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return BLTC_ERR_ARG;
+    }
+    Context& c = ctx->c;
+    c.device = device;
+    c.stream = static_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(device) != cudaSuccess) return BLTC_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return BLTC_ERR_CUDA;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c.pool, &props) != cudaSuccess) return BLTC_ERR_CUDA;
+    uint64_t keep = ~0ULL;   // keep freed memory in the pool for the next call
+    cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (cudaMallocHost(&c.pinned, sizeof(int64_t) * Context::kPinnedWords) != cudaSuccess) {
+        cudaMemPoolDestroy(c.pool);
+        return BLTC_ERR_CUDA;
+    }
+    *out = ctx.release();
+    return BLTC_OK;
+}
+
+void bltc_context_destroy(bltc_context* ctx) {
+    if (!ctx) return;
+    Context& c = ctx->c;
+    cudaSetDevice(c.device);
+    cudaStreamSynchronize(c.stream);
+    for (double*& t : c.cheb_t)
+        if (t) cudaFree(t);
+    for (cudaEvent_t& e : c.events)
+        if (e) cudaEventDestroy(e);
+    if (c.pinned) cudaFreeHost(c.pinned);
+    if (c.pool) cudaMemPoolDestroy(c.pool);
+    delete ctx;
+}
+
+bltc_status bltc_context_set_stream(bltc_context* ctx, void* stream) {
+    if (!ctx) return BLTC_ERR_ARG;
+    ctx->c.stream = static_cast<cudaStream_t>(stream);
+    return BLTC_OK;
+}
+
+bltc_status bltc_context_set_allocator(bltc_context* ctx, bltc_alloc_fn alloc, bltc_free_fn free_fn,
+                                       void* user) {
+    if (!ctx || (alloc == nullptr) != (free_fn == nullptr)) return BLTC_ERR_ARG;
+    ctx->c.alloc_fn = alloc;
+    ctx->c.free_fn = free_fn;
+    ctx->c.alloc_user = user;
+    return BLTC_OK;
+}
+
+bltc_status bltc_synchronize(bltc_context* ctx) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] { BLTC_CUDA(cudaStreamSynchronize(ctx->c.stream)); });
+}
+
+const char* bltc_last_error(const bltc_context* ctx) { return ctx ? ctx->c.err.c_str() : "no context"; }
+
+int bltc_device_sm_count(const bltc_context* ctx) { return ctx ? ctx->c.sm_count : 0; }
+
+int64_t bltc_context_launch_count(const bltc_context* ctx) { return ctx ? ctx->c.launches : -1; }
+
+bltc_status bltc_context_set_timing(bltc_context* ctx, int enable) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        Context& c = ctx->c;
+        if (enable && !c.events[0])
+            for (cudaEvent_t& e : c.events) BLTC_CUDA(cudaEventCreate(&e));
+        c.timing = enable != 0;
+        c.marked = 0;
+    });
+}
+
+bltc_status bltc_last_timings(bltc_context* ctx, float* ms) {
+    if (!ctx || !ms) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        Context& c = ctx->c;
+        const int pairs[7][2] = {{Context::kStart, Context::kTrees}, {Context::kTrees, Context::kLists},
+                                 {Context::kLists, Context::kUpward}, {Context::kUpward, Context::kSweepBegin},
+                                 {Context::kSweepBegin, Context::kSweepEnd}, {Context::kSweepEnd, Context::kEnd},
+                                 {Context::kStart, Context::kEnd}};
+        for (int i = 0; i < 7; ++i) {
+            ms[i] = -1.f;
+            const unsigned need = (1u << pairs[i][0]) | (1u << pairs[i][1]);
+            if ((c.marked & need) != need) continue;
+            BLTC_CUDA(cudaEventSynchronize(c.events[pairs[i][1]]));
+            BLTC_CUDA(cudaEventElapsedTime(&ms[i], c.events[pairs[i][0]], c.events[pairs[i][1]]));
+        }
+    });
+}
+
+bltc_status bltc_tree_build(bltc_context* ctx, const double* x, const double* y, const double* z,
+                            const double* q, int64_t n, int32_t max_leaf, bltc_tree** out) {
+    if (!ctx || !out) return BLTC_ERR_ARG;
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        std::unique_ptr<bltc_tree> t(new bltc_tree());
+        build_tree(&ctx->c, x, y, z, q, n, max_leaf, &t->t);
+        *out = t.release();
+    });
+}
+
+void bltc_tree_destroy(bltc_tree* tree) {
+    if (!tree) return;
+    if (tree->t.ctx) cudaSetDevice(tree->t.ctx->device);
+    delete tree;
+}
+
+bltc_status bltc_tree_info(const bltc_tree* tree, int64_t* n_particles, int64_t* n_nodes,
+                           int64_t* n_leaves, int32_t* n_levels) {
+    if (!tree) return BLTC_ERR_ARG;
+    if (n_particles) *n_particles = tree->t.n;
+    if (n_nodes) *n_nodes = tree->t.n_nodes;
+    if (n_leaves) *n_leaves = tree->t.n_leaves;
+    if (n_levels) *n_levels = tree->t.n_levels;
+    return BLTC_OK;
+}
+
+bltc_status bltc_tree_export(bltc_context* ctx, const bltc_tree* tree, int64_t* perm, int64_t* begin,
+                             int64_t* count, int32_t* parent, int32_t* level, int32_t* n_children,
+                             int32_t* children, double* lo, double* hi, double* center, double* radius) {
+    if (!ctx || !tree) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        const Tree& t = tree->t;
+        Context* c = &ctx->c;
+        const int64_t m = t.n_nodes;
+        copy_out(c, perm, t.perm.p, t.n);
+        copy_out(c, begin, t.begin.p, m);
+        copy_out(c, count, t.count.p, m);
+        copy_out(c, parent, t.parent.p, m);
+        copy_out(c, level, t.level.p, m);
+        copy_out(c, n_children, t.nch.p, m);
+        copy_out(c, children, t.child.p, 8 * m);
+        copy_out(c, lo, t.lo.p, 3 * m);
+        copy_out(c, hi, t.hi.p, 3 * m);
+        copy_out(c, center, t.center.p, 3 * m);
+        copy_out(c, radius, t.radius.p, m);
+    });
+}
+
+bltc_status bltc_lists_build(bltc_context* ctx, const bltc_tree* batches, const bltc_tree* sources,
+                             const bltc_params* params, bltc_lists** out) {
+    if (!ctx || !out || !batches || !sources) return BLTC_ERR_ARG;
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        require(params != nullptr, "params is NULL");
+        require(params->degree >= 1 && params->degree <= BLTC_MAX_DEGREE, "degree must be in [1, 16]");
+        require(std::isfinite(params->theta) && params->theta >= 0.0 && params->theta < 1.0,
+                "theta must satisfy 0 <= theta < 1");
+        std::unique_ptr<bltc_lists> l(new bltc_lists());
+        build_lists(&ctx->c, &batches->t, &sources->t, params->theta, params->degree, &l->l);
+        *out = l.release();
+    });
+}
+
+void bltc_lists_destroy(bltc_lists* lists) {
+    if (!lists) return;
+    if (lists->l.ctx) cudaSetDevice(lists->l.ctx->device);
+    delete lists;
+}
+
+bltc_status bltc_lists_info(const bltc_lists* lists, int64_t* n_batches, int64_t* n_approx,
+                            int64_t* n_direct) {
+    if (!lists) return BLTC_ERR_ARG;
+    if (n_batches) *n_batches = lists->l.n_batches;
+    if (n_approx) *n_approx = lists->l.n_app;
+    if (n_direct) *n_direct = lists->l.n_dir;
+    return BLTC_OK;
+}
+
+bltc_status bltc_lists_export(bltc_context* ctx, const bltc_lists* lists, int64_t* approx_off,
+                              int64_t* approx_ids, int64_t* direct_off, int64_t* direct_ids) {
+    if (!ctx || !lists) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        const Lists& L = lists->l;
+        Context* c = &ctx->c;
+        copy_out(c, approx_off, L.app_off.p, L.n_batches + 1);
+        copy_out(c, direct_off, L.dir_off.p, L.n_batches + 1);
+        copy_out(c, approx_ids, L.app_ids.p, L.n_app);
+        copy_out(c, direct_ids, L.dir_ids.p, L.n_dir);
+    });
+}
+
+bltc_status bltc_stats(bltc_context* ctx, const bltc_lists* lists, int64_t* n_direct_interactions,
+                       int64_t* n_approx_interactions) {
+    if (!ctx || !lists) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] { interaction_counts(&ctx->c, &lists->l, n_direct_interactions, n_approx_interactions); });
+}
+
+bltc_status bltc_modified_charges(bltc_context* ctx, bltc_tree* sources, const bltc_lists* lists,
+                                  const bltc_params* params) {
+    if (!ctx || !sources) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        require(params != nullptr, "params is NULL");
+        compute_modified_charges(&ctx->c, &sources->t, lists ? &lists->l : nullptr, params->degree,
+                                 params->precision);
+    });
+}
+
+bltc_status bltc_modified_charges_export(bltc_context* ctx, const bltc_tree* sources, double* qhat) {
+    if (!ctx || !sources || !qhat) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        const Tree& t = sources->t;
+        if (t.q_degree < 1) throw Error(BLTC_ERR_STATE, "no modified charges computed");
+        const int64_t np1 = t.q_degree + 1, P = np1 * np1 * np1;
+        std::unique_ptr<int32_t[]> slot(new int32_t[t.n_nodes]);
+        copy_out(&ctx->c, slot.get(), t.qslot.p, t.n_nodes);
+        std::unique_ptr<double[]> q(new double[t.q_slots * P + 1]);
+        copy_out(&ctx->c, q.get(), t.qhat64.p, t.q_slots * P);
+        for (int64_t v = 0; v < t.n_nodes; ++v)
+            for (int64_t k = 0; k < P; ++k)
+                qhat[v * P + k] = slot[v] >= 0 ? q[slot[v] * P + k] : std::nan("");
+    });
+}
+
+bltc_status bltc_evaluate(bltc_context* ctx, const bltc_lists* lists, const bltc_tree* batches,
+                          const bltc_tree* sources, const bltc_params* params, double* phi) {
+    if (!ctx || !lists || !batches || !sources) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        evaluate(&ctx->c, const_cast<Lists*>(&lists->l), &batches->t, &sources->t, *params, phi);
+    });
+}
+
+bltc_status bltc_solve(bltc_context* ctx, const double* x, const double* y, const double* z,
+                       const double* q, int64_t n, const bltc_params* params, double* phi) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(x && y && z && q && phi, "solve: NULL pointer");
+        solve_device(&ctx->c, x, y, z, q, n, *params, phi);
+    });
+}
+
+bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y, const double* z,
+                            const double* q, int64_t n, const bltc_params* params, double* phi) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(x && y && z && q && phi, "solve_host: NULL pointer");
+        require(n >= 1 && n < (int64_t(1) << 31), "solve_host: n must be in [1, 2^31)");
+        Context* c = &ctx->c;
+        DBuf<double> dx(c, n), dy(c, n), dz(c, n), dq(c, n), dphi(c, n);
+        const size_t bytes = sizeof(double) * n;
+        BLTC_CUDA(cudaMemcpyAsync(dx.p, x, bytes, cudaMemcpyHostToDevice, c->stream));
+        BLTC_CUDA(cudaMemcpyAsync(dy.p, y, bytes, cudaMemcpyHostToDevice, c->stream));
+        BLTC_CUDA(cudaMemcpyAsync(dz.p, z, bytes, cudaMemcpyHostToDevice, c->stream));
+        BLTC_CUDA(cudaMemcpyAsync(dq.p, q, bytes, cudaMemcpyHostToDevice, c->stream));
+        solve_device(c, dx.p, dy.p, dz.p, dq.p, n, *params, dphi.p);
+        BLTC_CUDA(cudaMemcpyAsync(phi, dphi.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+        BLTC_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+bltc_status bltc_direct_sum(bltc_context* ctx, const double* tx, const double* ty, const double* tz,
+                            int64_t nt, const double* sx, const double* sy, const double* sz,
+                            const double* sq, int64_t ns, const bltc_params* params, double* phi) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        require(params != nullptr, "params is NULL");
+        require(params->kernel == BLTC_KERNEL_COULOMB || params->kernel == BLTC_KERNEL_YUKAWA,
+                "unknown kernel");
+        require(params->kernel != BLTC_KERNEL_YUKAWA || (std::isfinite(params->kappa) && params->kappa >= 0.0),
+                "kappa must be finite and >= 0");
+        require(params->precision == BLTC_PRECISION_FP64 || params->precision == BLTC_PRECISION_MIXED,
+                "unknown precision");
+        direct_sum(&ctx->c, tx, ty, tz, nt, sx, sy, sz, sq, ns, *params, phi);
+    });
+}
+
+}  // extern "C"

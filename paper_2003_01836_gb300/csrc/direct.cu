@@ -1,0 +1,187 @@
+// direct.cu -- O(N^2) direct summation of Eq. 1 on the GPU (the baseline the treecode is
+// compared with; the paper computed it as one batch-cluster direct-sum launch over all
+// targets and all sources, Sec. IV "Single GPU vs. Single 6-Core CPU").
+//
+// Grid: (target tiles of 256*T targets) x (source splits).  Each block stages its sources
+// in shared-memory tiles and streams them against the targets held in registers, writing
+// one partial per (split, target) into a scratch buffer; a second kernel sums the splits
+// in order, so the result does not depend on scheduling.  MIXED evaluates in FP32 on the
+// coordinates rounded once from FP64, sums each staged tile in FP32 and tiles in FP64.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace bltc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTile32 = 2048;
+constexpr int kTile64 = 1024;
+
+struct DirectArgs {
+    const double *tx, *ty, *tz;
+    const double *sx, *sy, *sz, *sq;
+    int64_t nt, ns, per_split;
+    double* partial;            // [splits * nt]
+    double kappa;
+    float neg_kappa_log2e;
+};
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int KER, int T>
+__global__ void __launch_bounds__(kThreads, 2) k_direct_mixed(DirectArgs a) {
+    __shared__ __align__(16) float4 sm[kTile32];
+    const int64_t t0 = static_cast<int64_t>(blockIdx.x) * kThreads * T;
+    const int64_t s0 = static_cast<int64_t>(blockIdx.y) * a.per_split;
+    const int64_t s1 = std::min<int64_t>(a.ns, s0 + a.per_split);
+    float xt[T], yt[T], zt[T];
+    double acc[T];
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+        const int64_t t = std::min<int64_t>(t0 + threadIdx.x + kThreads * u, a.nt - 1);
+        xt[u] = __double2float_rn(a.tx[t]);
+        yt[u] = __double2float_rn(a.ty[t]);
+        zt[u] = __double2float_rn(a.tz[t]);
+        acc[u] = 0.0;
+    }
+    for (int64_t j0 = s0; j0 < s1; j0 += kTile32) {
+        const int m = static_cast<int>(std::min<int64_t>(kTile32, s1 - j0));
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kThreads)
+            sm[j] = make_float4(__double2float_rn(a.sx[j0 + j]), __double2float_rn(a.sy[j0 + j]),
+                                __double2float_rn(a.sz[j0 + j]), __double2float_rn(a.sq[j0 + j]));
+        __syncthreads();
+        float f[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) f[u] = 0.f;
+#pragma unroll 2
+        for (int j = 0; j < m; ++j) {
+            const float4 s = sm[j];
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+                const float dx = s.x - xt[u], dy = s.y - yt[u], dz = s.z - zt[u];
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float ri = rsqrt_approx(r2);
+                ri = r2 > 0.f ? ri : 0.f;
+                if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
+                f[u] = fmaf(s.w, ri, f[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(f[u]);
+    }
+    double* out = a.partial + static_cast<int64_t>(blockIdx.y) * a.nt;
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+        const int64_t t = t0 + threadIdx.x + kThreads * u;
+        if (t < a.nt) out[t] = acc[u];
+    }
+}
+
+template <int KER, int T>
+__global__ void __launch_bounds__(kThreads, 2) k_direct_fp64(DirectArgs a) {
+    __shared__ __align__(16) D4 sm[kTile64];
+    const int64_t t0 = static_cast<int64_t>(blockIdx.x) * kThreads * T;
+    const int64_t s0 = static_cast<int64_t>(blockIdx.y) * a.per_split;
+    const int64_t s1 = std::min<int64_t>(a.ns, s0 + a.per_split);
+    double xt[T], yt[T], zt[T], acc[T];
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+        const int64_t t = std::min<int64_t>(t0 + threadIdx.x + kThreads * u, a.nt - 1);
+        xt[u] = a.tx[t];
+        yt[u] = a.ty[t];
+        zt[u] = a.tz[t];
+        acc[u] = 0.0;
+    }
+    for (int64_t j0 = s0; j0 < s1; j0 += kTile64) {
+        const int m = static_cast<int>(std::min<int64_t>(kTile64, s1 - j0));
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kThreads)
+            sm[j] = D4{a.sx[j0 + j], a.sy[j0 + j], a.sz[j0 + j], a.sq[j0 + j]};
+        __syncthreads();
+        for (int j = 0; j < m; ++j) {
+            const D4 s = sm[j];
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+                const double dx = xt[u] - s.x, dy = yt[u] - s.y, dz = zt[u] - s.z;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 != 0.0) {
+                    const double ri = rsqrt(r2);
+                    acc[u] += KER == BLTC_KERNEL_YUKAWA ? s.w * ri * exp(-a.kappa * (r2 * ri))
+                                                        : s.w * ri;
+                }
+            }
+        }
+    }
+    double* out = a.partial + static_cast<int64_t>(blockIdx.y) * a.nt;
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+        const int64_t t = t0 + threadIdx.x + kThreads * u;
+        if (t < a.nt) out[t] = acc[u];
+    }
+}
+
+__global__ void k_direct_reduce(const double* __restrict__ partial, int64_t nt, int splits,
+                                double* __restrict__ phi) {
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < nt;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < splits; ++k) s += partial[static_cast<int64_t>(k) * nt + t];
+        phi[t] = s;
+    }
+}
+
+}  // namespace
+
+void direct_sum(Context* ctx, const double* tx, const double* ty, const double* tz, int64_t nt,
+                const double* sx, const double* sy, const double* sz, const double* sq,
+                int64_t ns, const bltc_params& p, double* phi) {
+    require(nt >= 1 && ns >= 1, "direct: nt and ns must be >= 1");
+    require(tx && ty && tz && sx && sy && sz && sq && phi, "direct: NULL pointer");
+    cudaStream_t s = ctx->stream;
+    const bool mixed = p.precision == BLTC_PRECISION_MIXED;
+    const int T = mixed ? 8 : 4;
+    const int64_t tiles = ceil_div(nt, static_cast<int64_t>(kThreads) * T);
+    const int64_t want = 4 * static_cast<int64_t>(std::max(1, ctx->sm_count));
+    const int64_t tile_src = mixed ? kTile32 : kTile64;
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, tiles), ceil_div(ns, tile_src)));
+    splits = std::min<int64_t>(splits, 65535);
+    const int64_t per = ceil_div(ceil_div(ns, splits), tile_src) * tile_src;
+    splits = ceil_div(ns, per);
+    DBuf<double> partial(ctx, splits * nt);
+    DirectArgs a{tx, ty, tz, sx, sy, sz, sq, nt, ns, per, partial.p, 0.0, 0.f};
+    const double kappa = p.kernel == BLTC_KERNEL_YUKAWA ? p.kappa : 0.0;
+    a.kappa = kappa;
+    a.neg_kappa_log2e = static_cast<float>(-kappa * 1.4426950408889634);
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(splits));
+    if (mixed) {
+        if (p.kernel == BLTC_KERNEL_YUKAWA) {
+            k_direct_mixed<BLTC_KERNEL_YUKAWA, 8><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+        }
+        else {
+            k_direct_mixed<BLTC_KERNEL_COULOMB, 8><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+        }
+    } else {
+        if (p.kernel == BLTC_KERNEL_YUKAWA) {
+            k_direct_fp64<BLTC_KERNEL_YUKAWA, 4><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+        }
+        else {
+            k_direct_fp64<BLTC_KERNEL_COULOMB, 4><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+        }
+    }
+    BLTC_LAUNCH_CHECK("direct");
+    k_direct_reduce<<<grid_for(nt, 256, 4096), 256, 0, s>>>(partial.p, nt, static_cast<int>(splits), phi); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("direct reduce");
+}
+
+}  // namespace bltc

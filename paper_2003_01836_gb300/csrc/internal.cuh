@@ -1,0 +1,195 @@
+// internal.cuh -- data structures and helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "bltc.h"
+
+namespace bltc {
+
+// Failure inside the library; converted to a bltc_status at the C boundary.
+struct Error : std::runtime_error {
+    bltc_status status;
+    Error(bltc_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define BLTC_CUDA(call)                                                                   \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            throw ::bltc::Error(BLTC_ERR_CUDA, std::string(#call) + ": " +                \
+                                                   cudaGetErrorString(e_));               \
+    } while (0)
+
+#define BLTC_LAUNCH_CHECK(what)                                                           \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess)                                                            \
+            throw ::bltc::Error(BLTC_ERR_CUDA, std::string("launch ") + (what) + ": " +   \
+                                                   cudaGetErrorString(e_));               \
+    } while (0)
+
+inline void require(bool ok, const std::string& msg) {
+    if (!ok) throw Error(BLTC_ERR_ARG, msg);
+}
+
+struct Context {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;
+    bltc_alloc_fn alloc_fn = nullptr;
+    bltc_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    std::string err;
+    double* cheb_t[BLTC_MAX_DEGREE + 1] = {};   // device: t_k = cos(pi k / n), k = 0..n
+    int64_t* pinned = nullptr;                  // small pinned host buffer for counters
+    static constexpr int kPinnedWords = 64;
+    int64_t launches = 0;                       // kernels launched through this context
+    uint64_t next_serial = 1;
+    // Optional phase timing: CUDA events recorded on the stream at the phase boundaries.
+    enum Mark { kStart, kTrees, kLists, kUpward, kSweepBegin, kSweepEnd, kEnd, kMarks };
+    bool timing = false;
+    cudaEvent_t events[kMarks] = {};
+    unsigned marked = 0;
+    void mark(Mark m) {
+        if (!timing) return;
+        if (m == kStart) marked = 0;
+        if (m == kSweepBegin) marked &= ~((1u << kSweepBegin) | (1u << kSweepEnd) | (1u << kEnd));
+        if (cudaEventRecord(events[m], stream) == cudaSuccess) marked |= 1u << m;
+    }
+
+    void* dalloc(size_t bytes);
+    void dfree(void* p, size_t bytes);
+    // Every allocation is rounded up to 16 bytes so small counters can be read as words.
+    template <typename T>
+    static size_t bytes_for(int64_t count) {
+        size_t b = sizeof(T) * static_cast<size_t>(count > 0 ? count : 1);
+        return (b + 15) & ~static_cast<size_t>(15);
+    }
+    template <typename T>
+    T* alloc(int64_t count) {
+        return static_cast<T*>(dalloc(bytes_for<T>(count)));
+    }
+    // Copies `words` int64 values from device to the pinned buffer and waits.
+    const int64_t* read_words(const void* dev, int words);
+    const double* cheb_table(int degree);
+};
+
+// RAII device buffer from the context allocator.
+template <typename T>
+struct DBuf {
+    Context* ctx = nullptr;
+    T* p = nullptr;
+    int64_t n = 0;
+    DBuf() = default;
+    DBuf(Context* c, int64_t count) : ctx(c), p(c->alloc<T>(count)), n(count) {}
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : ctx(o.ctx), p(o.p), n(o.n) { o.p = nullptr; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            reset();
+            ctx = o.ctx;
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+        }
+        return *this;
+    }
+    ~DBuf() { reset(); }
+    void reset() {
+        if (p && ctx) ctx->dfree(p, Context::bytes_for<T>(n));
+        p = nullptr;
+    }
+    T* release() {
+        T* q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+// A built tree (nodes in DFS pre-order; particles in tree order).
+struct Tree {
+    Context* ctx = nullptr;
+    int64_t n = 0;
+    int32_t max_leaf = 0;
+    int64_t n_nodes = 0, n_leaves = 0;
+    int32_t n_levels = 0;
+    bool has_q = false;
+    DBuf<double> px, py, pz, pq;      // particles in tree order
+    DBuf<int32_t> perm;               // perm[i] = original index
+    DBuf<int32_t> begin, count, parent, level, nch, child;  // child: 8 per node
+    DBuf<double> lo, hi, center, radius;                    // lo/hi/center: 3 per node
+    DBuf<int32_t> leaves;             // leaf node ids in DFS order
+    // modified charges for one (degree, precision)
+    int q_degree = -1, q_precision = -1;
+    uint64_t q_lists = 0;             // serial of the lists the charges were computed for (0: all)
+    int64_t q_slots = 0;
+    DBuf<int32_t> qslot;              // per node: row of qhat, or -1
+    DBuf<double> qhat64;              // [q_slots * P]
+    DBuf<float> qhat32;               // [q_slots * P] (mixed precision)
+};
+
+// Per-batch work items of one evaluation (cached in the lists).
+struct Plan {
+    bool valid = false;
+    int degree = -1;
+    int64_t n_items = 0;
+    int64_t partial_len = 0;
+    DBuf<int4> items;                 // {batch, e0, e1, chunk}
+    DBuf<int64_t> part_off;           // per batch: first partial
+    DBuf<int32_t> n_chunks;           // per batch
+};
+
+struct Lists {
+    Context* ctx = nullptr;
+    uint64_t serial = 0;              // unique per context, never 0
+    const Tree* bt = nullptr;
+    const Tree* st = nullptr;
+    double theta = 0.0;
+    int degree = 0;
+    int64_t n_batches = 0, n_app = 0, n_dir = 0;
+    DBuf<int32_t> app_off, app_ids, dir_off, dir_ids;
+    Plan plan;
+};
+
+// ---- steps (implemented in tree.cu, lists.cu, upward.cu, sweep.cu, direct.cu) -------
+void build_tree(Context* ctx, const double* x, const double* y, const double* z,
+                const double* q, int64_t n, int32_t max_leaf, Tree* out);
+void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int degree,
+                 Lists* out);
+void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int degree,
+                              int precision);
+void evaluate(Context* ctx, Lists* lists, const Tree* bt, const Tree* st,
+              const bltc_params& p, double* phi);
+void interaction_counts(Context* ctx, const Lists* lists, int64_t* n_dir, int64_t* n_app);
+void direct_sum(Context* ctx, const double* tx, const double* ty, const double* tz,
+                int64_t nt, const double* sx, const double* sy, const double* sz,
+                const double* sq, int64_t ns, const bltc_params& p, double* phi);
+
+// ---- device-wide exclusive scan (scan.cu) -------------------------------------------
+// out[i] = sum_{j<i} in[i]; *total (device, may be null) = sum of all.
+void exclusive_scan_i32(Context* ctx, const int32_t* in, int32_t* out, int64_t n,
+                        int32_t* total);
+void exclusive_scan_i64(Context* ctx, const int64_t* in, int64_t* out, int64_t n,
+                        int64_t* total);
+
+// 32-byte aligned (x, y, z, q) record for FP64 shared-memory staging.
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20) {
+    int64_t g = ceil_div(n, threads);
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return static_cast<unsigned>(g);
+}
+
+}  // namespace bltc

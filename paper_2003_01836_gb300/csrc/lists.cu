@@ -1,0 +1,156 @@
+// lists.cu -- A1: interaction lists of every target batch (Algorithm 1, Eq. 13).
+//
+// For each batch B (leaf of the batch tree, DFS order) one thread walks ComputePotential
+// from the root of the source tree with an explicit stack, children pushed in reverse so
+// that they are visited in stored order, exactly like the recursion:
+//   MAC passes ((r_B + r_C)/R < theta and (n+1)^3 < N_C)        -> approximation list
+//   geometric test fails ((r_B + r_C)/R not < theta): leaf       -> direct list
+//                                                     otherwise  -> the children
+//   geometric test passes but (n+1)^3 >= N_C                      -> direct list (whole C)
+// A first pass counts, a scan makes CSR offsets, a second pass fills the ids.  The MAC is
+// FP64 with IEEE-rounded intrinsics (no fused multiply-add; also --fmad=false), so the
+// lists are bit-identical to any other implementation of the same arithmetic.
+#include "internal.cuh"
+
+namespace bltc {
+namespace {
+
+constexpr int kThreads = 128;
+
+struct ListArgs {
+    const int32_t* b_leaves;
+    const double* b_center;
+    const double* b_radius;
+    const int32_t* s_count;
+    const int32_t* s_nch;
+    const int32_t* s_child;
+    const double* s_center;
+    const double* s_radius;
+    int64_t n_batches;
+    double theta;
+    int64_t P;
+    int32_t* stack;          // n_batches * stack_cap
+    int32_t stack_cap;
+    int32_t* app_cnt;        // pass 0
+    int32_t* dir_cnt;
+    const int32_t* app_off;  // pass 1
+    const int32_t* dir_off;
+    int32_t* app_ids;
+    int32_t* dir_ids;
+    int32_t* overflow;
+};
+
+template <bool kFill>
+__global__ void k_lists(ListArgs a) {
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= a.n_batches) return;
+    const int32_t B = a.b_leaves[b];
+    const double cbx = a.b_center[3 * B], cby = a.b_center[3 * B + 1], cbz = a.b_center[3 * B + 2];
+    const double rB = a.b_radius[B];
+    int32_t* st = a.stack + b * a.stack_cap;
+    int sp = 0;
+    st[sp++] = 0;
+    int32_t na = 0, nd = 0;
+    int32_t* app = kFill ? a.app_ids + a.app_off[b] : nullptr;
+    int32_t* dir = kFill ? a.dir_ids + a.dir_off[b] : nullptr;
+    while (sp > 0) {
+        const int32_t C = st[--sp];
+        const double dx = __dsub_rn(cbx, a.s_center[3 * C]);
+        const double dy = __dsub_rn(cby, a.s_center[3 * C + 1]);
+        const double dz = __dsub_rn(cbz, a.s_center[3 * C + 2]);
+        const double R = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                              __dmul_rn(dz, dz)));
+        const double ratio = __ddiv_rn(__dadd_rn(rB, a.s_radius[C]), R);
+        const bool geometric_ok = ratio < a.theta;
+        const bool size_ok = a.P < static_cast<int64_t>(a.s_count[C]);
+        if (geometric_ok && size_ok) {
+            if (kFill) app[na] = C;
+            ++na;
+        } else if (!geometric_ok) {
+            const int k = a.s_nch[C];
+            if (k == 0) {
+                if (kFill) dir[nd] = C;
+                ++nd;
+            } else {
+                if (sp + k > a.stack_cap) {
+                    atomicExch(a.overflow, 1);
+                    break;
+                }
+                for (int c = k - 1; c >= 0; --c) st[sp++] = a.s_child[8 * C + c];
+            }
+        } else {
+            if (kFill) dir[nd] = C;
+            ++nd;
+        }
+    }
+    if (!kFill) {
+        a.app_cnt[b] = na;
+        a.dir_cnt[b] = nd;
+    }
+}
+
+__global__ void k_append_total(int32_t* off, int64_t n, const int32_t* total) {
+    off[n] = *total;
+}
+
+}  // namespace
+
+void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int degree,
+                 Lists* out) {
+    require(degree >= 1 && degree <= BLTC_MAX_DEGREE, "lists: degree out of range");
+    require(theta >= 0.0 && theta < 1.0, "lists: theta must satisfy 0 <= theta < 1");
+    cudaStream_t s = ctx->stream;
+    const int64_t nb = bt->n_leaves;
+    const int64_t n1 = degree + 1;
+    out->ctx = ctx;
+    out->serial = ctx->next_serial++;
+    out->bt = bt;
+    out->st = st;
+    out->theta = theta;
+    out->degree = degree;
+    out->n_batches = nb;
+
+    ListArgs a{};
+    a.b_leaves = bt->leaves.p;
+    a.b_center = bt->center.p;
+    a.b_radius = bt->radius.p;
+    a.s_count = st->count.p;
+    a.s_nch = st->nch.p;
+    a.s_child = st->child.p;
+    a.s_center = st->center.p;
+    a.s_radius = st->radius.p;
+    a.n_batches = nb;
+    a.theta = theta;
+    a.P = n1 * n1 * n1;
+    a.stack_cap = 7 * st->n_levels + 8;
+    DBuf<int32_t> stack(ctx, nb * a.stack_cap);
+    DBuf<int32_t> cnt(ctx, 2 * nb), flags(ctx, 4);
+    out->app_off = DBuf<int32_t>(ctx, nb + 1);
+    out->dir_off = DBuf<int32_t>(ctx, nb + 1);
+    a.stack = stack.p;
+    a.app_cnt = cnt.p;
+    a.dir_cnt = cnt.p + nb;
+    a.overflow = flags.p + 2;
+    BLTC_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int32_t), s));
+    k_lists<false><<<grid_for(nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("lists count");
+    exclusive_scan_i32(ctx, a.app_cnt, out->app_off.p, nb, flags.p);
+    exclusive_scan_i32(ctx, a.dir_cnt, out->dir_off.p, nb, flags.p + 1);
+    k_append_total<<<1, 1, 0, s>>>(out->app_off.p, nb, flags.p); ++ctx->launches;
+    k_append_total<<<1, 1, 0, s>>>(out->dir_off.p, nb, flags.p + 1); ++ctx->launches;
+    const int32_t* w = reinterpret_cast<const int32_t*>(ctx->read_words(flags.p, 2));
+    const int32_t n_app = w[0], n_dir = w[1], overflow = w[2];
+    if (overflow) throw Error(BLTC_ERR_CUDA, "lists: traversal stack overflow");
+    out->n_app = n_app;
+    out->n_dir = n_dir;
+    out->app_ids = DBuf<int32_t>(ctx, n_app);
+    out->dir_ids = DBuf<int32_t>(ctx, n_dir);
+    a.app_off = out->app_off.p;
+    a.dir_off = out->dir_off.p;
+    a.app_ids = out->app_ids.p;
+    a.dir_ids = out->dir_ids.p;
+    k_lists<true><<<grid_for(nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("lists fill");
+}
+
+}  // namespace bltc

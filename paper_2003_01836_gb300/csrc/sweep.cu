@@ -1,0 +1,595 @@
+// sweep.cu -- A3/A4/A5: far-field and near-field batch-cluster sums and the finalize.
+//
+// Far field (Eq. 11): phi_i += sum_k G(x_i, s_k) qhat_k over the (n+1)^3 Chebyshev points
+// s_k = (s1[k1], s2[k2], s3[k3]) of each approximated cluster.  Near field (Eq. 9):
+// phi_i += sum_{y_j in C} G(x_i, y_j) q_j over each directly summed cluster.
+//
+// GB300 mapping.  The target batch is the unit of work, as in the paper (the MAC is applied
+// per batch so all its targets share one list, Sec. III-B "Target Batching").  Each
+// batch's combined list (approximated clusters, then direct clusters) is cut into items of
+// roughly equal interaction count; one persistent launch of (SMs x 2) blocks pulls items
+// from an atomic counter.  A block holds up to 256*T targets in registers (T per thread),
+// stages one cluster at a time in shared memory (sources as float4 (x, y, z, q) relative
+// to the batch centre, or the proxy grid: 3 x (n+1) point coordinates and (n+1)^3
+// modified charges), and every thread streams the staged sources against its T targets.
+// The proxy grid is used in tensor form: for each (k1, k2) the partial r^2 of a target is
+// reused across the n+1 values of k3 (Eq. 8's tensor product).  Each item writes one
+// partial potential per target; the finalize sums a target's partials in item order (FP64)
+// and scatters to the caller's order, so results are deterministic (the paper used atomics
+// across four streams instead, Sec. III-B "Asynchronous Streams").
+//
+// Precision.  MIXED: kernel evaluations in FP32 on coordinates taken relative to the batch
+// centre (the FP64 differences rounded once), FP32 sums over one staged tile, FP64 across
+// tiles and clusters.  FP64: every operation in double on absolute coordinates.
+// A pair with r^2 == 0 (a target meeting itself) is skipped; for the far field theta < 1
+// keeps every proxy point away from every target, so no test is needed there.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace bltc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSrcTile32 = 2048;      // float4 sources per staged tile (32 KB)
+constexpr int kSrcTile64 = 1280;      // D4 sources per staged tile (40 KB)
+constexpr int kSmemBytes = 40960;     // also holds 3(n+1) + (n+1)^3 doubles for n <= 16
+constexpr int kItemsPerBlock = 12;    // work items per resident block (load balance)
+
+struct SweepArgs {
+    // target batches
+    const int32_t* b_leaves;
+    const int32_t* b_begin;
+    const int32_t* b_count;
+    const double* b_center;
+    const double *tx, *ty, *tz;
+    // source clusters
+    const int32_t* s_begin;
+    const int32_t* s_count;
+    const double* s_lo;
+    const double* s_hi;
+    const double *sx, *sy, *sz, *sq;
+    const int32_t* qslot;
+    const double* qhat64;
+    const float* qhat32;
+    const double* cheb_t;
+    int np1;
+    // lists and items
+    const int32_t* app_off;
+    const int32_t* app_ids;
+    const int32_t* dir_off;
+    const int32_t* dir_ids;
+    const int4* items;
+    const int64_t* part_off;
+    double* partials;
+    int n_items;
+    unsigned int* counter;
+    // kernel
+    double kappa;
+    float neg_kappa_log2e;
+};
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ double cheb_point(const double* t, int k, int n, double lo, double hi) {
+    if (k == 0) return hi;
+    if (k == n) return lo;
+    return __dadd_rn(lo, __dmul_rn(__dmul_rn(0.5, __dadd_rn(t[k], 1.0)), __dsub_rn(hi, lo)));
+}
+
+// ---- mixed precision ------------------------------------------------------------------
+
+template <int KER>
+__device__ __forceinline__ float g_mixed(float r2, float q, float nkl2e) {
+    float ri = rsqrt_approx(r2);
+    if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(nkl2e * (r2 * ri));
+    return q * ri;
+}
+
+template <int KER, int T>
+__device__ void near_mixed(const SweepArgs& a, int C, const double cb[3], const float (&xt)[T],
+                           const float (&yt)[T], const float (&zt)[T], double (&acc)[T],
+                           float4* sm) {
+    const int cs = a.s_begin[C], nc = a.s_count[C];
+    for (int j0 = 0; j0 < nc; j0 += kSrcTile32) {
+        const int m = min(kSrcTile32, nc - j0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kThreads) {
+            const int p = cs + j0 + j;
+            sm[j] = make_float4(__double2float_rn(a.sx[p] - cb[0]), __double2float_rn(a.sy[p] - cb[1]),
+                                __double2float_rn(a.sz[p] - cb[2]), __double2float_rn(a.sq[p]));
+        }
+        __syncthreads();
+        float f[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) f[u] = 0.f;
+#pragma unroll 2
+        for (int j = 0; j < m; ++j) {
+            const float4 s = sm[j];
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+                const float dx = s.x - xt[u], dy = s.y - yt[u], dz = s.z - zt[u];
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float ri = rsqrt_approx(r2);
+                ri = r2 > 0.f ? ri : 0.f;
+                if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
+                f[u] = fmaf(s.w, ri, f[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(f[u]);
+    }
+}
+
+template <int KER, int T>
+__device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const float (&xt)[T],
+                          const float (&yt)[T], const float (&zt)[T], double (&acc)[T],
+                          float* sm) {
+    const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1;
+    const float* qh = a.qhat32 + static_cast<int64_t>(a.qslot[C]) * P;
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * np1; k += kThreads) {
+        const int d = k / np1, kk = k - d * np1;
+        const double s = cheb_point(a.cheb_t, kk, n, a.s_lo[3 * C + d], a.s_hi[3 * C + d]);
+        sm[k] = __double2float_rn(s - cb[d]);
+    }
+    float* sq = sm + 3 * np1;
+    for (int k = threadIdx.x; k < P; k += kThreads) sq[k] = qh[k];
+    __syncthreads();
+    float f[T];
+#pragma unroll
+    for (int u = 0; u < T; ++u) f[u] = 0.f;
+    for (int k1 = 0; k1 < np1; ++k1) {
+        float dx2[T];
+        const float sxk = sm[k1];
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const float dx = sxk - xt[u];
+            dx2[u] = dx * dx;
+        }
+        for (int k2 = 0; k2 < np1; ++k2) {
+            float t[T];
+            const float syk = sm[np1 + k2];
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+                const float dy = syk - yt[u];
+                t[u] = fmaf(dy, dy, dx2[u]);
+            }
+            const float* qrow = sq + (k1 * np1 + k2) * np1;
+            const float* sz = sm + 2 * np1;
+#pragma unroll 3
+            for (int k3 = 0; k3 < np1; ++k3) {
+                const float q = qrow[k3], szk = sz[k3];
+#pragma unroll
+                for (int u = 0; u < T; ++u) {
+                    const float dz = szk - zt[u];
+                    const float r2 = fmaf(dz, dz, t[u]);
+                    f[u] += g_mixed<KER>(r2, q, a.neg_kappa_log2e);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(f[u]);
+}
+
+template <int KER, int T>
+__device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
+    const int b = it.x;
+    const int B = a.b_leaves[b];
+    const int tb = a.b_begin[B], nb = a.b_count[B];
+    const double cb[3] = {a.b_center[3 * B], a.b_center[3 * B + 1], a.b_center[3 * B + 2]};
+    const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
+    double* out = a.partials + a.part_off[b] + static_cast<int64_t>(it.w) * nb;
+    for (int t0 = 0; t0 < nb; t0 += kThreads * T) {
+        float xt[T], yt[T], zt[T];
+        double acc[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const int t = min(t0 + static_cast<int>(threadIdx.x) + kThreads * u, nb - 1);
+            xt[u] = __double2float_rn(a.tx[tb + t] - cb[0]);
+            yt[u] = __double2float_rn(a.ty[tb + t] - cb[1]);
+            zt[u] = __double2float_rn(a.tz[tb + t] - cb[2]);
+            acc[u] = 0.0;
+        }
+        for (int e = it.y; e < it.z; ++e) {
+            if (e < na)
+                far_mixed<KER, T>(a, a.app_ids[a0 + e], cb, xt, yt, zt, acc,
+                                  reinterpret_cast<float*>(sm));
+            else
+                near_mixed<KER, T>(a, a.dir_ids[d0 + e - na], cb, xt, yt, zt, acc, sm);
+        }
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const int t = t0 + static_cast<int>(threadIdx.x) + kThreads * u;
+            if (t < nb) out[t] = acc[u];
+        }
+    }
+}
+
+template <int KER>
+__global__ void __launch_bounds__(kThreads, 2) k_sweep_mixed(SweepArgs a) {
+    __shared__ __align__(16) float4 sm[kSmemBytes / sizeof(float4)];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(a.counter, 1u));
+        __syncthreads();
+        const int i = s_item;
+        if (i >= a.n_items) return;
+        const int4 it = a.items[i];
+        const int nb = a.b_count[a.b_leaves[it.x]];
+        if (nb <= kThreads)
+            item_mixed<KER, 1>(a, it, sm);
+        else if (nb <= 2 * kThreads)
+            item_mixed<KER, 2>(a, it, sm);
+        else if (nb <= 4 * kThreads)
+            item_mixed<KER, 4>(a, it, sm);
+        else
+            item_mixed<KER, 8>(a, it, sm);
+    }
+}
+
+// ---- FP64 ---------------------------------------------------------------------------
+
+template <int KER>
+__device__ __forceinline__ double g_fp64(double r2, double q, double kappa) {
+    const double ri = rsqrt(r2);
+    if (KER == BLTC_KERNEL_YUKAWA) return q * ri * exp(-kappa * (r2 * ri));
+    return q * ri;
+}
+
+template <int KER, int T>
+__device__ void near_fp64(const SweepArgs& a, int C, const double (&xt)[T], const double (&yt)[T],
+                          const double (&zt)[T], double (&acc)[T], D4* sm) {
+    const int cs = a.s_begin[C], nc = a.s_count[C];
+    for (int j0 = 0; j0 < nc; j0 += kSrcTile64) {
+        const int m = min(kSrcTile64, nc - j0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kThreads) {
+            const int p = cs + j0 + j;
+            sm[j] = D4{a.sx[p], a.sy[p], a.sz[p], a.sq[p]};
+        }
+        __syncthreads();
+        for (int j = 0; j < m; ++j) {
+            const D4 s = sm[j];
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+                const double dx = xt[u] - s.x, dy = yt[u] - s.y, dz = zt[u] - s.z;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 != 0.0) acc[u] += g_fp64<KER>(r2, s.w, a.kappa);
+            }
+        }
+    }
+}
+
+template <int KER, int T>
+__device__ void far_fp64(const SweepArgs& a, int C, const double (&xt)[T], const double (&yt)[T],
+                         const double (&zt)[T], double (&acc)[T], double* sm) {
+    const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1;
+    const double* qh = a.qhat64 + static_cast<int64_t>(a.qslot[C]) * P;
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * np1; k += kThreads) {
+        const int d = k / np1, kk = k - d * np1;
+        sm[k] = cheb_point(a.cheb_t, kk, n, a.s_lo[3 * C + d], a.s_hi[3 * C + d]);
+    }
+    double* sq = sm + 3 * np1;
+    for (int k = threadIdx.x; k < P; k += kThreads) sq[k] = qh[k];
+    __syncthreads();
+    for (int k1 = 0; k1 < np1; ++k1) {
+        double dx2[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const double dx = xt[u] - sm[k1];
+            dx2[u] = dx * dx;
+        }
+        for (int k2 = 0; k2 < np1; ++k2) {
+            double t[T];
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+                const double dy = yt[u] - sm[np1 + k2];
+                t[u] = dx2[u] + dy * dy;
+            }
+            const double* qrow = sq + (k1 * np1 + k2) * np1;
+            for (int k3 = 0; k3 < np1; ++k3) {
+                const double q = qrow[k3], szk = sm[2 * np1 + k3];
+#pragma unroll
+                for (int u = 0; u < T; ++u) {
+                    const double dz = zt[u] - szk;
+                    acc[u] += g_fp64<KER>(t[u] + dz * dz, q, a.kappa);
+                }
+            }
+        }
+    }
+}
+
+template <int KER, int T>
+__device__ void item_fp64(const SweepArgs& a, int4 it, D4* sm) {
+    const int b = it.x;
+    const int B = a.b_leaves[b];
+    const int tb = a.b_begin[B], nb = a.b_count[B];
+    const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
+    double* out = a.partials + a.part_off[b] + static_cast<int64_t>(it.w) * nb;
+    for (int t0 = 0; t0 < nb; t0 += kThreads * T) {
+        double xt[T], yt[T], zt[T], acc[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const int t = min(t0 + static_cast<int>(threadIdx.x) + kThreads * u, nb - 1);
+            xt[u] = a.tx[tb + t];
+            yt[u] = a.ty[tb + t];
+            zt[u] = a.tz[tb + t];
+            acc[u] = 0.0;
+        }
+        for (int e = it.y; e < it.z; ++e) {
+            if (e < na)
+                far_fp64<KER, T>(a, a.app_ids[a0 + e], xt, yt, zt, acc, reinterpret_cast<double*>(sm));
+            else
+                near_fp64<KER, T>(a, a.dir_ids[d0 + e - na], xt, yt, zt, acc, sm);
+        }
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const int t = t0 + static_cast<int>(threadIdx.x) + kThreads * u;
+            if (t < nb) out[t] = acc[u];
+        }
+    }
+}
+
+template <int KER>
+__global__ void __launch_bounds__(kThreads, 2) k_sweep_fp64(SweepArgs a) {
+    __shared__ __align__(16) D4 sm[kSmemBytes / sizeof(D4)];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(a.counter, 1u));
+        __syncthreads();
+        const int i = s_item;
+        if (i >= a.n_items) return;
+        const int4 it = a.items[i];
+        const int nb = a.b_count[a.b_leaves[it.x]];
+        if (nb <= kThreads)
+            item_fp64<KER, 1>(a, it, sm);
+        else if (nb <= 2 * kThreads)
+            item_fp64<KER, 2>(a, it, sm);
+        else
+            item_fp64<KER, 4>(a, it, sm);
+    }
+}
+
+// ---- work plan ------------------------------------------------------------------------
+
+struct PlanArgs {
+    const int32_t* b_leaves;
+    const int32_t* b_count;
+    const int32_t* s_count;
+    const int32_t* app_off;
+    const int32_t* dir_off;
+    const int32_t* dir_ids;
+    int64_t n_batches;
+    int64_t P;
+    int64_t cut;                 // target interactions per item
+    int64_t* cost;               // per batch (pass 0)
+    unsigned long long* total;
+    int32_t* n_chunks;           // per batch
+    int64_t* part_len;           // per batch: n_chunks * nb
+    const int32_t* item_off;     // pass 2
+    int4* items;
+};
+
+__global__ void k_batch_cost(PlanArgs a) {
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= a.n_batches) return;
+    const int64_t nb = a.b_count[a.b_leaves[b]];
+    int64_t c = static_cast<int64_t>(a.app_off[b + 1] - a.app_off[b]) * a.P;
+    for (int e = a.dir_off[b]; e < a.dir_off[b + 1]; ++e) c += a.s_count[a.dir_ids[e]];
+    a.cost[b] = c * nb;
+    atomicAdd(a.total, static_cast<unsigned long long>(c * nb));
+}
+
+// Greedy cut of a batch's list (approximated clusters first, then direct ones) into items
+// of at most `cut` interactions (an item always takes at least one entry).
+template <bool kFill>
+__global__ void k_chunks(PlanArgs a) {
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= a.n_batches) return;
+    const int64_t nb = a.b_count[a.b_leaves[b]];
+    const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0;
+    const int d0 = a.dir_off[b], nd = a.dir_off[b + 1] - d0;
+    const int ne = na + nd;
+    int chunk = 0, start = 0;
+    int64_t acc = 0;
+    int4* out = kFill ? a.items + a.item_off[b] : nullptr;
+    for (int e = 0; e < ne; ++e) {
+        const int64_t c = nb * (e < na ? a.P : static_cast<int64_t>(a.s_count[a.dir_ids[d0 + e - na]]));
+        if (acc > 0 && acc + c > a.cut) {
+            if (kFill) out[chunk] = make_int4(static_cast<int>(b), start, e, chunk);
+            ++chunk;
+            start = e;
+            acc = 0;
+        }
+        acc += c;
+    }
+    if (kFill) out[chunk] = make_int4(static_cast<int>(b), start, ne, chunk);
+    ++chunk;
+    if (!kFill) {
+        a.n_chunks[b] = chunk;
+        a.part_len[b] = chunk * nb;
+    }
+}
+
+__global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* __restrict__ b_begin,
+                           const int32_t* __restrict__ b_count, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ n_chunks, const int64_t* __restrict__ part_off,
+                           const double* __restrict__ partials, double* __restrict__ phi) {
+    const int b = blockIdx.x;
+    const int B = b_leaves[b];
+    const int tb = b_begin[B], nb = b_count[B], K = n_chunks[b];
+    const double* p = partials + part_off[b];
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < K; ++c) s += p[static_cast<int64_t>(c) * nb + t];
+        phi[perm[tb + t]] = s;
+    }
+}
+
+__global__ void k_counts(const int32_t* b_leaves, const int32_t* b_count, const int32_t* s_count,
+                         const int32_t* app_off, const int32_t* dir_off, const int32_t* dir_ids,
+                         int64_t n_batches, int64_t P, unsigned long long* out) {
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= n_batches) return;
+    const int64_t nb = b_count[b_leaves[b]];
+    int64_t d = 0;
+    for (int e = dir_off[b]; e < dir_off[b + 1]; ++e) d += s_count[dir_ids[e]];
+    atomicAdd(&out[0], static_cast<unsigned long long>(d * nb));
+    atomicAdd(&out[1], static_cast<unsigned long long>(static_cast<int64_t>(app_off[b + 1] - app_off[b]) * P * nb));
+}
+
+void build_plan(Context* ctx, Lists* L, int degree) {
+    cudaStream_t s = ctx->stream;
+    const int64_t nb = L->n_batches;
+    const int64_t np1 = degree + 1;
+    Plan& pl = L->plan;
+    PlanArgs a{};
+    a.b_leaves = L->bt->leaves.p;
+    a.b_count = L->bt->count.p;
+    a.s_count = L->st->count.p;
+    a.app_off = L->app_off.p;
+    a.dir_off = L->dir_off.p;
+    a.dir_ids = L->dir_ids.p;
+    a.n_batches = nb;
+    a.P = np1 * np1 * np1;
+    DBuf<int64_t> cost(ctx, nb), part_len(ctx, nb), words(ctx, 4);
+    BLTC_CUDA(cudaMemsetAsync(words.p, 0, 4 * sizeof(int64_t), s));
+    a.cost = cost.p;
+    a.total = reinterpret_cast<unsigned long long*>(words.p);
+    k_batch_cost<<<grid_for(nb, 128), 128, 0, s>>>(a); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("plan cost");
+    const int64_t total = ctx->read_words(words.p, 1)[0];
+    const int64_t blocks = 2 * static_cast<int64_t>(std::max(1, ctx->sm_count));
+    a.cut = std::max<int64_t>(total / (blocks * kItemsPerBlock), int64_t(1) << 20);
+    pl.n_chunks = DBuf<int32_t>(ctx, nb);
+    pl.part_off = DBuf<int64_t>(ctx, nb);
+    DBuf<int32_t> item_off(ctx, nb);
+    a.n_chunks = pl.n_chunks.p;
+    a.part_len = part_len.p;
+    k_chunks<false><<<grid_for(nb, 128), 128, 0, s>>>(a); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("plan chunks");
+    exclusive_scan_i32(ctx, pl.n_chunks.p, item_off.p, nb, reinterpret_cast<int32_t*>(words.p + 1));
+    exclusive_scan_i64(ctx, part_len.p, pl.part_off.p, nb, words.p + 2);
+    const int64_t* w = ctx->read_words(words.p, 3);
+    pl.n_items = *reinterpret_cast<const int32_t*>(w + 1);
+    pl.partial_len = w[2];
+    pl.items = DBuf<int4>(ctx, pl.n_items);
+    a.item_off = item_off.p;
+    a.items = pl.items.p;
+    k_chunks<true><<<grid_for(nb, 128), 128, 0, s>>>(a); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("plan items");
+    pl.degree = degree;
+    pl.valid = true;
+}
+
+}  // namespace
+
+void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
+              double* phi) {
+    if (L->bt != bt || L->st != st)
+        throw Error(BLTC_ERR_STATE, "evaluate: lists were built for other trees");
+    if (L->degree != p.degree)
+        throw Error(BLTC_ERR_STATE, "evaluate: lists were built for another degree");
+    if (st->q_degree != p.degree || st->q_precision != p.precision)
+        throw Error(BLTC_ERR_STATE, "evaluate: modified charges missing for this degree/precision");
+    if (!st->has_q) throw Error(BLTC_ERR_STATE, "evaluate: source tree has no charges");
+    if (st->q_lists != 0 && st->q_lists != L->serial)
+        throw Error(BLTC_ERR_STATE, "evaluate: modified charges were computed for other lists");
+    require(phi != nullptr, "evaluate: phi is NULL");
+    cudaStream_t s = ctx->stream;
+    if (!L->plan.valid || L->plan.degree != p.degree) build_plan(ctx, L, p.degree);
+    Plan& pl = L->plan;
+    DBuf<double> partials(ctx, pl.partial_len);
+    DBuf<unsigned int> counter(ctx, 1);
+    BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
+
+    SweepArgs a{};
+    a.b_leaves = bt->leaves.p;
+    a.b_begin = bt->begin.p;
+    a.b_count = bt->count.p;
+    a.b_center = bt->center.p;
+    a.tx = bt->px.p;
+    a.ty = bt->py.p;
+    a.tz = bt->pz.p;
+    a.s_begin = st->begin.p;
+    a.s_count = st->count.p;
+    a.s_lo = st->lo.p;
+    a.s_hi = st->hi.p;
+    a.sx = st->px.p;
+    a.sy = st->py.p;
+    a.sz = st->pz.p;
+    a.sq = st->pq.p;
+    a.qslot = st->qslot.p;
+    a.qhat64 = st->qhat64.p;
+    a.qhat32 = st->qhat32.p;
+    a.cheb_t = ctx->cheb_table(p.degree);
+    a.np1 = p.degree + 1;
+    a.app_off = L->app_off.p;
+    a.app_ids = L->app_ids.p;
+    a.dir_off = L->dir_off.p;
+    a.dir_ids = L->dir_ids.p;
+    a.items = pl.items.p;
+    a.part_off = pl.part_off.p;
+    a.partials = partials.p;
+    a.n_items = static_cast<int>(pl.n_items);
+    a.counter = counter.p;
+    const double kappa = p.kernel == BLTC_KERNEL_YUKAWA ? p.kappa : 0.0;
+    a.kappa = kappa;
+    a.neg_kappa_log2e = static_cast<float>(-kappa * 1.4426950408889634);
+    const unsigned grid = static_cast<unsigned>(
+        std::min<int64_t>(pl.n_items, 2 * static_cast<int64_t>(std::max(1, ctx->sm_count))));
+    ctx->mark(Context::kSweepBegin);
+    if (pl.n_items > 0) {
+        if (p.precision == BLTC_PRECISION_MIXED) {
+            if (p.kernel == BLTC_KERNEL_YUKAWA) {
+                k_sweep_mixed<BLTC_KERNEL_YUKAWA><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+            }
+            else {
+                k_sweep_mixed<BLTC_KERNEL_COULOMB><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+            }
+        } else {
+            if (p.kernel == BLTC_KERNEL_YUKAWA) {
+                k_sweep_fp64<BLTC_KERNEL_YUKAWA><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+            }
+            else {
+                k_sweep_fp64<BLTC_KERNEL_COULOMB><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+            }
+        }
+        BLTC_LAUNCH_CHECK("sweep");
+    }
+    ctx->mark(Context::kSweepEnd);
+    k_finalize<<<static_cast<unsigned>(L->n_batches), 256, 0, s>>>(
+        bt->leaves.p, bt->begin.p, bt->count.p, bt->perm.p, pl.n_chunks.p, pl.part_off.p,
+        partials.p, phi); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("finalize");
+    ctx->mark(Context::kEnd);
+}
+
+void interaction_counts(Context* ctx, const Lists* L, int64_t* n_dir, int64_t* n_app) {
+    DBuf<int64_t> w(ctx, 2);
+    BLTC_CUDA(cudaMemsetAsync(w.p, 0, 2 * sizeof(int64_t), ctx->stream));
+    const int64_t np1 = L->degree + 1;
+    k_counts<<<grid_for(L->n_batches, 128), 128, 0, ctx->stream>>>(
+        L->bt->leaves.p, L->bt->count.p, L->st->count.p, L->app_off.p, L->dir_off.p,
+        L->dir_ids.p, L->n_batches, np1 * np1 * np1, reinterpret_cast<unsigned long long*>(w.p)); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("counts");
+    const int64_t* r = ctx->read_words(w.p, 2);
+    if (n_dir) *n_dir = r[0];
+    if (n_app) *n_app = r[1];
+}
+
+}  // namespace bltc

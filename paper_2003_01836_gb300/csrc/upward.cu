@@ -1,0 +1,292 @@
+// upward.cu -- A2: modified charges of the source clusters (Eq. 12, Sec. II-C).
+//
+//   qhat_k = sum_{y_j in C} L_k1(y_j1) L_k2(y_j2) L_k3(y_j3) q_j,   k = (k1, k2, k3)
+//
+// with L_k(y) = (w_k / (y - s_k)) / sum_k' (w_k' / (y - s_k')) on the Chebyshev points of
+// the second kind of C's box (Eq. 4, 6, 7), and L_k(y) = delta_{k k'} enforced when y is
+// within DBL_MIN of s_k' (Sec. II-C).  The factorisation of Eq. 14-15 (one pass per
+// particle for the three 1D denominators, then a contraction over the particles) maps to:
+//   item = (cluster, chunk of <= 2048 particles), one block per item;
+//   phase A: one thread per (particle, dimension) computes the n+1 one-dimensional factors
+//            in FP64 (differences y - s_k, exact-hit test; FP32 after the difference in
+//            the mixed path) and folds q_j into the first dimension;
+//   phase B: one thread per (k1, k2) pair (times particle groups) accumulates
+//            sum_j a1[k1] a2[k2] a3[k3] over the chunk for all k3 in registers;
+//   a second kernel sums the chunk partials of a cluster in chunk order (FP64).
+// Only clusters that some batch approximates need modified charges (a cluster's charges
+// do not depend on which batches use it).
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace bltc {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kTile = 128;            // particles per phase-A tile
+constexpr int kItem = 2048;           // particles per item
+constexpr int kMaxNp1 = BLTC_MAX_DEGREE + 1;
+
+struct UpArgs {
+    const double *px, *py, *pz, *pq;
+    const int32_t* begin;
+    const int32_t* count;
+    const double* lo;
+    const double* hi;
+    const double* cheb_t;
+    const int32_t* slot_node;         // slot -> node
+    const int4* items;                // {slot, first particle, end particle, -}
+    double* partial;                  // [n_items * P]
+    int np1;
+};
+
+// Chebyshev point k of [lo, hi] (Eq. 6 mapped linearly; s_0 = hi and s_n = lo exactly).
+__device__ __forceinline__ double cheb_point(const double* t, int k, int n, double lo, double hi) {
+    if (k == 0) return hi;
+    if (k == n) return lo;
+    return __dadd_rn(lo, __dmul_rn(__dmul_rn(0.5, __dadd_rn(t[k], 1.0)), __dsub_rn(hi, lo)));
+}
+
+template <typename F>
+__global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    F* fac = reinterpret_cast<F*>(smem_raw);       // [3][np1][kTile + 1]
+    const int np1 = a.np1, n = np1 - 1;
+    const int pairs = np1 * np1;
+    const int P = pairs * np1;
+    const int G = max(1, kThreads / pairs);
+    const int stride = kTile + 1;
+    const int4 it = a.items[blockIdx.x];
+    const int node = a.slot_node[it.x];
+    const double lo[3] = {a.lo[3 * node], a.lo[3 * node + 1], a.lo[3 * node + 2]};
+    const double hi[3] = {a.hi[3 * node], a.hi[3 * node + 1], a.hi[3 * node + 2]};
+    const int tid = threadIdx.x;
+    const bool active = tid < pairs * G;
+    const int p = tid % pairs, g = tid / pairs;
+    const int k1 = p / np1, k2 = p % np1;
+    F acc[kMaxNp1];
+#pragma unroll
+    for (int k = 0; k < kMaxNp1; ++k) acc[k] = F(0);
+
+    for (int j0 = it.y; j0 < it.z; j0 += kTile) {
+        const int m = min(kTile, it.z - j0);
+        __syncthreads();
+        if (tid < 3 * kTile) {
+            const int j = tid % kTile, d = tid / kTile;
+            if (j < m) {
+                const int pos = j0 + j;
+                const double yv = d == 0 ? a.px[pos] : (d == 1 ? a.py[pos] : a.pz[pos]);
+                const double lod = d == 0 ? lo[0] : (d == 1 ? lo[1] : lo[2]);
+                const double hid = d == 0 ? hi[0] : (d == 1 ? hi[1] : hi[2]);
+                const double qv = d == 0 ? a.pq[pos] : 1.0;
+                double dk[kMaxNp1];
+                int hit = -1;
+#pragma unroll
+                for (int k = 0; k < kMaxNp1; ++k) {
+                    if (k < np1) {
+                        dk[k] = yv - cheb_point(a.cheb_t, k, n, lod, hid);
+                        bool h = fabs(dk[k]) < 2.2250738585072014e-308;
+                        if (sizeof(F) == 4) h = h || fabsf(static_cast<float>(dk[k])) < 1.17549435e-38f;
+                        if (h && hit < 0) hit = k;
+                    }
+                }
+                F* row = fac + d * np1 * stride + j;
+                if (hit >= 0) {
+#pragma unroll
+                    for (int k = 0; k < kMaxNp1; ++k)
+                        if (k < np1) row[k * stride] = k == hit ? F(qv) : F(0);
+                } else {
+                    F raw[kMaxNp1];
+                    F den = F(0);
+#pragma unroll
+                    for (int k = 0; k < kMaxNp1; ++k) {
+                        if (k < np1) {
+                            const F w = ((k == 0 || k == n) ? F(0.5) : F(1)) * ((k & 1) ? F(-1) : F(1));
+                            raw[k] = w / F(dk[k]);
+                            den += raw[k];
+                        }
+                    }
+                    const F scale = F(qv) / den;
+#pragma unroll
+                    for (int k = 0; k < kMaxNp1; ++k)
+                        if (k < np1) row[k * stride] = raw[k] * scale;
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const F* f0 = fac + k1 * stride;
+            const F* f1 = fac + (np1 + k2) * stride;
+            const F* f2 = fac + 2 * np1 * stride;
+            for (int j = g; j < m; j += G) {
+                const F a12 = f0[j] * f1[j];
+#pragma unroll
+                for (int k = 0; k < kMaxNp1; ++k)
+                    if (k < np1) acc[k] += a12 * f2[k * stride + j];
+            }
+        }
+    }
+    // Sum the particle groups in a fixed order.
+    __syncthreads();
+    F* red = fac;                                   // [G][P]
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < kMaxNp1; ++k)
+            if (k < np1) red[g * P + p * np1 + k] = acc[k];
+    }
+    __syncthreads();
+    double* out = a.partial + static_cast<int64_t>(blockIdx.x) * P;
+    for (int o = tid; o < P; o += kThreads) {
+        double s = 0.0;
+        for (int gg = 0; gg < G; ++gg) s += static_cast<double>(red[gg * P + o]);
+        out[o] = s;
+    }
+}
+
+__global__ void k_upward_reduce(const double* __restrict__ partial,
+                                const int32_t* __restrict__ item0, int P, double* qhat64,
+                                float* qhat32) {
+    const int slot = blockIdx.x;
+    const int i0 = item0[slot], i1 = item0[slot + 1];
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        double s = 0.0;
+        for (int i = i0; i < i1; ++i) s += partial[static_cast<int64_t>(i) * P + k];
+        qhat64[static_cast<int64_t>(slot) * P + k] = s;
+        if (qhat32) qhat32[static_cast<int64_t>(slot) * P + k] = static_cast<float>(s);
+    }
+}
+
+__global__ void k_mark_from_lists(const int32_t* __restrict__ app_ids, int64_t n,
+                                  int32_t* flag) {
+    int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) flag[app_ids[i]] = 1;
+}
+
+__global__ void k_mark_by_size(const int32_t* __restrict__ count, int64_t m, int64_t P,
+                               int32_t* flag) {
+    int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v < m) flag[v] = static_cast<int64_t>(count[v]) > P ? 1 : 0;
+}
+
+__global__ void k_slots(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                        const int32_t* __restrict__ count, int64_t m, int32_t* qslot,
+                        int32_t* slot_node, int32_t* slot_items) {
+    int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= m) return;
+    if (flag[v]) {
+        qslot[v] = pos[v];
+        slot_node[pos[v]] = static_cast<int32_t>(v);
+        slot_items[pos[v]] = (count[v] + kItem - 1) / kItem;
+    } else {
+        qslot[v] = -1;
+    }
+}
+
+__global__ void k_items(const int32_t* __restrict__ slot_node,
+                        const int32_t* __restrict__ item0, const int32_t* __restrict__ begin,
+                        const int32_t* __restrict__ count, int64_t n_slots, int4* items) {
+    int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= n_slots) return;
+    const int v = slot_node[s];
+    const int b = begin[v], c = count[v];
+    for (int i = item0[s], p0 = b; p0 < b + c; ++i, p0 += kItem)
+        items[i] = make_int4(static_cast<int>(s), p0, min(b + c, p0 + kItem), 0);
+}
+
+__global__ void k_append_total(int32_t* off, int64_t n, const int32_t* total) { off[n] = *total; }
+
+template <typename F>
+size_t upward_smem(int np1) {
+    const int pairs = np1 * np1, P = pairs * np1;
+    const int G = std::max(1, kThreads / pairs);
+    size_t a = sizeof(F) * 3 * np1 * (kTile + 1);
+    size_t b = sizeof(F) * static_cast<size_t>(G) * P;
+    return std::max(a, b);
+}
+
+}  // namespace
+
+void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int degree,
+                              int precision) {
+    require(degree >= 1 && degree <= BLTC_MAX_DEGREE, "modified charges: degree out of range");
+    require(precision == BLTC_PRECISION_FP64 || precision == BLTC_PRECISION_MIXED,
+            "modified charges: bad precision");
+    if (!st->has_q) throw Error(BLTC_ERR_STATE, "modified charges: source tree has no charges");
+    if (lists && lists->st != st)
+        throw Error(BLTC_ERR_STATE, "modified charges: lists were built for another source tree");
+    cudaStream_t s = ctx->stream;
+    const int np1 = degree + 1;
+    const int P = np1 * np1 * np1;
+    const int64_t m = st->n_nodes;
+
+    DBuf<int32_t> flag(ctx, m), pos(ctx, m), tot(ctx, 2);
+    if (lists) {
+        BLTC_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int32_t) * m, s));
+        if (lists->n_app > 0) {
+            k_mark_from_lists<<<grid_for(lists->n_app, 256), 256, 0, s>>>(lists->app_ids.p,
+                                                                           lists->n_app, flag.p); ++ctx->launches;
+        }
+    } else {
+        k_mark_by_size<<<grid_for(m, 256), 256, 0, s>>>(st->count.p, m, P, flag.p); ++ctx->launches;
+    }
+    BLTC_LAUNCH_CHECK("upward mark");
+    exclusive_scan_i32(ctx, flag.p, pos.p, m, tot.p);
+    const int32_t n_slots = *reinterpret_cast<const int32_t*>(ctx->read_words(tot.p, 1));
+
+    st->qslot = DBuf<int32_t>(ctx, m);
+    st->q_slots = n_slots;
+    st->q_degree = degree;
+    st->q_precision = precision;
+    st->q_lists = lists ? lists->serial : 0;
+    st->qhat64 = DBuf<double>(ctx, static_cast<int64_t>(n_slots) * P);
+    st->qhat32 = precision == BLTC_PRECISION_MIXED
+                     ? DBuf<float>(ctx, static_cast<int64_t>(n_slots) * P)
+                     : DBuf<float>();
+    DBuf<int32_t> slot_node(ctx, n_slots), slot_items(ctx, n_slots), item0(ctx, n_slots + 1);
+    k_slots<<<grid_for(m, 256), 256, 0, s>>>(flag.p, pos.p, st->count.p, m, st->qslot.p,
+                                             slot_node.p, slot_items.p); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("upward slots");
+    if (n_slots == 0) return;
+    exclusive_scan_i32(ctx, slot_items.p, item0.p, n_slots, tot.p + 1);
+    k_append_total<<<1, 1, 0, s>>>(item0.p, n_slots, tot.p + 1); ++ctx->launches;
+    const int32_t n_items = reinterpret_cast<const int32_t*>(ctx->read_words(tot.p, 1))[1];
+    DBuf<int4> items(ctx, n_items);
+    k_items<<<grid_for(n_slots, 128), 128, 0, s>>>(slot_node.p, item0.p, st->begin.p,
+                                                   st->count.p, n_slots, items.p); ++ctx->launches;
+    DBuf<double> partial(ctx, static_cast<int64_t>(n_items) * P);
+
+    UpArgs a{};
+    a.px = st->px.p;
+    a.py = st->py.p;
+    a.pz = st->pz.p;
+    a.pq = st->pq.p;
+    a.begin = st->begin.p;
+    a.count = st->count.p;
+    a.lo = st->lo.p;
+    a.hi = st->hi.p;
+    a.cheb_t = ctx->cheb_table(degree);
+    a.slot_node = slot_node.p;
+    a.items = items.p;
+    a.partial = partial.p;
+    a.np1 = np1;
+    if (precision == BLTC_PRECISION_MIXED) {
+        const size_t sm = upward_smem<float>(np1);
+        BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm)));
+        k_upward_partial<float><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
+    } else {
+        const size_t sm = upward_smem<double>(np1);
+        BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm)));
+        k_upward_partial<double><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
+    }
+    BLTC_LAUNCH_CHECK("upward partial");
+    k_upward_reduce<<<n_slots, 256, 0, s>>>(partial.p, item0.p, P, st->qhat64.p,
+                                             precision == BLTC_PRECISION_MIXED ? st->qhat32.p
+                                                                               : nullptr); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("upward reduce");
+}
+
+}  // namespace bltc

@@ -1,0 +1,351 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: the tree and the interaction lists are bit-identical to the oracle's; the FP64 GPU
+treecode matches the oracle's Algorithm 1 to relative 2-norm 1e-12 (per target 1e-12 of the
+absolute-value sum of its terms); the mixed-precision path matches the FP64 GPU path to
+relative 2-norm 1e-6.  Sizes span several work tiles and ragged tails; the full-size
+workload (1e6 particles, theta 0.7, n 8, N_L = N_B = 2000) is checked on sampled batches.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2003_01836_gb300 as b
+from gpu_helpers import (FP64_ELEM, FP64_REL2, MIXED_ELEM, MIXED_REL2, assert_close_abs,
+                         batch_targets, dev, gpu_solve, gpu_tree, host, system)
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+TREE_KEYS = ("perm", "begin", "count", "parent", "level", "n_children", "children", "lo", "hi",
+             "center", "radius")
+
+
+def _compare_trees(ot: oracle.Tree, gt: dict):
+    for k in TREE_KEYS:
+        a, g = getattr(ot, k), gt[k]
+        assert a.shape == g.shape, k
+        if a.dtype.kind == "f":
+            assert np.array_equal(a.view(np.int64), g.view(np.int64)), f"{k} differs bitwise"
+        else:
+            assert np.array_equal(a, g.astype(a.dtype)), f"{k} differs"
+
+
+# ---- A0: tree -----------------------------------------------------------------------------
+
+def _golden_cases():
+    with open(os.path.join(GOLDEN, "trees_small.json")) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c["name"])
+def test_tree_golden_bit_exact(gpu, case):
+    x, y, z = (np.array(case[k], dtype=np.float64) for k in ("x", "y", "z"))
+    h, _ = gpu_tree(gpu, x, y, z, None, case["max_leaf"])
+    try:
+        gt = b.bltc_tree_export(gpu.h, h)
+        assert gt["perm"].tolist() == case["perm"]
+        _compare_trees(oracle.Tree(x, y, z, case["max_leaf"]), gt)
+    finally:
+        b.bltc_tree_destroy(h)
+
+
+@pytest.mark.parametrize("kind,n,leaf", [("cube", 1, 1), ("cube", 7, 2), ("cube", 10000, 500),
+                                          ("cube", 30001, 2000), ("plummer", 20000, 100),
+                                          ("cube", 4099, 1), ("plummer", 50000, 3000)])
+def test_tree_bit_exact(gpu, kind, n, leaf):
+    x, y, z, q = system(kind, n, 1000 + n)
+    h, _ = gpu_tree(gpu, x, y, z, q, leaf)
+    try:
+        _compare_trees(oracle.Tree(x, y, z, leaf), b.bltc_tree_export(gpu.h, h))
+    finally:
+        b.bltc_tree_destroy(h)
+
+
+def test_tree_degenerate_inputs_bit_exact(gpu):
+    rng = np.random.default_rng(3)
+    # duplicates, a lattice (many exact midpoint hits), signed zeros, adjacent doubles
+    lat = np.array(np.meshgrid(np.arange(8.0), np.arange(8.0), np.arange(4.0))).reshape(3, -1)
+    cases = [
+        (np.repeat(rng.uniform(-1, 1, (3, 50)), 7, axis=1), 4),
+        (lat, 3),
+        (np.stack([np.array([0.0, -0.0] * 40), rng.uniform(-1, 1, 80), np.zeros(80)]), 5),
+        (np.stack([1.0 + np.arange(64) * 2.0 ** -52, np.zeros(64), np.zeros(64)]), 3),
+    ]
+    for pts, leaf in cases:
+        h, _ = gpu_tree(gpu, pts[0], pts[1], pts[2], None, leaf)
+        try:
+            _compare_trees(oracle.Tree(pts[0], pts[1], pts[2], leaf), b.bltc_tree_export(gpu.h, h))
+        finally:
+            b.bltc_tree_destroy(h)
+
+
+def test_tree_rejects_non_finite(gpu):
+    x, y, z, q = system("cube", 100, 1)
+    y[17] = np.nan
+    with pytest.raises(b.BltcError) as e:
+        gpu_tree(gpu, x, y, z, q, 10)
+    assert e.value.status == b.BLTC_ERR_ARG
+    x, y, z, q = system("cube", 100, 1)
+    q[3] = np.inf
+    with pytest.raises(b.BltcError):
+        gpu_tree(gpu, x, y, z, q, 10)
+
+
+# ---- A1: lists ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,leaf,batch,theta,deg", [(10000, 500, 500, 0.7, 4),
+                                                     (30001, 2000, 2000, 0.7, 8),
+                                                     (20000, 300, 700, 0.5, 3),
+                                                     (20000, 64, 64, 0.9, 1),
+                                                     (5000, 100, 100, 0.0, 4)])
+def test_lists_bit_exact(gpu, n, leaf, batch, theta, deg):
+    x, y, z, q = system("cube", n, 7 * n)
+    st, _ = gpu_tree(gpu, x, y, z, q, leaf)
+    bt, _ = gpu_tree(gpu, x, y, z, None, batch) if batch != leaf else (st, None)
+    try:
+        p = b.params(deg, theta, leaf, batch)
+        L = b.bltc_lists_build(gpu.h, bt, st, p)
+        got = b.bltc_lists_export(gpu.h, L)
+        b.bltc_lists_destroy(L)
+        ost, obt = oracle.Tree(x, y, z, leaf), oracle.Tree(x, y, z, batch)
+        want = oracle.lists(obt, ost, theta, deg)
+        for k in ("approx_off", "approx_ids", "direct_off", "direct_ids"):
+            assert np.array_equal(want[k], got[k]), k
+    finally:
+        b.bltc_tree_destroy(st)
+        if bt != st:
+            b.bltc_tree_destroy(bt)
+
+
+def test_lists_plummer_bit_exact(gpu):
+    x, y, z, q = system("plummer", 40000, 11)
+    st, _ = gpu_tree(gpu, x, y, z, q, 400)
+    try:
+        L = b.bltc_lists_build(gpu.h, st, st, b.params(6, 0.8, 400))
+        got = b.bltc_lists_export(gpu.h, L)
+        b.bltc_lists_destroy(L)
+        ot = oracle.Tree(x, y, z, 400)
+        want = oracle.lists(ot, ot, 0.8, 6)
+        for k in want:
+            assert np.array_equal(want[k], got[k]), k
+    finally:
+        b.bltc_tree_destroy(st)
+
+
+# ---- A2: modified charges -----------------------------------------------------------------
+
+@pytest.mark.parametrize("deg", [1, 4, 8, 16])
+def test_modified_charges(gpu, deg):
+    n, leaf = (30000, 600) if deg < 16 else (60000, 6000)
+    x, y, z, q = system("cube", n, 5 + deg)
+    st, _ = gpu_tree(gpu, x, y, z, q, leaf)
+    try:
+        ot = oracle.Tree(x, y, z, leaf)
+        want = oracle.modified_charges(ot, q, deg)
+        P = (deg + 1) ** 3
+        scale = np.array([np.abs(q[ot.perm[ot.begin[v]:ot.begin[v] + ot.count[v]]]).sum()
+                          for v in range(ot.n_nodes)])
+        for prec, tol in ((b.BLTC_PRECISION_FP64, 1e-13), (b.BLTC_PRECISION_MIXED, 2e-6)):
+            b.bltc_modified_charges(gpu.h, st, None, b.params(deg, 0.7, leaf, precision=prec))
+            got = b.bltc_modified_charges_export(gpu.h, st, deg)
+            has = ot.count > P
+            assert np.all(np.isnan(got[~has])) and not np.any(np.isnan(got[has]))
+            err = np.abs(got[has] - want[has]).max(axis=1) / scale[has]
+            assert err.max() <= tol, (prec, err.max())
+    finally:
+        b.bltc_tree_destroy(st)
+
+
+def test_modified_charges_exact_hit_corner(gpu):
+    # particles on the box corners hit s_0 / s_n exactly (Sec. II-C)
+    x = np.array([0.0, 1.0] * 40 + [0.5])
+    y = np.array([0.0, 1.0] * 40 + [0.25])
+    z = np.array([0.0, 1.0] * 40 + [0.75])
+    q = np.linspace(-1, 1, 81)
+    st, _ = gpu_tree(gpu, x, y, z, q, 1000)
+    try:
+        b.bltc_modified_charges(gpu.h, st, None, b.params(3, 0.7, 1000, precision=b.BLTC_PRECISION_FP64))
+        got = b.bltc_modified_charges_export(gpu.h, st, 3)
+        ot = oracle.Tree(x, y, z, 1000)
+        want = oracle.modified_charges(ot, q, 3)
+        assert np.allclose(got[0], want[0], rtol=0, atol=1e-14)
+    finally:
+        b.bltc_tree_destroy(st)
+
+
+# ---- A3-A5: the whole treecode ------------------------------------------------------------
+
+def _oracle(x, y, z, q, p, batches=None):
+    phi, phi_abs, _ = oracle.bltc(x, y, z, q, p.theta, p.degree, p.leaf_size, p.batch_size,
+                                  p.kernel, p.kappa, batches=batches, with_abs=True)
+    return phi, phi_abs
+
+
+CASES = [
+    # kind, n, leaf, batch, theta, degree, kernel, kappa
+    ("cube", 10000, 500, 500, 0.7, 4, 0, 0.0),        # the small configuration
+    ("cube", 10000, 500, 500, 0.7, 4, 1, 0.5),
+    ("cube", 30001, 2000, 2000, 0.7, 8, 0, 0.0),      # several 2048-target tiles, ragged
+    ("cube", 20011, 700, 300, 0.6, 5, 1, 0.25),       # batch tree != source tree
+    ("plummer", 40000, 400, 400, 0.8, 6, 1, 0.5),     # uneven tree
+    ("cube", 50000, 3000, 3000, 0.7, 2, 0, 0.0),      # > 2048 targets and sources per tile
+    ("cube", 3001, 64, 64, 0.9, 1, 0, 0.0),           # degree 1
+    ("cube", 7, 2, 2, 0.5, 3, 0, 0.0),                # tiny
+    ("cube", 1, 1, 1, 0.7, 4, 1, 0.5),                # a single particle: phi = 0
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}{c[1]}-L{c[2]}-B{c[3]}-t{c[4]}-n{c[5]}-k{c[6]}")
+def test_bltc_fp64_and_mixed(gpu, case):
+    kind, n, leaf, batch, theta, deg, ker, kappa = case
+    x, y, z, q = system(kind, n, 31 * n + deg)
+    p64 = b.params(deg, theta, leaf, batch, ker, kappa, b.BLTC_PRECISION_FP64)
+    pmx = b.params(deg, theta, leaf, batch, ker, kappa, b.BLTC_PRECISION_MIXED)
+    want, want_abs = _oracle(x, y, z, q, p64)
+    got64 = gpu_solve(gpu, x, y, z, q, p64)
+    gotmx = gpu_solve(gpu, x, y, z, q, pmx)
+    if n == 1:
+        assert got64[0] == 0.0 and gotmx[0] == 0.0
+        return
+    assert_close_abs(want, got64, want_abs, FP64_REL2, FP64_ELEM, "fp64 vs oracle")
+    assert_close_abs(got64, gotmx, want_abs, MIXED_REL2, MIXED_ELEM, "mixed vs fp64")
+
+
+def test_degree16_sampled(gpu):
+    x, y, z, q = system("cube", 100000, 16)
+    p64 = b.params(16, 0.6, 6000, 6000, 0, 0.0, b.BLTC_PRECISION_FP64)
+    ot = oracle.Tree(x, y, z, 6000)
+    pick = np.array([0, len(ot.leaves) // 3, len(ot.leaves) - 1])
+    want, want_abs = _oracle(x, y, z, q, p64, pick)
+    idx = batch_targets(ot, pick)
+    got64 = gpu_solve(gpu, x, y, z, q, p64)
+    assert_close_abs(want[idx], got64[idx], want_abs[idx], FP64_REL2, FP64_ELEM, "n=16")
+    gotmx = gpu_solve(gpu, x, y, z, q, b.params(16, 0.6, 6000, 6000))
+    assert_close_abs(got64, gotmx, np.abs(got64).max() * np.ones_like(got64), MIXED_REL2, 1e-3, "n=16 mixed")
+
+
+def test_theta_zero_is_direct_sum(gpu):
+    x, y, z, q = system("cube", 6000, 99)
+    pts = np.stack([x, y, z])
+    ref, ref_abs = oracle.direct_sum(pts, pts, q, with_abs=True)
+    got = gpu_solve(gpu, x, y, z, q, b.params(4, 0.0, 300, precision=b.BLTC_PRECISION_FP64))
+    assert_close_abs(ref, got, ref_abs, 1e-14, 1e-14, "theta=0")
+
+
+def test_yukawa_kappa0_equals_coulomb(gpu):
+    x, y, z, q = system("cube", 20000, 5)
+    for prec in (b.BLTC_PRECISION_FP64, b.BLTC_PRECISION_MIXED):
+        c = gpu_solve(gpu, x, y, z, q, b.params(6, 0.7, 800, precision=prec))
+        yk = gpu_solve(gpu, x, y, z, q, b.params(6, 0.7, 800, kernel=1, kappa=0.0, precision=prec))
+        assert np.array_equal(c, yk)
+
+
+def test_deterministic_bits(gpu):
+    x, y, z, q = system("cube", 40000, 8)
+    for prec in (b.BLTC_PRECISION_FP64, b.BLTC_PRECISION_MIXED):
+        p = b.params(6, 0.7, 1000, precision=prec)
+        assert np.array_equal(gpu_solve(gpu, x, y, z, q, p), gpu_solve(gpu, x, y, z, q, p))
+
+
+def test_step_api_matches_solve_and_stats(gpu):
+    import torch
+    x, y, z, q = system("cube", 30000, 4)
+    p = b.params(5, 0.7, 1000)
+    X = dev(x, y, z, q)
+    st = b.bltc_tree_build(gpu.h, *X, 1000)
+    L = b.bltc_lists_build(gpu.h, st, st, p)
+    b.bltc_modified_charges(gpu.h, st, L, p)
+    phi = torch.empty_like(X[0])
+    b.bltc_evaluate(gpu.h, L, st, st, p, phi)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(phi), gpu_solve(gpu, x, y, z, q, p))
+    s = b.bltc_stats(gpu.h, L)
+    ot = oracle.Tree(x, y, z, 1000)
+    lw = oracle.lists(ot, ot, 0.7, 5)
+    nb = ot.count[ot.leaves]
+    d = sum(nb[i] * ot.count[lw["direct_ids"][lw["direct_off"][i]:lw["direct_off"][i + 1]]].sum()
+            for i in range(len(nb)))
+    a = sum(nb[i] * (lw["approx_off"][i + 1] - lw["approx_off"][i]) * 216 for i in range(len(nb)))
+    assert s == {"direct": d, "approx": a}
+    # evaluate without modified charges for this precision is a state error
+    with pytest.raises(b.BltcError) as e:
+        b.bltc_evaluate(gpu.h, L, st, st, b.params(5, 0.7, 1000, precision=0), phi)
+    assert e.value.status == b.BLTC_ERR_STATE
+    b.bltc_lists_destroy(L)
+    b.bltc_tree_destroy(st)
+
+
+def test_solve_host_matches_device(gpu):
+    x, y, z, q = system("cube", 20000, 6)
+    p = b.params(6, 0.7, 1000)
+    phi = np.empty_like(x)
+    b.bltc_solve_host(gpu.h, x, y, z, q, p, phi)
+    assert np.array_equal(phi, gpu_solve(gpu, x, y, z, q, p))
+
+
+@pytest.mark.parametrize("bad", [dict(theta=1.0), dict(theta=-0.1), dict(theta=math.nan),
+                                 dict(degree=0), dict(degree=17), dict(leaf_size=0),
+                                 dict(kernel=1, kappa=-1.0), dict(precision=3)])
+def test_invalid_parameters_rejected(gpu, bad):
+    x, y, z, q = system("cube", 100, 2)
+    kw = dict(degree=4, theta=0.7, leaf_size=10)
+    kw.update(bad)
+    with pytest.raises(b.BltcError) as e:
+        gpu_solve(gpu, x, y, z, q, b.params(**kw))
+    assert e.value.status == b.BLTC_ERR_ARG
+
+
+# ---- direct sum (the GPU baseline) --------------------------------------------------------
+
+@pytest.mark.parametrize("nt,ns,ker", [(3000, 3000, 0), (2047, 5001, 1), (1, 17, 0), (40000, 40000, 0)])
+def test_direct_sum(gpu, nt, ns, ker):
+    import torch
+    xs = system("cube", max(nt, ns), nt + ns)
+    t = [a[:nt] for a in xs[:3]]
+    s = [a[:ns] for a in xs[:3]]
+    q = xs[3][:ns]
+    T, S, Q = dev(*t), dev(*s), dev(q)[0]
+    if nt > 5000:
+        pick = np.arange(0, nt, 97)
+    else:
+        pick = np.arange(nt)
+    ref, ref_abs = oracle.direct_sum(np.stack(t)[:, pick], np.stack(s), q, ker, 0.5, with_abs=True)
+    for prec, r2, el in ((0, 1e-14, 1e-14), (1, 1e-6, 1e-5)):
+        phi = torch.empty_like(T[0])
+        b.bltc_direct_sum(gpu.h, *T, *S, Q, b.params(4, 0.5, 10, kernel=ker, kappa=0.5, precision=prec), phi)
+        got = host(phi)[pick]
+        assert_close_abs(ref, got, ref_abs, r2, el, f"direct prec={prec}")
+
+
+# ---- the full-size workload, sampled ------------------------------------------------------
+
+def test_full_size_1e6_sampled(gpu):
+    x, y, z, q = system("cube", 1_000_000, 20031838)
+    p64 = b.params(8, 0.7, 2000, 2000, 0, 0.0, b.BLTC_PRECISION_FP64)
+    pmx = b.params(8, 0.7, 2000, 2000, 0, 0.0, b.BLTC_PRECISION_MIXED)
+    h, _ = gpu_tree(gpu, x, y, z, q, 2000)
+    ot = oracle.Tree(x, y, z, 2000)
+    try:
+        _compare_trees(ot, b.bltc_tree_export(gpu.h, h))
+        L = b.bltc_lists_build(gpu.h, h, h, pmx)
+        got = b.bltc_lists_export(gpu.h, L)
+        b.bltc_lists_destroy(L)
+        want = oracle.lists(ot, ot, 0.7, 8)
+        for k in want:
+            assert np.array_equal(want[k], got[k]), k
+    finally:
+        b.bltc_tree_destroy(h)
+    nl = len(ot.leaves)
+    pick = np.array([0, 1, nl // 2, nl - 2, nl - 1])
+    want, want_abs = _oracle(x, y, z, q, p64, pick)
+    idx = batch_targets(ot, pick)
+    got64 = gpu_solve(gpu, x, y, z, q, p64)
+    gotmx = gpu_solve(gpu, x, y, z, q, pmx)
+    assert_close_abs(want[idx], got64[idx], want_abs[idx], FP64_REL2, FP64_ELEM, "1e6 fp64 sampled")
+    e = oracle.rel_err(got64, gotmx)
+    assert e <= MIXED_REL2, e
