@@ -17,6 +17,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kTile32 = 2048;
 constexpr int kTile64 = 1024;
+constexpr int kBlock = 32;       // FP32 block folded into a TwoSum accumulator
 
 struct DirectArgs {
     const double *tx, *ty, *tz;
@@ -36,6 +37,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Knuth's TwoSum fold of a short FP32 block sum into a compensated FP32 accumulator.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
 }
 
 template <int KER, int T>
@@ -61,24 +71,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_direct_mixed(DirectArgs a) {
             sm[j] = make_float4(__double2float_rn(a.sx[j0 + j]), __double2float_rn(a.sy[j0 + j]),
                                 __double2float_rn(a.sz[j0 + j]), __double2float_rn(a.sq[j0 + j]));
         __syncthreads();
-        float f[T];
+        float hi[T], lo[T];
 #pragma unroll
-        for (int u = 0; u < T; ++u) f[u] = 0.f;
+        for (int u = 0; u < T; ++u) hi[u] = lo[u] = 0.f;
+        for (int jb = 0; jb < m; jb += kBlock) {
+            const int je = min(jb + kBlock, m);
+            float f[T];
+#pragma unroll
+            for (int u = 0; u < T; ++u) f[u] = 0.f;
 #pragma unroll 2
-        for (int j = 0; j < m; ++j) {
-            const float4 s = sm[j];
+            for (int j = jb; j < je; ++j) {
+                const float4 s = sm[j];
 #pragma unroll
-            for (int u = 0; u < T; ++u) {
-                const float dx = s.x - xt[u], dy = s.y - yt[u], dz = s.z - zt[u];
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float ri = rsqrt_approx(r2);
-                ri = r2 > 0.f ? ri : 0.f;
-                if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
-                f[u] = fmaf(s.w, ri, f[u]);
+                for (int u = 0; u < T; ++u) {
+                    const float dx = s.x - xt[u], dy = s.y - yt[u], dz = s.z - zt[u];
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float ri = rsqrt_approx(r2);
+                    ri = r2 > 0.f ? ri : 0.f;
+                    if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
+                    f[u] = fmaf(s.w, ri, f[u]);
+                }
             }
+#pragma unroll
+            for (int u = 0; u < T; ++u) two_sum_add(hi[u], lo[u], f[u]);
         }
 #pragma unroll
-        for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(f[u]);
+        for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
     }
     double* out = a.partial + static_cast<int64_t>(blockIdx.y) * a.nt;
 #pragma unroll
@@ -116,9 +134,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_direct_fp64(DirectArgs a) {
                 const double dx = xt[u] - s.x, dy = yt[u] - s.y, dz = zt[u] - s.z;
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 != 0.0) {
-                    const double ri = rsqrt(r2);
-                    acc[u] += KER == BLTC_KERNEL_YUKAWA ? s.w * ri * exp(-a.kappa * (r2 * ri))
-                                                        : s.w * ri;
+                    double ri = rsqrt(r2);
+                    if (KER == BLTC_KERNEL_YUKAWA) ri *= exp(-a.kappa * (r2 * ri));
+                    acc[u] += s.w * ri;
                 }
             }
         }

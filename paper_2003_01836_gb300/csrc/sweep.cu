@@ -35,6 +35,7 @@ constexpr int kSrcTile32 = 2048;      // float4 sources per staged tile (32 KB)
 constexpr int kSrcTile64 = 1280;      // D4 sources per staged tile (40 KB)
 constexpr int kSmemBytes = 40960;     // also holds 3(n+1) + (n+1)^3 doubles for n <= 16
 constexpr int kItemsPerBlock = 12;    // work items per resident block (load balance)
+constexpr int kBlock = 32;            // near-field FP32 block folded into a TwoSum accumulator
 
 struct SweepArgs {
     // target batches
@@ -80,6 +81,16 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return r;
 }
 
+// Knuth's TwoSum: hi + lo += v exactly up to the rounding of lo (no magnitude ordering
+// needed).  Folds a short FP32 block sum into a compensated FP32 accumulator.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
 __device__ __forceinline__ double cheb_point(const double* t, int k, int n, double lo, double hi) {
     if (k == 0) return hi;
     if (k == n) return lo;
@@ -88,98 +99,204 @@ __device__ __forceinline__ double cheb_point(const double* t, int k, int n, doub
 
 // ---- mixed precision ------------------------------------------------------------------
 
+// G(r) without the charge: 1/r, or e^{-kappa r}/r as 2^{-kappa log2(e) r} / r.  The charge
+// multiplies last in both kernels, so kappa = 0 reproduces Coulomb bit for bit.
 template <int KER>
-__device__ __forceinline__ float g_mixed(float r2, float q, float nkl2e) {
+__device__ __forceinline__ float ri_mixed(float r2, float nkl2e) {
     float ri = rsqrt_approx(r2);
     if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(nkl2e * (r2 * ri));
-    return q * ri;
+    return ri;
 }
 
+// Packed FP32x2 arithmetic (FADD2 / FMUL2 / FFMA2 on sm_100 and later): one instruction
+// works on two targets, which halves the FMA-pipe issue slots per interaction so that the
+// SFU (one MUFU.RSQ per interaction) becomes the binding pipe.  Each lane of a packed
+// operation rounds exactly like the scalar operation, so both paths give identical bits.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int KER>
+__device__ __forceinline__ float2 ri2_mixed(float2 r2, float nkl2e, bool skip_zero) {
+    float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    if (skip_zero) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    if (KER == BLTC_KERNEL_YUKAWA) {
+        const float2 a = mul2(make_float2(nkl2e, nkl2e), mul2(r2, ri));
+        ri = mul2(ri, make_float2(ex2_approx(a.x), ex2_approx(a.y)));
+    }
+    return ri;
+}
+
+// Targets of one thread: T values per coordinate, relative to the batch centre.  For the
+// packed path they are kept negated in pairs: (-x[2v], -x[2v+1]).
+template <int T>
+struct Targets {
+    float2 x[(T + 1) / 2], y[(T + 1) / 2], z[(T + 1) / 2];   // target u is component u % 2 of [u / 2]
+};
+
+// Near field (Eq. 9) of cluster C.  Shared memory holds each staged source as two float4:
+// (x, x, y, y) and (z, z, q, q), relative to the batch centre, so a packed operand is one
+// aligned register pair.  Sums run over blocks of kBlock sources in FP32, folded into a
+// TwoSum accumulator, then into FP64 per staged tile.
 template <int KER, int T>
-__device__ void near_mixed(const SweepArgs& a, int C, const double cb[3], const float (&xt)[T],
-                           const float (&yt)[T], const float (&zt)[T], double (&acc)[T],
-                           float4* sm) {
+__device__ void near_mixed(const SweepArgs& a, int C, const double cb[3], const Targets<T>& tg,
+                           double (&acc)[T], float4* sm) {
+    constexpr int kTile = kSrcTile32 / 2;
     const int cs = a.s_begin[C], nc = a.s_count[C];
-    for (int j0 = 0; j0 < nc; j0 += kSrcTile32) {
-        const int m = min(kSrcTile32, nc - j0);
+    for (int j0 = 0; j0 < nc; j0 += kTile) {
+        const int m = min(kTile, nc - j0);
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += kThreads) {
             const int p = cs + j0 + j;
-            sm[j] = make_float4(__double2float_rn(a.sx[p] - cb[0]), __double2float_rn(a.sy[p] - cb[1]),
-                                __double2float_rn(a.sz[p] - cb[2]), __double2float_rn(a.sq[p]));
+            const float sx = __double2float_rn(a.sx[p] - cb[0]);
+            const float sy = __double2float_rn(a.sy[p] - cb[1]);
+            const float sz = __double2float_rn(a.sz[p] - cb[2]);
+            const float sq = __double2float_rn(a.sq[p]);
+            sm[2 * j] = make_float4(sx, sx, sy, sy);
+            sm[2 * j + 1] = make_float4(sz, sz, sq, sq);
         }
         __syncthreads();
-        float f[T];
+        float hi[T], lo[T];
 #pragma unroll
-        for (int u = 0; u < T; ++u) f[u] = 0.f;
+        for (int u = 0; u < T; ++u) hi[u] = lo[u] = 0.f;
+        for (int jb = 0; jb < m; jb += kBlock) {
+            const int je = min(jb + kBlock, m);
+            if constexpr (T == 1) {
+                float f = 0.f;
+#pragma unroll 4
+                for (int j = jb; j < je; ++j) {
+                    const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
+                    const float dx = p0.x + tg.x[0].x, dy = p0.z + tg.y[0].x, dz = p1.x + tg.z[0].x;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float ri = rsqrt_approx(r2);
+                    ri = r2 > 0.f ? ri : 0.f;
+                    if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
+                    f = fmaf(p1.z, ri, f);
+                }
+                two_sum_add(hi[0], lo[0], f);
+            } else {
+                constexpr int H = T / 2;
+                float2 f[H];
+#pragma unroll
+                for (int v = 0; v < H; ++v) f[v] = make_float2(0.f, 0.f);
 #pragma unroll 2
-        for (int j = 0; j < m; ++j) {
-            const float4 s = sm[j];
+                for (int j = jb; j < je; ++j) {
+                    const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
+                    const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
+                    const float2 sz = make_float2(p1.x, p1.y), sq = make_float2(p1.z, p1.w);
 #pragma unroll
-            for (int u = 0; u < T; ++u) {
-                const float dx = s.x - xt[u], dy = s.y - yt[u], dz = s.z - zt[u];
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float ri = rsqrt_approx(r2);
-                ri = r2 > 0.f ? ri : 0.f;
-                if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
-                f[u] = fmaf(s.w, ri, f[u]);
+                    for (int v = 0; v < H; ++v) {
+                        const float2 dx = add2(sx, tg.x[v]);
+                        const float2 dy = add2(sy, tg.y[v]);
+                        const float2 dz = add2(sz, tg.z[v]);
+                        const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                        f[v] = fma2(sq, ri2_mixed<KER>(r2, a.neg_kappa_log2e, true), f[v]);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < H; ++v) {
+                    two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
+                    two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
+                }
             }
         }
 #pragma unroll
-        for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(f[u]);
+        for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
     }
 }
 
+// Far field (Eq. 11) of cluster C on its tensor grid of Chebyshev points (Eq. 8).  Shared
+// memory holds (s, s) pairs of the 3(n+1) point coordinates relative to the batch centre,
+// then (qhat, qhat) pairs of the (n+1)^3 modified charges.  For each (k1, k2) the partial
+// r^2 of a target is reused over the n+1 values of k3; each (k1, k2) row of n+1 terms is
+// summed in FP32 and folded into a TwoSum accumulator.
 template <int KER, int T>
-__device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const float (&xt)[T],
-                          const float (&yt)[T], const float (&zt)[T], double (&acc)[T],
-                          float* sm) {
+__device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const Targets<T>& tg,
+                          double (&acc)[T], float2* sm) {
     const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1;
     const float* qh = a.qhat32 + static_cast<int64_t>(a.qslot[C]) * P;
     __syncthreads();
     for (int k = threadIdx.x; k < 3 * np1; k += kThreads) {
         const int d = k / np1, kk = k - d * np1;
         const double s = cheb_point(a.cheb_t, kk, n, a.s_lo[3 * C + d], a.s_hi[3 * C + d]);
-        sm[k] = __double2float_rn(s - cb[d]);
+        const float v = __double2float_rn(s - (d == 0 ? cb[0] : (d == 1 ? cb[1] : cb[2])));
+        sm[k] = make_float2(v, v);
     }
-    float* sq = sm + 3 * np1;
-    for (int k = threadIdx.x; k < P; k += kThreads) sq[k] = qh[k];
+    float2* sq = sm + 3 * np1;
+    for (int k = threadIdx.x; k < P; k += kThreads) {
+        const float v = qh[k];
+        sq[k] = make_float2(v, v);
+    }
     __syncthreads();
-    float f[T];
+    const float2* sxp = sm;
+    const float2* syp = sm + np1;
+    const float2* szp = sm + 2 * np1;
+    float hi[T], lo[T];
 #pragma unroll
-    for (int u = 0; u < T; ++u) f[u] = 0.f;
-    for (int k1 = 0; k1 < np1; ++k1) {
-        float dx2[T];
-        const float sxk = sm[k1];
-#pragma unroll
-        for (int u = 0; u < T; ++u) {
-            const float dx = sxk - xt[u];
-            dx2[u] = dx * dx;
-        }
-        for (int k2 = 0; k2 < np1; ++k2) {
-            float t[T];
-            const float syk = sm[np1 + k2];
-#pragma unroll
-            for (int u = 0; u < T; ++u) {
-                const float dy = syk - yt[u];
-                t[u] = fmaf(dy, dy, dx2[u]);
-            }
-            const float* qrow = sq + (k1 * np1 + k2) * np1;
-            const float* sz = sm + 2 * np1;
+    for (int u = 0; u < T; ++u) hi[u] = lo[u] = 0.f;
+    if constexpr (T == 1) {
+        for (int k1 = 0; k1 < np1; ++k1) {
+            const float dx = sxp[k1].x + tg.x[0].x;
+            const float dx2 = dx * dx;
+            for (int k2 = 0; k2 < np1; ++k2) {
+                const float dy = syp[k2].x + tg.y[0].x;
+                const float t = fmaf(dy, dy, dx2);
+                const float2* qrow = sq + (k1 * np1 + k2) * np1;
+                float f = 0.f;
 #pragma unroll 3
-            for (int k3 = 0; k3 < np1; ++k3) {
-                const float q = qrow[k3], szk = sz[k3];
+                for (int k3 = 0; k3 < np1; ++k3) {
+                    const float dz = szp[k3].x + tg.z[0].x;
+                    const float r2 = fmaf(dz, dz, t);
+                    f = fmaf(qrow[k3].x, ri_mixed<KER>(r2, a.neg_kappa_log2e), f);
+                }
+                two_sum_add(hi[0], lo[0], f);
+            }
+        }
+    } else {
+        constexpr int H = T / 2;
+        for (int k1 = 0; k1 < np1; ++k1) {
+            float2 dx2[H];
+            const float2 sx = sxp[k1];
 #pragma unroll
-                for (int u = 0; u < T; ++u) {
-                    const float dz = szk - zt[u];
-                    const float r2 = fmaf(dz, dz, t[u]);
-                    f[u] += g_mixed<KER>(r2, q, a.neg_kappa_log2e);
+            for (int v = 0; v < H; ++v) {
+                const float2 dx = add2(sx, tg.x[v]);
+                dx2[v] = mul2(dx, dx);
+            }
+            for (int k2 = 0; k2 < np1; ++k2) {
+                float2 t[H];
+                const float2 sy = syp[k2];
+#pragma unroll
+                for (int v = 0; v < H; ++v) {
+                    const float2 dy = add2(sy, tg.y[v]);
+                    t[v] = fma2(dy, dy, dx2[v]);
+                }
+                const float2* qrow = sq + (k1 * np1 + k2) * np1;
+                float2 f[H];
+#pragma unroll
+                for (int v = 0; v < H; ++v) f[v] = make_float2(0.f, 0.f);
+#pragma unroll 3
+                for (int k3 = 0; k3 < np1; ++k3) {
+                    const float2 sz = szp[k3], q = qrow[k3];
+#pragma unroll
+                    for (int v = 0; v < H; ++v) {
+                        const float2 dz = add2(sz, tg.z[v]);
+                        const float2 r2 = fma2(dz, dz, t[v]);
+                        f[v] = fma2(q, ri2_mixed<KER>(r2, a.neg_kappa_log2e, false), f[v]);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < H; ++v) {
+                    two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
+                    two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
                 }
             }
         }
     }
 #pragma unroll
-    for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(f[u]);
+    for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
 }
 
 template <int KER, int T>
@@ -191,22 +308,30 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
     const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
     double* out = a.partials + a.part_off[b] + static_cast<int64_t>(it.w) * nb;
     for (int t0 = 0; t0 < nb; t0 += kThreads * T) {
-        float xt[T], yt[T], zt[T];
+        Targets<T> tg;          // negated batch-relative coordinates: s + (-x) = s - x
         double acc[T];
 #pragma unroll
         for (int u = 0; u < T; ++u) {
             const int t = min(t0 + static_cast<int>(threadIdx.x) + kThreads * u, nb - 1);
-            xt[u] = __double2float_rn(a.tx[tb + t] - cb[0]);
-            yt[u] = __double2float_rn(a.ty[tb + t] - cb[1]);
-            zt[u] = __double2float_rn(a.tz[tb + t] - cb[2]);
+            const float nx = -__double2float_rn(a.tx[tb + t] - cb[0]);
+            const float ny = -__double2float_rn(a.ty[tb + t] - cb[1]);
+            const float nz = -__double2float_rn(a.tz[tb + t] - cb[2]);
+            if (u & 1) {
+                tg.x[u / 2].y = nx;
+                tg.y[u / 2].y = ny;
+                tg.z[u / 2].y = nz;
+            } else {
+                tg.x[u / 2].x = nx;
+                tg.y[u / 2].x = ny;
+                tg.z[u / 2].x = nz;
+            }
             acc[u] = 0.0;
         }
         for (int e = it.y; e < it.z; ++e) {
             if (e < na)
-                far_mixed<KER, T>(a, a.app_ids[a0 + e], cb, xt, yt, zt, acc,
-                                  reinterpret_cast<float*>(sm));
+                far_mixed<KER, T>(a, a.app_ids[a0 + e], cb, tg, acc, reinterpret_cast<float2*>(sm));
             else
-                near_mixed<KER, T>(a, a.dir_ids[d0 + e - na], cb, xt, yt, zt, acc, sm);
+                near_mixed<KER, T>(a, a.dir_ids[d0 + e - na], cb, tg, acc, sm);
         }
 #pragma unroll
         for (int u = 0; u < T; ++u) {
@@ -243,8 +368,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_mixed(SweepArgs a) {
 
 template <int KER>
 __device__ __forceinline__ double g_fp64(double r2, double q, double kappa) {
-    const double ri = rsqrt(r2);
-    if (KER == BLTC_KERNEL_YUKAWA) return q * ri * exp(-kappa * (r2 * ri));
+    double ri = rsqrt(r2);
+    if (KER == BLTC_KERNEL_YUKAWA) ri *= exp(-kappa * (r2 * ri));
     return q * ri;
 }
 
