@@ -348,6 +348,109 @@ def run_e2e(ctx, b, x, y, z, q, p, args, dist, w):
             "d2h_bytes_per_step": 8 * w["n"], "steps": k, "ms_per_step": t * 1e3}
 
 
+# ---- serving: continuous batching of a request stream --------------------------------------
+
+SERVE_METRIC = "served requests: targets/s at saturation; p50/p99 latency (ms) at Poisson load"
+
+
+def serve_requests(count, seed=20031836 + 4):
+    """The request mix: N log-uniform in [1e3, 1e6], cube or Plummer, Coulomb or Yukawa
+    (kappa uniform [0.1, 1]), theta uniform [0.5, 0.8], n in {4, 6, 8, 10}, mixed precision."""
+    import paper_2003_01836_gb300 as b
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(10 ** rng.uniform(3.0, 6.0)))
+        kind = "cube" if rng.random() < 0.5 else "plummer"
+        ker = int(rng.random() < 0.5)
+        kappa = float(rng.uniform(0.1, 1.0)) if ker else 0.0
+        theta = float(rng.uniform(0.5, 0.8))
+        deg = int(rng.choice([4, 6, 8, 10]))
+        out.append((kind, n, seed * 10000 + i,
+                    b.params(deg, theta, 2000, 2000, ker, kappa, b.BLTC_PRECISION_MIXED)))
+    return out
+
+
+def run_serving(args, dist: Dist):
+    import concurrent.futures as cf
+    import threading
+
+    import paper_2003_01836_gb300 as b
+    from paper_2003_01836_gb300 import build, inputs
+    build.build()
+    reqs = serve_requests(args.serve_requests)
+
+    def make(r):
+        kind, n, sd, _ = r
+        return [np.ascontiguousarray(a) for a in inputs.system(kind, n, sd)]
+
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        data = list(ex.map(make, reqs))
+    total_targets = sum(r[1] for r in reqs)
+    srv = b.Server(dist.local_rank, setup_workers=args.serve_workers, max_batch=64)
+    try:
+        # warm-up: a few requests
+        for i in range(min(8, len(reqs))):
+            srv.wait(srv.submit(*data[i], reqs[i][3]))
+
+        def run_load(rate):
+            """Submits every request (Poisson arrivals at `rate` per second, or all at once
+            for rate None) and returns the wall time and per-request latencies."""
+            rng = np.random.default_rng(7)
+            gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+            tickets = [None] * len(reqs)
+            t0 = time.perf_counter()
+
+            def submitter():
+                t = t0
+                for i, g in enumerate(gaps):
+                    t += g
+                    d = t - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    tickets[i] = srv.submit(*data[i], reqs[i][3])
+            th = threading.Thread(target=submitter)
+            th.start()
+            lat = []
+            for i in range(len(reqs)):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                st, _, info = srv.wait(tickets[i])
+                if st != b.BLTC_OK:
+                    raise RuntimeError(f"request {i} failed with status {st}")
+                lat.append((info["t_done"] - info["t_submit"]) * 1e3)
+            th.join()
+            return time.perf_counter() - t0, np.array(lat)
+
+        wall, lat = run_load(None)
+        x_req = len(reqs) / wall
+        levels = [{"load": "saturated (all submitted at t=0)", "requests_per_s": x_req,
+                   "targets_per_s": total_targets / wall, "p50_ms": float(np.percentile(lat, 50)),
+                   "p99_ms": float(np.percentile(lat, 99))}]
+        for frac in (0.5, 0.8, 1.0):
+            wall_f, lat_f = run_load(frac * x_req)
+            levels.append({"load": f"Poisson at {frac:.1f} x saturated rate",
+                           "offered_requests_per_s": frac * x_req,
+                           "requests_per_s": len(reqs) / wall_f,
+                           "targets_per_s": total_targets / wall_f,
+                           "p50_ms": float(np.percentile(lat_f, 50)),
+                           "p99_ms": float(np.percentile(lat_f, 99))})
+        stats = srv.stats()
+    finally:
+        srv.close()
+    return {"metric": SERVE_METRIC, "value": levels[0]["targets_per_s"], "unit": "targets/s",
+            "n_gpus": dist.world, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (f64 accumulation)", "data": "synthetic",
+            "config": {"workload": "serving stream", "requests": len(reqs),
+                       "total_targets": total_targets,
+                       "mix": "N log-uniform [1e3,1e6]; cube|Plummer; Coulomb|Yukawa kappa U[0.1,1]; "
+                              "theta U[0.5,0.8]; n in {4,6,8,10}; N_L=N_B=2000; mixed",
+                       "setup_workers": args.serve_workers, "max_batch": 64},
+            "levels": levels,
+            "server": {k: stats[k] for k in ("sweep_launches", "max_batch", "peak_reserved_bytes",
+                                             "peak_live_bytes", "budget_bytes")}}
+
+
 # ---- reference arm: the oracle --------------------------------------------------------------
 
 def run_reference(args, dist: Dist):
@@ -391,12 +494,21 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="time the serving runtime on the request stream instead")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-workers", type=int, default=3)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     dist = Dist()
     try:
-        out = run_reference(args, dist) if args.impl == "reference" else run_ours(args, dist)
+        if args.impl == "reference":
+            out = run_reference(args, dist)
+        elif args.serving:
+            out = run_serving(args, dist)
+        else:
+            out = run_ours(args, dist)
         if out is not None and dist.rank == 0:
             print(json.dumps(out), flush=True)
     finally:

@@ -58,7 +58,8 @@ typedef enum bltc_status {
     BLTC_ERR_OOM = -2,      /* the allocator returned no memory */
     BLTC_ERR_CUDA = -3,     /* a CUDA call failed; the message names it */
     BLTC_ERR_TIMEOUT = -4,  /* reserved for bounded device-side waits (none in this version) */
-    BLTC_ERR_STATE = -5     /* handles that do not belong together, or a step missing */
+    BLTC_ERR_STATE = -5,    /* handles that do not belong together, or a step missing */
+    BLTC_ERR_CANCELLED = -6 /* a served request was cancelled before admission */
 } bltc_status;
 
 enum { BLTC_KERNEL_COULOMB = 0, BLTC_KERNEL_YUKAWA = 1 };
@@ -204,6 +205,20 @@ bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,
                             const double* z, const double* q, int64_t n,
                             const bltc_params* params, double* phi);
 
+/* ---- autotuning of the leaf and batch sizes --------------------------------------- */
+
+/* Times bltc_solve of the given system for each candidate (leaf_size, batch_size) pair
+ * (leaf[i], batch[i]; batch may be NULL for batch = leaf), `repeats` times each after one
+ * warm-up, and writes the fastest into *best (a copy of *params with those sizes) and the
+ * fastest time of every candidate into ms[n_candidates] (may be NULL).  The choice is cached
+ * in the context under (floor(log2 n), degree, kernel, precision, theta to 1e-3): a later call
+ * with the same key and use_cache != 0 returns the cached choice without timing (ms untouched).
+ * Device pointers as bltc_solve.  Synchronizes.  Errors: ARG, OOM, CUDA. */
+bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, const double* z,
+                          const double* q, int64_t n, const bltc_params* params,
+                          const int32_t* leaf, const int32_t* batch, int32_t n_candidates,
+                          int32_t repeats, int32_t use_cache, bltc_params* best, float* ms);
+
 /* ---- direct summation, Eq. 1 (the GPU baseline) ----------------------------------- */
 
 /* phi[i] = sum_j G(x_i, y_j) q_j over all nt targets (tx, ty, tz) and ns sources
@@ -214,6 +229,64 @@ bltc_status bltc_direct_sum(bltc_context* ctx, const double* tx, const double* t
                             const double* tz, int64_t nt, const double* sx, const double* sy,
                             const double* sz, const double* sq, int64_t ns,
                             const bltc_params* params, double* phi);
+
+/* ---- serving: continuous batching of many requests on one GPU -------------------- */
+/* Not in the paper (which runs one system per rank); the runtime that keeps the GPU busy
+ * with a stream of independent particle systems of uneven size.  Each request is the whole
+ * of Algorithm 1 in mixed precision (targets = sources).  Requests are admitted in
+ * arrival order while their estimated device memory fits the HBM budget; setup workers
+ * (host threads with their own streams) build each admitted request's tree, lists,
+ * modified charges and work plan; one engine merges the far/near sweeps of all prepared
+ * requests into one persistent launch (work items of all requests, longest first), then
+ * finalizes each request and copies its potentials out.  Setup of later requests overlaps
+ * the running sweep.  A request's potentials are bit-identical to bltc_solve of that
+ * request alone, whatever else is in flight. */
+
+typedef struct bltc_server bltc_server;
+
+typedef struct bltc_server_config {
+    int32_t device;           /* CUDA device */
+    int32_t setup_workers;    /* host threads preparing requests, 1..64 */
+    int32_t max_batch;        /* most requests merged into one sweep launch, >= 1 */
+    int32_t reserved;         /* must be 0 */
+    int64_t hbm_budget_bytes; /* device bytes admitted requests may reserve; 0 = 80% of free */
+} bltc_server_config;
+
+typedef struct bltc_request_info {
+    int32_t status;           /* bltc_status of the request */
+    int32_t batch;            /* requests in the sweep launch it ran in */
+    int64_t bytes_reserved;   /* device bytes reserved for it at admission */
+    double t_submit, t_admit, t_ready, t_done;   /* host monotonic clock, seconds */
+} bltc_request_info;
+
+typedef struct bltc_server_stats {
+    int64_t submitted, completed, failed, cancelled, queued;
+    int64_t sweep_launches, max_batch;
+    int64_t budget_bytes, reserved_bytes, peak_reserved_bytes;
+    int64_t live_bytes, peak_live_bytes;   /* actually allocated through the server */
+} bltc_server_counters;
+
+/* Starts the server threads on cfg->device.  Errors: ARG, CUDA. */
+bltc_status bltc_server_create(const bltc_server_config* cfg, bltc_server** out);
+/* Queues one request.  x, y, z, q (inputs) and phi (output, n values in input order) are
+ * HOST pointers that the caller keeps valid until bltc_server_wait has returned for the
+ * ticket (pinned memory is faster).  params->precision must be BLTC_PRECISION_MIXED.
+ * Returns at once with *ticket.  Errors: ARG (bad sizes or parameters), OOM (the request
+ * alone exceeds the budget), STATE (server shutting down). */
+bltc_status bltc_server_submit(bltc_server* server, const double* x, const double* y,
+                               const double* z, const double* q, int64_t n,
+                               const bltc_params* params, double* phi, uint64_t* ticket);
+/* Waits for a request (timeout_s < 0: no limit), fills *info (may be NULL) and retires the
+ * ticket.  Returns the request's status; TIMEOUT if it is still running (the ticket stays
+ * valid); ARG for an unknown ticket. */
+bltc_status bltc_server_wait(bltc_server* server, uint64_t ticket, double timeout_s,
+                             bltc_request_info* info);
+/* Cancels a request that has not been admitted (its wait returns CANCELLED).  Errors: ARG
+ * (unknown ticket), STATE (already admitted). */
+bltc_status bltc_server_cancel(bltc_server* server, uint64_t ticket);
+bltc_status bltc_server_stats(bltc_server* server, bltc_server_counters* out);
+/* Cancels queued requests, lets admitted ones finish, stops the threads. */
+void bltc_server_destroy(bltc_server* server);
 
 #ifdef __cplusplus
 }

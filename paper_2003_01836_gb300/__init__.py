@@ -27,6 +27,7 @@ BLTC_ERR_OOM = -2
 BLTC_ERR_CUDA = -3
 BLTC_ERR_TIMEOUT = -4
 BLTC_ERR_STATE = -5
+BLTC_ERR_CANCELLED = -6
 BLTC_KERNEL_COULOMB = 0
 BLTC_KERNEL_YUKAWA = 1
 BLTC_PRECISION_FP64 = 0
@@ -34,7 +35,7 @@ BLTC_PRECISION_MIXED = 1
 BLTC_MAX_DEGREE = 16
 
 _STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
-           -5: "ERR_STATE"}
+           -5: "ERR_STATE", -6: "ERR_CANCELLED"}
 
 
 class BltcError(RuntimeError):
@@ -56,6 +57,25 @@ def params(degree=8, theta=0.7, leaf_size=2000, batch_size=None, kernel=BLTC_KER
     return bltc_params(int(degree), int(leaf_size),
                        int(leaf_size if batch_size is None else batch_size), int(kernel),
                        int(precision), 0, float(theta), float(kappa))
+
+
+class bltc_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("setup_workers", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class bltc_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("bytes_reserved", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_ready", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class bltc_server_counters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "submitted", "completed", "failed", "cancelled", "queued", "sweep_launches", "max_batch",
+        "budget_bytes", "reserved_bytes", "peak_reserved_bytes", "live_bytes", "peak_live_bytes")]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -98,6 +118,16 @@ _SIGNATURES = {
     "bltc_solve_host": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_direct_sum": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                         ctypes.c_int),
+    "bltc_autotune": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                       ctypes.c_int32, _P, _vp], ctypes.c_int),
+    "bltc_server_create": ([ctypes.POINTER(bltc_server_config), _pp], ctypes.c_int),
+    "bltc_server_submit": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, ctypes.POINTER(ctypes.c_uint64)],
+                           ctypes.c_int),
+    "bltc_server_wait": ([_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(bltc_request_info)],
+                         ctypes.c_int),
+    "bltc_server_cancel": ([_vp, ctypes.c_uint64], ctypes.c_int),
+    "bltc_server_stats": ([_vp, ctypes.POINTER(bltc_server_counters)], ctypes.c_int),
+    "bltc_server_destroy": ([_vp], None),
 }
 
 
@@ -339,6 +369,110 @@ def bltc_direct_sum(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):
     _check(ctx, lib().bltc_direct_sum(ctx, _ptr(tx), _ptr(ty), _ptr(tz), tx.numel(), _ptr(sx),
                                       _ptr(sy), _ptr(sz), _ptr(sq), sx.numel(), ctypes.byref(p),
                                       _ptr(phi)))
+
+
+def bltc_autotune(ctx, x, y, z, q, p: bltc_params, leaf=(500, 1000, 2000, 3000, 4000),
+                  batch=None, repeats=2, use_cache=True):
+    """Returns (best params, {(leaf, batch): fastest ms}) for the device system x, y, z, q."""
+    _stream(ctx)
+    L = np.ascontiguousarray(leaf, dtype=np.int32)
+    B = None if batch is None else np.ascontiguousarray(batch, dtype=np.int32)
+    ms = np.full(len(L), np.nan, dtype=np.float32)
+    best = bltc_params()
+    _check(ctx, lib().bltc_autotune(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.numel(),
+                                    ctypes.byref(p), L.ctypes.data,
+                                    None if B is None else B.ctypes.data, len(L), int(repeats),
+                                    1 if use_cache else 0, ctypes.byref(best), ms.ctypes.data))
+    keys = [(int(l), int(bb)) for l, bb in zip(L, L if B is None else B)]
+    return best, {k: float(v) for k, v in zip(keys, ms)}
+
+
+# ---- serving -------------------------------------------------------------------------
+
+def bltc_server_create(device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0):
+    cfg = bltc_server_config(int(device), int(setup_workers), int(max_batch), 0,
+                             int(hbm_budget_bytes))
+    h = ctypes.c_void_p()
+    st = lib().bltc_server_create(ctypes.byref(cfg), ctypes.byref(h))
+    if st != BLTC_OK:
+        raise BltcError(st, "server creation failed")
+    return h.value
+
+
+def bltc_server_submit(server, x, y, z, q, p: bltc_params, phi):
+    """Host arrays (contiguous float64); they must stay alive until bltc_server_wait returns."""
+    t = ctypes.c_uint64()
+    st = lib().bltc_server_submit(server, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.shape[0],
+                                  ctypes.byref(p), _ptr(phi), ctypes.byref(t))
+    if st != BLTC_OK:
+        raise BltcError(st, "submit rejected")
+    return t.value
+
+
+def bltc_server_wait(server, ticket, timeout_s=-1.0):
+    """Returns (status, info dict); status TIMEOUT leaves the ticket valid."""
+    info = bltc_request_info()
+    st = lib().bltc_server_wait(server, ticket, float(timeout_s), ctypes.byref(info))
+    return st, {k: getattr(info, k) for k, _ in bltc_request_info._fields_}
+
+
+def bltc_server_cancel(server, ticket):
+    st = lib().bltc_server_cancel(server, ticket)
+    if st != BLTC_OK:
+        raise BltcError(st, "cancel refused")
+
+
+def bltc_server_stats(server):
+    c = bltc_server_counters()
+    st = lib().bltc_server_stats(server, ctypes.byref(c))
+    if st != BLTC_OK:
+        raise BltcError(st, "stats failed")
+    return {k: getattr(c, k) for k, _ in bltc_server_counters._fields_}
+
+
+def bltc_server_destroy(server):
+    lib().bltc_server_destroy(server)
+
+
+class Server:
+    """Owns a serving runtime; keeps each request's host arrays alive until it is waited."""
+
+    def __init__(self, device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0):
+        self.h = bltc_server_create(device, setup_workers, max_batch, hbm_budget_bytes)
+        self._keep = {}
+
+    def submit(self, x, y, z, q, p, phi=None):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, q)]
+        if phi is None:
+            phi = np.empty(arrs[0].shape[0])
+        t = bltc_server_submit(self.h, *arrs, p, phi)
+        self._keep[t] = (arrs, phi)
+        return t
+
+    def wait(self, ticket, timeout_s=-1.0):
+        st, info = bltc_server_wait(self.h, ticket, timeout_s)
+        if st == BLTC_ERR_TIMEOUT:
+            return st, None, info
+        arrs, phi = self._keep.pop(ticket)
+        return st, phi, info
+
+    def cancel(self, ticket):
+        bltc_server_cancel(self.h, ticket)
+
+    def stats(self):
+        return bltc_server_stats(self.h)
+
+    def close(self):
+        if self.h:
+            bltc_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience owner of a context ----------------------------------------------------

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbltc.so")
 
-SOURCES = ["api.cu", "scan.cu", "tree.cu", "lists.cu", "upward.cu", "sweep.cu", "direct.cu"]
+SOURCES = ["api.cu", "scan.cu", "tree.cu", "lists.cu", "upward.cu", "sweep.cu", "direct.cu",
+           "server.cu"]
 NO_FMAD = {"tree.cu", "lists.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -3,13 +3,17 @@
 // the steps into Algorithm 1 (bltc_solve).
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
+#include <tuple>
 
 #include "internal.cuh"
 
 struct bltc_context {
     bltc::Context c;
+    // autotuner cache: (log2 n, degree, kernel, precision, theta * 1000) -> (leaf, batch)
+    std::map<std::tuple<int, int, int, int, int>, std::pair<int32_t, int32_t>> tuned;
 };
 struct bltc_tree {
     bltc::Tree t;
@@ -406,6 +410,71 @@ bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,
         solve_device(c, dx.p, dy.p, dz.p, dq.p, n, *params, dphi.p);
         BLTC_CUDA(cudaMemcpyAsync(phi, dphi.p, bytes, cudaMemcpyDeviceToHost, c->stream));
         BLTC_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, const double* z,
+                          const double* q, int64_t n, const bltc_params* params,
+                          const int32_t* leaf, const int32_t* batch, int32_t n_candidates,
+                          int32_t repeats, int32_t use_cache, bltc_params* best, float* ms) {
+    if (!ctx || !best) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(x && y && z && q, "autotune: NULL pointer");
+        require(n >= 1 && n < (int64_t(1) << 31), "autotune: n must be in [1, 2^31)");
+        require(leaf && n_candidates >= 1 && repeats >= 1, "autotune: need candidates and repeats");
+        for (int i = 0; i < n_candidates; ++i)
+            require(leaf[i] >= 1 && (!batch || batch[i] >= 1), "autotune: sizes must be >= 1");
+        int lg = 0;
+        while ((int64_t(1) << (lg + 1)) <= n) ++lg;
+        const auto key = std::make_tuple(lg, params->degree, params->kernel, params->precision,
+                                         static_cast<int>(std::lround(params->theta * 1000.0)));
+        *best = *params;
+        if (use_cache) {
+            auto it = ctx->tuned.find(key);
+            if (it != ctx->tuned.end()) {
+                best->leaf_size = it->second.first;
+                best->batch_size = it->second.second;
+                return;
+            }
+        }
+        Context* c = &ctx->c;
+        DBuf<double> phi(c, n);
+        cudaEvent_t e0, e1;
+        BLTC_CUDA(cudaEventCreate(&e0));
+        BLTC_CUDA(cudaEventCreate(&e1));
+        float best_ms = 3.0e38f;
+        try {
+            for (int i = 0; i < n_candidates; ++i) {
+                bltc_params p = *params;
+                p.leaf_size = leaf[i];
+                p.batch_size = batch ? batch[i] : leaf[i];
+                solve_device(c, x, y, z, q, n, p, phi.p);     // warm-up
+                float t_min = 3.0e38f;
+                for (int r = 0; r < repeats; ++r) {
+                    BLTC_CUDA(cudaEventRecord(e0, c->stream));
+                    solve_device(c, x, y, z, q, n, p, phi.p);
+                    BLTC_CUDA(cudaEventRecord(e1, c->stream));
+                    BLTC_CUDA(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    BLTC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                    t_min = std::min(t_min, t);
+                }
+                if (ms) ms[i] = t_min;
+                if (t_min < best_ms) {
+                    best_ms = t_min;
+                    best->leaf_size = p.leaf_size;
+                    best->batch_size = p.batch_size;
+                }
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->tuned[key] = {best->leaf_size, best->batch_size};
     });
 }
 

@@ -6,6 +6,7 @@
 
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "bltc.h"
 
@@ -144,6 +145,9 @@ struct Plan {
     DBuf<int4> items;                 // {batch, e0, e1, chunk}
     DBuf<int64_t> part_off;           // per batch: first partial
     DBuf<int32_t> n_chunks;           // per batch
+    DBuf<uint8_t> dir_sel;            // per direct entry: self-pair test needed (mixed sweep)
+    DBuf<float> dir_tau2;             // per direct entry: r^2 below which pairs are redone in FP64
+    std::vector<int64_t> h_cost;      // host copy of the items' interaction counts (queue order)
 };
 
 struct Lists {
@@ -168,6 +172,20 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
 void evaluate(Context* ctx, Lists* lists, const Tree* bt, const Tree* st,
               const bltc_params& p, double* phi);
 void interaction_counts(Context* ctx, const Lists* lists, int64_t* n_dir, int64_t* n_app);
+// Work plan of a list set (items, partial layout, self-pair flags); built once per degree.
+void build_plan(Context* ctx, Lists* L, int degree);
+void prepare_plan(Context* ctx, Lists* L, int degree);
+// One request of a multi-request sweep: its lists, trees, parameters and device phi.
+struct SweepJob {
+    Lists* L;
+    const Tree* bt;
+    const Tree* st;
+    bltc_params p;
+    double* phi;
+};
+// Mixed-precision sweep of several prepared requests in one persistent launch, then each
+// request's finalize; results are identical to evaluate() of each request alone.
+void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs);
 void direct_sum(Context* ctx, const double* tx, const double* ty, const double* tz,
                 int64_t nt, const double* sx, const double* sy, const double* sz,
                 const double* sq, int64_t ns, const bltc_params& p, double* phi);

@@ -1,8 +1,8 @@
 // lists.cu -- A1: interaction lists of every target batch (Algorithm 1, Eq. 13).
 //
-// For each batch B (leaf of the batch tree, DFS order) one thread walks ComputePotential
-// from the root of the source tree with an explicit stack, children pushed in reverse so
-// that they are visited in stored order, exactly like the recursion:
+// For each batch B (leaf of the batch tree, DFS order) one warp walks ComputePotential from
+// the root of the source tree with an explicit stack, children pushed in reverse so that
+// they are visited in stored order, exactly like the recursion:
 //   MAC passes ((r_B + r_C)/R < theta and (n+1)^3 < N_C)        -> approximation list
 //   geometric test fails ((r_B + r_C)/R not < theta): leaf       -> direct list
 //                                                     otherwise  -> the children
@@ -15,7 +15,7 @@
 namespace bltc {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 64;   // two warps (two batches) per block
 
 struct ListArgs {
     const int32_t* b_leaves;
@@ -28,6 +28,7 @@ struct ListArgs {
     const double* s_radius;
     int64_t n_batches;
     double theta;
+    double theta2;           // theta * theta
     int64_t P;
     int32_t* stack;          // n_batches * stack_cap
     int32_t stack_cap;
@@ -40,52 +41,83 @@ struct ListArgs {
     int32_t* overflow;
 };
 
+enum : int { kApprox = 0, kDirect = 1, kRecurse = 2 };
+
+// Algorithm 1's decision for batch B (centre cb, radius rB) and cluster C.
+__device__ __forceinline__ int classify(const ListArgs& a, double cbx, double cby, double cbz,
+                                        double rB, int C) {
+    const double dx = __dsub_rn(cbx, a.s_center[3 * C]);
+    const double dy = __dsub_rn(cby, a.s_center[3 * C + 1]);
+    const double dz = __dsub_rn(cbz, a.s_center[3 * C + 2]);
+    const double R2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double rs = __dadd_rn(rB, a.s_radius[C]);
+    // (r_B + r_C)/R < theta decided from squares when far from the boundary (each side
+    // carries a relative rounding error below 1e-15, so a 1e-10 margin cannot flip the
+    // decision); otherwise, and for R = 0 or non-finite values, the literal IEEE division
+    // and square root of the reading are evaluated.
+    const double lhs = __dmul_rn(rs, rs), rhs = __dmul_rn(a.theta2, R2);
+    const bool fast = rhs > 1e-290 && rhs < 1e300 && lhs < 1e300;   // normal range
+    bool geometric_ok;
+    if (fast && lhs < __dmul_rn(rhs, 1.0 - 1e-10))
+        geometric_ok = true;
+    else if (fast && lhs > __dmul_rn(rhs, 1.0 + 1e-10))
+        geometric_ok = false;
+    else
+        geometric_ok = __ddiv_rn(rs, __dsqrt_rn(R2)) < a.theta;
+    const bool size_ok = a.P < static_cast<int64_t>(a.s_count[C]);
+    if (geometric_ok && size_ok) return kApprox;
+    if (!geometric_ok) return a.s_nch[C] == 0 ? kDirect : kRecurse;
+    return kDirect;       // the ratio passes but (n+1)^3 >= N_C: the whole cluster directly
+}
+
+// One warp per batch.  The stack holds (cluster, decision); expanding a cluster decides all
+// of its children at once (one lane each) and pushes them in reverse so they pop in stored
+// order, which reproduces the recursion's visit order exactly.
 template <bool kFill>
 __global__ void k_lists(ListArgs a) {
-    const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     if (b >= a.n_batches) return;
     const int32_t B = a.b_leaves[b];
     const double cbx = a.b_center[3 * B], cby = a.b_center[3 * B + 1], cbz = a.b_center[3 * B + 2];
     const double rB = a.b_radius[B];
-    int32_t* st = a.stack + b * a.stack_cap;
+    int2* st = reinterpret_cast<int2*>(a.stack) + b * a.stack_cap;
     int sp = 0;
-    st[sp++] = 0;
+    if (lane == 0) st[0] = make_int2(0, classify(a, cbx, cby, cbz, rB, 0));
+    sp = 1;
+    __syncwarp();
     int32_t na = 0, nd = 0;
     int32_t* app = kFill ? a.app_ids + a.app_off[b] : nullptr;
     int32_t* dir = kFill ? a.dir_ids + a.dir_off[b] : nullptr;
+    bool overflow = false;
     while (sp > 0) {
-        const int32_t C = st[--sp];
-        const double dx = __dsub_rn(cbx, a.s_center[3 * C]);
-        const double dy = __dsub_rn(cby, a.s_center[3 * C + 1]);
-        const double dz = __dsub_rn(cbz, a.s_center[3 * C + 2]);
-        const double R = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                              __dmul_rn(dz, dz)));
-        const double ratio = __ddiv_rn(__dadd_rn(rB, a.s_radius[C]), R);
-        const bool geometric_ok = ratio < a.theta;
-        const bool size_ok = a.P < static_cast<int64_t>(a.s_count[C]);
-        if (geometric_ok && size_ok) {
-            if (kFill) app[na] = C;
+        const int2 top = st[--sp];
+        if (top.y == kApprox) {
+            if (kFill && lane == 0) app[na] = top.x;
             ++na;
-        } else if (!geometric_ok) {
-            const int k = a.s_nch[C];
-            if (k == 0) {
-                if (kFill) dir[nd] = C;
-                ++nd;
-            } else {
-                if (sp + k > a.stack_cap) {
-                    atomicExch(a.overflow, 1);
-                    break;
-                }
-                for (int c = k - 1; c >= 0; --c) st[sp++] = a.s_child[8 * C + c];
-            }
-        } else {
-            if (kFill) dir[nd] = C;
+        } else if (top.y == kDirect) {
+            if (kFill && lane == 0) dir[nd] = top.x;
             ++nd;
+        } else {
+            const int k = a.s_nch[top.x];
+            if (sp + k > a.stack_cap) {
+                overflow = true;
+                break;
+            }
+            if (lane < k) {
+                const int c = a.s_child[8 * top.x + lane];
+                st[sp + (k - 1 - lane)] = make_int2(c, classify(a, cbx, cby, cbz, rB, c));
+            }
+            sp += k;
+            __syncwarp();
         }
     }
-    if (!kFill) {
-        a.app_cnt[b] = na;
-        a.dir_cnt[b] = nd;
+    if (lane == 0) {
+        if (overflow) atomicExch(a.overflow, 1);
+        if (!kFill) {
+            a.app_cnt[b] = na;
+            a.dir_cnt[b] = nd;
+        }
     }
 }
 
@@ -121,9 +153,10 @@ void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int
     a.s_radius = st->radius.p;
     a.n_batches = nb;
     a.theta = theta;
+    a.theta2 = theta * theta;
     a.P = n1 * n1 * n1;
     a.stack_cap = 7 * st->n_levels + 8;
-    DBuf<int32_t> stack(ctx, nb * a.stack_cap);
+    DBuf<int32_t> stack(ctx, 2 * nb * a.stack_cap);     // int2 entries
     DBuf<int32_t> cnt(ctx, 2 * nb), flags(ctx, 4);
     out->app_off = DBuf<int32_t>(ctx, nb + 1);
     out->dir_off = DBuf<int32_t>(ctx, nb + 1);
@@ -132,7 +165,7 @@ void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int
     a.dir_cnt = cnt.p + nb;
     a.overflow = flags.p + 2;
     BLTC_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int32_t), s));
-    k_lists<false><<<grid_for(nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
+    k_lists<false><<<grid_for(32 * nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("lists count");
     exclusive_scan_i32(ctx, a.app_cnt, out->app_off.p, nb, flags.p);
     exclusive_scan_i32(ctx, a.dir_cnt, out->dir_off.p, nb, flags.p + 1);
@@ -149,7 +182,7 @@ void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int
     a.dir_off = out->dir_off.p;
     a.app_ids = out->app_ids.p;
     a.dir_ids = out->dir_ids.p;
-    k_lists<true><<<grid_for(nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
+    k_lists<true><<<grid_for(32 * nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("lists fill");
 }
 

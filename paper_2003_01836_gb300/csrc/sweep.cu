@@ -24,6 +24,7 @@
 // A pair with r^2 == 0 (a target meeting itself) is skipped; for the far field theta < 1
 // keeps every proxy point away from every target, so no test is needed there.
 #include <algorithm>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -34,8 +35,9 @@ constexpr int kThreads = 256;
 constexpr int kSrcTile32 = 2048;      // float4 sources per staged tile (32 KB)
 constexpr int kSrcTile64 = 1280;      // D4 sources per staged tile (40 KB)
 constexpr int kSmemBytes = 40960;     // also holds 3(n+1) + (n+1)^3 doubles for n <= 16
-constexpr int kItemsPerBlock = 12;    // work items per resident block (load balance)
+constexpr int kItemsPerBlock = 16;    // work items per resident block (load balance)
 constexpr int kBlock = 32;            // near-field FP32 block folded into a TwoSum accumulator
+constexpr int kFarEmuPairs = 0;       // far-field target pairs per k3 step using rsqrt2_fma
 
 struct SweepArgs {
     // target batches
@@ -60,12 +62,15 @@ struct SweepArgs {
     const int32_t* app_ids;
     const int32_t* dir_off;
     const int32_t* dir_ids;
+    const uint8_t* dir_sel;    // per direct entry: bit 0 = r^2 == 0 possible, bit 1 = close pairs possible
+    const float* dir_tau2;     // per direct entry: pairs closer than this (r^2) are redone in FP64
     const int4* items;
     const int64_t* part_off;
     double* partials;
     int n_items;
     unsigned int* counter;
     // kernel
+    int kernel;
     double kappa;
     float neg_kappa_log2e;
 };
@@ -116,6 +121,20 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// 1/sqrt(x) on the FMA pipe for two values: the magic-constant initial estimate of Lomont
+// ("Fast inverse square root", 2003) refined by three Newton-Raphson steps
+// y <- y (3/2 - (x/2) y^2), packed.  Used for a share of the far-field terms so that the SFU
+// and FMA pipes are loaded together; relative error within a few FP32 ulps for normal x.
+__device__ __forceinline__ float2 rsqrt2_fma(float2 x) {
+    const float2 nh = mul2(x, make_float2(-0.5f, -0.5f));
+    float2 y = make_float2(__int_as_float(0x5F375A86 - (__float_as_int(x.x) >> 1)),
+                           __int_as_float(0x5F375A86 - (__float_as_int(x.y) >> 1)));
+    const float2 c15 = make_float2(1.5f, 1.5f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y = mul2(y, fma2(nh, mul2(y, y), c15));
+    return y;
+}
+
 template <int KER>
 __device__ __forceinline__ float2 ri2_mixed(float2 r2, float nkl2e, bool skip_zero) {
     float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
@@ -130,20 +149,33 @@ __device__ __forceinline__ float2 ri2_mixed(float2 r2, float nkl2e, bool skip_ze
     return ri;
 }
 
-// Targets of one thread: T values per coordinate, relative to the batch centre.  For the
-// packed path they are kept negated in pairs: (-x[2v], -x[2v+1]).
-template <int T>
+// Targets of one thread: 8 values per coordinate relative to the batch centre, negated and
+// paired: (-x[2v], -x[2v+1]), so s - x is one packed add.
+constexpr int kT = 8;                 // targets per thread (even)
+constexpr int kH = kT / 2;
+constexpr int kMinBlocks = 2;         // resident blocks per SM the register budget must allow
 struct Targets {
-    float2 x[(T + 1) / 2], y[(T + 1) / 2], z[(T + 1) / 2];   // target u is component u % 2 of [u / 2]
+    float2 x[kH], y[kH], z[kH];
 };
+
+// Source groups.  A block is 256 threads x kT targets.  A batch of nb targets uses G groups
+// of 256/G threads (G = 1, 2, 4, 8 as nb shrinks below 256*kT, 128*kT, 64*kT): every group covers
+// all targets of the batch and takes every G-th block of work of each cluster (blocks of
+// kBlock sources in the near field, (k1, k2) rows of the proxy grid in the far field).  Each
+// group keeps its own partial potentials; they are added in group order at the end of the
+// item, so the result is fixed by the batch alone.
+__device__ __forceinline__ int groups_for(int nb) {
+    return nb > 128 * kT ? 1 : (nb > 64 * kT ? 2 : (nb > 32 * kT ? 4 : 8));
+}
 
 // Near field (Eq. 9) of cluster C.  Shared memory holds each staged source as two float4:
 // (x, x, y, y) and (z, z, q, q), relative to the batch centre, so a packed operand is one
 // aligned register pair.  Sums run over blocks of kBlock sources in FP32, folded into a
 // TwoSum accumulator, then into FP64 per staged tile.
-template <int KER, int T>
-__device__ void near_mixed(const SweepArgs& a, int C, const double cb[3], const Targets<T>& tg,
-                           double (&acc)[T], float4* sm) {
+template <int KER, bool SEL, bool CHECK>
+__device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double cb[3], const Targets& tg,
+                           double (&acc)[kT], float4* sm, int g, int G, int tb, int nb, int t0,
+                           int l, int tpg) {
     constexpr int kTile = kSrcTile32 / 2;
     const int cs = a.s_begin[C], nc = a.s_count[C];
     for (int j0 = 0; j0 < nc; j0 += kTile) {
@@ -159,63 +191,85 @@ __device__ void near_mixed(const SweepArgs& a, int C, const double cb[3], const 
             sm[2 * j + 1] = make_float4(sz, sz, sq, sq);
         }
         __syncthreads();
-        float hi[T], lo[T];
+        float hi[kT], lo[kT];
 #pragma unroll
-        for (int u = 0; u < T; ++u) hi[u] = lo[u] = 0.f;
-        for (int jb = 0; jb < m; jb += kBlock) {
+        for (int u = 0; u < kT; ++u) hi[u] = lo[u] = 0.f;
+        for (int jb = g * kBlock; jb < m; jb += G * kBlock) {
             const int je = min(jb + kBlock, m);
-            if constexpr (T == 1) {
-                float f = 0.f;
-#pragma unroll 4
-                for (int j = jb; j < je; ++j) {
-                    const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
-                    const float dx = p0.x + tg.x[0].x, dy = p0.z + tg.y[0].x, dz = p1.x + tg.z[0].x;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float ri = rsqrt_approx(r2);
-                    ri = r2 > 0.f ? ri : 0.f;
-                    if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
-                    f = fmaf(p1.z, ri, f);
-                }
-                two_sum_add(hi[0], lo[0], f);
-            } else {
-                constexpr int H = T / 2;
-                float2 f[H];
+            float2 f[kH];
 #pragma unroll
-                for (int v = 0; v < H; ++v) f[v] = make_float2(0.f, 0.f);
+            for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
+            float rmin = 3.0e38f;      // smallest non-zero r^2 this thread met in the block
 #pragma unroll 2
+            for (int j = jb; j < je; ++j) {
+                const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
+                const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
+                const float2 sz = make_float2(p1.x, p1.y), sq = make_float2(p1.z, p1.w);
+#pragma unroll
+                for (int v = 0; v < kH; ++v) {
+                    const float2 dx = add2(sx, tg.x[v]);
+                    const float2 dy = add2(sy, tg.y[v]);
+                    const float2 dz = add2(sz, tg.z[v]);
+                    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                    if (CHECK) {
+                        if (SEL) {
+                            rmin = fminf(rmin, r2.x > 0.f ? r2.x : 3.0e38f);
+                            rmin = fminf(rmin, r2.y > 0.f ? r2.y : 3.0e38f);
+                        } else {
+                            rmin = fminf(rmin, fminf(r2.x, r2.y));
+                        }
+                    }
+                    f[v] = fma2(sq, ri2_mixed<KER>(r2, a.neg_kappa_log2e, SEL), f[v]);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < kH; ++v) {
+                two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
+                two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
+            }
+            if (CHECK && rmin < tau2) {
+                // Close pairs: their FP32 distance carries the rounding of the batch-relative
+                // coordinates (about 2^-23 of the box extent), far too much relative to a tiny
+                // r.  Recompute those terms from the FP64 coordinates and add the difference.
                 for (int j = jb; j < je; ++j) {
                     const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
-                    const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
-                    const float2 sz = make_float2(p1.x, p1.y), sq = make_float2(p1.z, p1.w);
 #pragma unroll
-                    for (int v = 0; v < H; ++v) {
-                        const float2 dx = add2(sx, tg.x[v]);
-                        const float2 dy = add2(sy, tg.y[v]);
-                        const float2 dz = add2(sz, tg.z[v]);
-                        const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                        f[v] = fma2(sq, ri2_mixed<KER>(r2, a.neg_kappa_log2e, true), f[v]);
+                    for (int u = 0; u < kT; ++u) {
+                        const float2 ptx = tg.x[u / 2], pty = tg.y[u / 2], ptz = tg.z[u / 2];
+                        const float dx = p0.x + ((u & 1) ? ptx.y : ptx.x);
+                        const float dy = p0.z + ((u & 1) ? pty.y : pty.x);
+                        const float dz = p1.x + ((u & 1) ? ptz.y : ptz.x);
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (r2 > 0.f && r2 < tau2) {
+                            const int t = min(t0 + l + tpg * u, nb - 1);
+                            const int ps = cs + j0 + j;
+                            const double ex = a.sx[ps] - a.tx[tb + t], ey = a.sy[ps] - a.ty[tb + t];
+                            const double ez = a.sz[ps] - a.tz[tb + t];
+                            const double r2d = ex * ex + ey * ey + ez * ez;
+                            double rid = rsqrt(r2d);
+                            if (KER == BLTC_KERNEL_YUKAWA) rid *= exp(-a.kappa * (r2d * rid));
+                            float ri = rsqrt_approx(r2);
+                            if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
+                            const double corr = a.sq[ps] * rid - static_cast<double>(p1.z * ri);
+                            lo[u] += static_cast<float>(corr);
+                        }
                     }
-                }
-#pragma unroll
-                for (int v = 0; v < H; ++v) {
-                    two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
-                    two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
                 }
             }
         }
 #pragma unroll
-        for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
+        for (int u = 0; u < kT; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
     }
 }
 
 // Far field (Eq. 11) of cluster C on its tensor grid of Chebyshev points (Eq. 8).  Shared
 // memory holds (s, s) pairs of the 3(n+1) point coordinates relative to the batch centre,
-// then (qhat, qhat) pairs of the (n+1)^3 modified charges.  For each (k1, k2) the partial
-// r^2 of a target is reused over the n+1 values of k3; each (k1, k2) row of n+1 terms is
-// summed in FP32 and folded into a TwoSum accumulator.
-template <int KER, int T>
-__device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const Targets<T>& tg,
-                          double (&acc)[T], float2* sm) {
+// then (qhat, qhat) pairs of the (n+1)^3 modified charges.  Within a (k1, k2) row the
+// partial r^2 of a target is reused over the n+1 values of k3; each row is summed in FP32
+// and folded into a TwoSum accumulator.
+template <int KER>
+__device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const Targets& tg,
+                          double (&acc)[kT], float2* sm, int g, int G) {
     const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1;
     const float* qh = a.qhat32 + static_cast<int64_t>(a.qslot[C]) * P;
     __syncthreads();
@@ -234,72 +288,47 @@ __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const T
     const float2* sxp = sm;
     const float2* syp = sm + np1;
     const float2* szp = sm + 2 * np1;
-    float hi[T], lo[T];
+    float hi[kT], lo[kT];
 #pragma unroll
-    for (int u = 0; u < T; ++u) hi[u] = lo[u] = 0.f;
-    if constexpr (T == 1) {
-        for (int k1 = 0; k1 < np1; ++k1) {
-            const float dx = sxp[k1].x + tg.x[0].x;
-            const float dx2 = dx * dx;
-            for (int k2 = 0; k2 < np1; ++k2) {
-                const float dy = syp[k2].x + tg.y[0].x;
-                const float t = fmaf(dy, dy, dx2);
-                const float2* qrow = sq + (k1 * np1 + k2) * np1;
-                float f = 0.f;
+    for (int u = 0; u < kT; ++u) hi[u] = lo[u] = 0.f;
+    for (int row = g; row < np1 * np1; row += G) {
+        const int k1 = row / np1, k2 = row - k1 * np1;
+        const float2 sx = sxp[k1], sy = syp[k2];
+        float2 t[kH];
+#pragma unroll
+        for (int v = 0; v < kH; ++v) {
+            const float2 dx = add2(sx, tg.x[v]);
+            const float2 dy = add2(sy, tg.y[v]);
+            t[v] = fma2(dy, dy, mul2(dx, dx));
+        }
+        const float2* qrow = sq + row * np1;
+        float2 f[kH];
+#pragma unroll
+        for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
 #pragma unroll 3
-                for (int k3 = 0; k3 < np1; ++k3) {
-                    const float dz = szp[k3].x + tg.z[0].x;
-                    const float r2 = fmaf(dz, dz, t);
-                    f = fmaf(qrow[k3].x, ri_mixed<KER>(r2, a.neg_kappa_log2e), f);
-                }
-                two_sum_add(hi[0], lo[0], f);
+        for (int k3 = 0; k3 < np1; ++k3) {
+            const float2 sz = szp[k3], q = qrow[k3];
+#pragma unroll
+            for (int v = 0; v < kH; ++v) {
+                const float2 dz = add2(sz, tg.z[v]);
+                const float2 r2 = fma2(dz, dz, t[v]);
+                if (KER == BLTC_KERNEL_COULOMB && v >= kH - kFarEmuPairs)
+                    f[v] = fma2(q, rsqrt2_fma(r2), f[v]);
+                else
+                    f[v] = fma2(q, ri2_mixed<KER>(r2, a.neg_kappa_log2e, false), f[v]);
             }
         }
-    } else {
-        constexpr int H = T / 2;
-        for (int k1 = 0; k1 < np1; ++k1) {
-            float2 dx2[H];
-            const float2 sx = sxp[k1];
 #pragma unroll
-            for (int v = 0; v < H; ++v) {
-                const float2 dx = add2(sx, tg.x[v]);
-                dx2[v] = mul2(dx, dx);
-            }
-            for (int k2 = 0; k2 < np1; ++k2) {
-                float2 t[H];
-                const float2 sy = syp[k2];
-#pragma unroll
-                for (int v = 0; v < H; ++v) {
-                    const float2 dy = add2(sy, tg.y[v]);
-                    t[v] = fma2(dy, dy, dx2[v]);
-                }
-                const float2* qrow = sq + (k1 * np1 + k2) * np1;
-                float2 f[H];
-#pragma unroll
-                for (int v = 0; v < H; ++v) f[v] = make_float2(0.f, 0.f);
-#pragma unroll 3
-                for (int k3 = 0; k3 < np1; ++k3) {
-                    const float2 sz = szp[k3], q = qrow[k3];
-#pragma unroll
-                    for (int v = 0; v < H; ++v) {
-                        const float2 dz = add2(sz, tg.z[v]);
-                        const float2 r2 = fma2(dz, dz, t[v]);
-                        f[v] = fma2(q, ri2_mixed<KER>(r2, a.neg_kappa_log2e, false), f[v]);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < H; ++v) {
-                    two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
-                    two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
-                }
-            }
+        for (int v = 0; v < kH; ++v) {
+            two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
+            two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
         }
     }
 #pragma unroll
-    for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
+    for (int u = 0; u < kT; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
 }
 
-template <int KER, int T>
+template <int KER>
 __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
     const int b = it.x;
     const int B = a.b_leaves[b];
@@ -307,12 +336,15 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
     const double cb[3] = {a.b_center[3 * B], a.b_center[3 * B + 1], a.b_center[3 * B + 2]};
     const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
     double* out = a.partials + a.part_off[b] + static_cast<int64_t>(it.w) * nb;
-    for (int t0 = 0; t0 < nb; t0 += kThreads * T) {
-        Targets<T> tg;          // negated batch-relative coordinates: s + (-x) = s - x
-        double acc[T];
+    const int G = groups_for(nb);
+    const int tpg = kThreads / G;                       // threads per group
+    const int g = static_cast<int>(threadIdx.x) / tpg, l = static_cast<int>(threadIdx.x) - g * tpg;
+    for (int t0 = 0; t0 < nb; t0 += tpg * kT) {
+        Targets tg;
+        double acc[kT];
 #pragma unroll
-        for (int u = 0; u < T; ++u) {
-            const int t = min(t0 + static_cast<int>(threadIdx.x) + kThreads * u, nb - 1);
+        for (int u = 0; u < kT; ++u) {
+            const int t = min(t0 + l + tpg * u, nb - 1);
             const float nx = -__double2float_rn(a.tx[tb + t] - cb[0]);
             const float ny = -__double2float_rn(a.ty[tb + t] - cb[1]);
             const float nz = -__double2float_rn(a.tz[tb + t] - cb[2]);
@@ -329,20 +361,43 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
         }
         for (int e = it.y; e < it.z; ++e) {
             if (e < na)
-                far_mixed<KER, T>(a, a.app_ids[a0 + e], cb, tg, acc, reinterpret_cast<float2*>(sm));
-            else
-                near_mixed<KER, T>(a, a.dir_ids[d0 + e - na], cb, tg, acc, sm);
+                far_mixed<KER>(a, a.app_ids[a0 + e], cb, tg, acc, reinterpret_cast<float2*>(sm), g, G);
+            else {
+                const int de = d0 + e - na;
+                const int C = a.dir_ids[de];
+                const float tau2 = a.dir_tau2[de];
+                switch (a.dir_sel[de]) {
+                    case 0: near_mixed<KER, false, false>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                    case 2: near_mixed<KER, false, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                    default: near_mixed<KER, true, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                }
+            }
         }
+        if (G == 1) {
 #pragma unroll
-        for (int u = 0; u < T; ++u) {
-            const int t = t0 + static_cast<int>(threadIdx.x) + kThreads * u;
-            if (t < nb) out[t] = acc[u];
+            for (int u = 0; u < kT; ++u) {
+                const int t = t0 + l + tpg * u;
+                if (t < nb) out[t] = acc[u];
+            }
+        } else {
+            // add the groups' partials in group order
+            double* red = reinterpret_cast<double*>(sm);   // [G][tpg * kT]
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kT; ++u) red[g * tpg * kT + u * tpg + l] = acc[u];
+            __syncthreads();
+            for (int i = threadIdx.x; i < tpg * kT; i += kThreads) {
+                double s2 = red[i];
+                for (int gg = 1; gg < G; ++gg) s2 += red[gg * tpg * kT + i];
+                const int u = i / tpg, t = t0 + (i - u * tpg) + tpg * u;
+                if (t < nb) out[t] = s2;
+            }
         }
     }
 }
 
 template <int KER>
-__global__ void __launch_bounds__(kThreads, 2) k_sweep_mixed(SweepArgs a) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_mixed(SweepArgs a) {
     __shared__ __align__(16) float4 sm[kSmemBytes / sizeof(float4)];
     __shared__ int s_item;
     for (;;) {
@@ -351,16 +406,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_mixed(SweepArgs a) {
         __syncthreads();
         const int i = s_item;
         if (i >= a.n_items) return;
-        const int4 it = a.items[i];
-        const int nb = a.b_count[a.b_leaves[it.x]];
-        if (nb <= kThreads)
-            item_mixed<KER, 1>(a, it, sm);
-        else if (nb <= 2 * kThreads)
-            item_mixed<KER, 2>(a, it, sm);
-        else if (nb <= 4 * kThreads)
-            item_mixed<KER, 4>(a, it, sm);
-        else
-            item_mixed<KER, 8>(a, it, sm);
+        item_mixed<KER>(a, a.items[i], sm);
+    }
+}
+
+// Several requests' sweeps in one persistent launch (the serving engine).  `order` lists
+// (request, item) pairs longest first; each block copies the request's arguments to shared
+// memory when the request changes.  An item computes exactly what it computes in a
+// single-request launch, so every request's potentials are the same bits alone or in a mix.
+template <int KER>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_multi(const SweepArgs* __restrict__ reqs,
+                                                             const int2* __restrict__ order,
+                                                             int total, unsigned int* counter) {
+    __shared__ __align__(16) float4 sm[kSmemBytes / sizeof(float4)];
+    __shared__ __align__(16) SweepArgs s_a;
+    __shared__ int s_item;
+    int cur = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(counter, 1u));
+        __syncthreads();
+        const int i = s_item;
+        if (i >= total) return;
+        const int2 o = order[i];
+        if (o.x != cur) {
+            const int* src = reinterpret_cast<const int*>(reqs + o.x);
+            int* dst = reinterpret_cast<int*>(&s_a);
+            for (int w = threadIdx.x; w < static_cast<int>(sizeof(SweepArgs) / sizeof(int)); w += kThreads) dst[w] = src[w];
+            cur = o.x;
+            __syncthreads();
+        }
+        item_mixed<KER>(s_a, s_a.items[o.y], sm);
     }
 }
 
@@ -507,7 +583,59 @@ struct PlanArgs {
     int64_t* part_len;           // per batch: n_chunks * nb
     const int32_t* item_off;     // pass 2
     int4* items;
+    // boxes for the self-pair test
+    const double* b_lo;
+    const double* b_hi;
+    const double* b_center;
+    const double* s_lo;
+    const double* s_hi;
+    uint8_t* dir_sel;
+    float* dir_tau2;
 };
+
+// Marks the direct entries where the mixed sweep must test r^2 == 0.  A target t of batch B
+// and a source s of cluster C enter the sweep as fp32(t - c_B) and fp32(s - c_B); each
+// rounding moves a coordinate by at most half an FP32 ulp of M, the largest |coordinate -
+// c_B| over both boxes in that dimension.  If the boxes are separated in some dimension by
+// more than M * 2^-20 (eight ulps) and by more than 1e-18 (so that the squared difference
+// stays a normal float), every such pair has a non-zero FP32 difference there, r^2 > 0, and
+// the test can be skipped.  Everything else (in particular a batch against itself) keeps
+// the test.
+__global__ void k_dir_flags(PlanArgs a, int64_t n_dir) {
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n_dir) return;
+    // the batch owning entry e: the last b with dir_off[b] <= e
+    int64_t lo = 0, hi = a.n_batches;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a.dir_off[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int B = a.b_leaves[lo];
+    const int C = a.dir_ids[e];
+    bool separated = false;
+    double Mmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double bl = a.b_lo[3 * B + d], bh = a.b_hi[3 * B + d];
+        const double cl = a.s_lo[3 * C + d], ch = a.s_hi[3 * C + d];
+        const double c = a.b_center[3 * B + d];
+        const double gap = fmax(cl - bh, bl - ch);
+        const double M = fmax(fmax(fabs(bl - c), fabs(bh - c)), fmax(fabs(cl - c), fabs(ch - c)));
+        if (gap > M * 9.5367431640625e-07 && gap > 1e-18) separated = true;
+        Mmax = fmax(Mmax, M);
+    }
+    // Pairs closer than tau = M/64 are recomputed in FP64 by the mixed sweep (their FP32
+    // relative error would exceed about 2^-23 * 64 * sqrt(3) ~ 1.3e-5).  Only entries whose
+    // boxes come within 1.01 tau of each other can hold such pairs.
+    const double tau = Mmax * 0.015625;
+    double d2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double gap = fmax(fmax(a.s_lo[3 * C + d] - a.b_hi[3 * B + d], a.b_lo[3 * B + d] - a.s_hi[3 * C + d]), 0.0);
+        d2 += gap * gap;
+    }
+    const bool close = d2 <= 1.0201 * tau * tau;
+    a.dir_sel[e] = static_cast<uint8_t>((separated ? 0 : 1) | (close ? 2 : 0));
+    a.dir_tau2[e] = static_cast<float>(tau * tau);
+}
 
 __global__ void k_batch_cost(PlanArgs a) {
     const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -550,6 +678,20 @@ __global__ void k_chunks(PlanArgs a) {
     }
 }
 
+// Interaction count of each item (for longest-first ordering).
+__global__ void k_item_costs(PlanArgs a, const int4* __restrict__ items, int64_t n_items,
+                             int64_t* cost) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_items) return;
+    const int4 it = items[i];
+    const int b = it.x;
+    const int64_t nb = a.b_count[a.b_leaves[b]];
+    const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
+    int64_t c = 0;
+    for (int e = it.y; e < it.z; ++e) c += e < na ? a.P : static_cast<int64_t>(a.s_count[a.dir_ids[d0 + e - na]]);
+    cost[i] = c * nb;
+}
+
 __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* __restrict__ b_begin,
                            const int32_t* __restrict__ b_count, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ n_chunks, const int64_t* __restrict__ part_off,
@@ -577,6 +719,8 @@ __global__ void k_counts(const int32_t* b_leaves, const int32_t* b_count, const 
     atomicAdd(&out[1], static_cast<unsigned long long>(static_cast<int64_t>(app_off[b + 1] - app_off[b]) * P * nb));
 }
 
+}  // namespace
+
 void build_plan(Context* ctx, Lists* L, int degree) {
     cudaStream_t s = ctx->stream;
     const int64_t nb = L->n_batches;
@@ -598,7 +742,7 @@ void build_plan(Context* ctx, Lists* L, int degree) {
     k_batch_cost<<<grid_for(nb, 128), 128, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("plan cost");
     const int64_t total = ctx->read_words(words.p, 1)[0];
-    const int64_t blocks = 2 * static_cast<int64_t>(std::max(1, ctx->sm_count));
+    const int64_t blocks = kMinBlocks * static_cast<int64_t>(std::max(1, ctx->sm_count));
     a.cut = std::max<int64_t>(total / (blocks * kItemsPerBlock), int64_t(1) << 20);
     pl.n_chunks = DBuf<int32_t>(ctx, nb);
     pl.part_off = DBuf<int64_t>(ctx, nb);
@@ -617,14 +761,51 @@ void build_plan(Context* ctx, Lists* L, int degree) {
     a.items = pl.items.p;
     k_chunks<true><<<grid_for(nb, 128), 128, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("plan items");
+    // Longest-first order (LPT): the persistent sweep takes items in queue order, so the
+    // short ones fill the gaps at the end.  The order does not change any result (each item
+    // writes its own partials); ties keep batch order (stable sort).
+    if (pl.n_items > 1) {
+        DBuf<int64_t> cost(ctx, pl.n_items);
+        k_item_costs<<<grid_for(pl.n_items, 256), 256, 0, s>>>(a, pl.items.p, pl.n_items, cost.p); ++ctx->launches;
+        BLTC_LAUNCH_CHECK("plan costs");
+        std::vector<int4> h_items(static_cast<size_t>(pl.n_items));
+        std::vector<int64_t> h_cost(static_cast<size_t>(pl.n_items));
+        BLTC_CUDA(cudaMemcpyAsync(h_items.data(), pl.items.p, sizeof(int4) * pl.n_items, cudaMemcpyDeviceToHost, s));
+        BLTC_CUDA(cudaMemcpyAsync(h_cost.data(), cost.p, sizeof(int64_t) * pl.n_items, cudaMemcpyDeviceToHost, s));
+        BLTC_CUDA(cudaStreamSynchronize(s));
+        std::vector<int64_t> order(static_cast<size_t>(pl.n_items));
+        for (int64_t i = 0; i < pl.n_items; ++i) order[static_cast<size_t>(i)] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int64_t x, int64_t y) { return h_cost[static_cast<size_t>(x)] > h_cost[static_cast<size_t>(y)]; });
+        std::vector<int4> sorted(static_cast<size_t>(pl.n_items));
+        for (int64_t i = 0; i < pl.n_items; ++i) sorted[static_cast<size_t>(i)] = h_items[static_cast<size_t>(order[static_cast<size_t>(i)])];
+        BLTC_CUDA(cudaMemcpyAsync(pl.items.p, sorted.data(), sizeof(int4) * pl.n_items, cudaMemcpyHostToDevice, s));
+        BLTC_CUDA(cudaStreamSynchronize(s));
+        pl.h_cost.resize(static_cast<size_t>(pl.n_items));
+        for (int64_t i = 0; i < pl.n_items; ++i) pl.h_cost[static_cast<size_t>(i)] = h_cost[static_cast<size_t>(order[static_cast<size_t>(i)])];
+    } else {
+        pl.h_cost.assign(static_cast<size_t>(pl.n_items), 1);
+    }
+    pl.dir_sel = DBuf<uint8_t>(ctx, L->n_dir);
+    pl.dir_tau2 = DBuf<float>(ctx, L->n_dir);
+    a.dir_tau2 = pl.dir_tau2.p;
+    a.b_lo = L->bt->lo.p;
+    a.b_hi = L->bt->hi.p;
+    a.b_center = L->bt->center.p;
+    a.s_lo = L->st->lo.p;
+    a.s_hi = L->st->hi.p;
+    a.dir_sel = pl.dir_sel.p;
+    if (L->n_dir > 0) {
+        k_dir_flags<<<grid_for(L->n_dir, 256), 256, 0, s>>>(a, L->n_dir); ++ctx->launches;
+    }
+    BLTC_LAUNCH_CHECK("plan flags");
     pl.degree = degree;
     pl.valid = true;
 }
 
-}  // namespace
 
-void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
-              double* phi) {
+static void check_eval(const Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
+                       const double* phi) {
     if (L->bt != bt || L->st != st)
         throw Error(BLTC_ERR_STATE, "evaluate: lists were built for other trees");
     if (L->degree != p.degree)
@@ -635,13 +816,11 @@ void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc
     if (st->q_lists != 0 && st->q_lists != L->serial)
         throw Error(BLTC_ERR_STATE, "evaluate: modified charges were computed for other lists");
     require(phi != nullptr, "evaluate: phi is NULL");
-    cudaStream_t s = ctx->stream;
-    if (!L->plan.valid || L->plan.degree != p.degree) build_plan(ctx, L, p.degree);
-    Plan& pl = L->plan;
-    DBuf<double> partials(ctx, pl.partial_len);
-    DBuf<unsigned int> counter(ctx, 1);
-    BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
+}
 
+static SweepArgs make_args(Context* ctx, const Lists* L, const Tree* bt, const Tree* st,
+                           const bltc_params& p, double* partials, unsigned int* counter) {
+    const Plan& pl = L->plan;
     SweepArgs a{};
     a.b_leaves = bt->leaves.p;
     a.b_begin = bt->begin.p;
@@ -667,30 +846,49 @@ void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc
     a.app_ids = L->app_ids.p;
     a.dir_off = L->dir_off.p;
     a.dir_ids = L->dir_ids.p;
+    a.dir_sel = pl.dir_sel.p;
+    a.dir_tau2 = pl.dir_tau2.p;
     a.items = pl.items.p;
     a.part_off = pl.part_off.p;
-    a.partials = partials.p;
+    a.partials = partials;
     a.n_items = static_cast<int>(pl.n_items);
-    a.counter = counter.p;
+    a.counter = counter;
+    a.kernel = p.kernel;
     const double kappa = p.kernel == BLTC_KERNEL_YUKAWA ? p.kappa : 0.0;
     a.kappa = kappa;
     a.neg_kappa_log2e = static_cast<float>(-kappa * 1.4426950408889634);
+    return a;
+}
+
+void prepare_plan(Context* ctx, Lists* L, int degree) {
+    if (!L->plan.valid || L->plan.degree != degree) build_plan(ctx, L, degree);
+}
+
+void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
+              double* phi) {
+    check_eval(L, bt, st, p, phi);
+    cudaStream_t s = ctx->stream;
+    prepare_plan(ctx, L, p.degree);
+    Plan& pl = L->plan;
+    DBuf<double> partials(ctx, pl.partial_len);
+    DBuf<unsigned int> counter(ctx, 1);
+    BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
+    const SweepArgs a = make_args(ctx, L, bt, st, p, partials.p, counter.p);
+    const int per_sm = p.precision == BLTC_PRECISION_MIXED ? kMinBlocks : 2;
     const unsigned grid = static_cast<unsigned>(
-        std::min<int64_t>(pl.n_items, 2 * static_cast<int64_t>(std::max(1, ctx->sm_count))));
+        std::min<int64_t>(pl.n_items, per_sm * static_cast<int64_t>(std::max(1, ctx->sm_count))));
     ctx->mark(Context::kSweepBegin);
     if (pl.n_items > 0) {
         if (p.precision == BLTC_PRECISION_MIXED) {
             if (p.kernel == BLTC_KERNEL_YUKAWA) {
                 k_sweep_mixed<BLTC_KERNEL_YUKAWA><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
-            }
-            else {
+            } else {
                 k_sweep_mixed<BLTC_KERNEL_COULOMB><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
             }
         } else {
             if (p.kernel == BLTC_KERNEL_YUKAWA) {
                 k_sweep_fp64<BLTC_KERNEL_YUKAWA><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
-            }
-            else {
+            } else {
                 k_sweep_fp64<BLTC_KERNEL_COULOMB><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
             }
         }
@@ -702,6 +900,70 @@ void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc
         partials.p, phi); ++ctx->launches;
     BLTC_LAUNCH_CHECK("finalize");
     ctx->mark(Context::kEnd);
+}
+
+void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
+    if (jobs.empty()) return;
+    cudaStream_t s = ctx->stream;
+    const int R = static_cast<int>(jobs.size());
+    std::vector<DBuf<double>> partials;
+    std::vector<SweepArgs> args;
+    partials.reserve(jobs.size());
+    args.reserve(jobs.size());
+    DBuf<unsigned int> counter(ctx, 1);
+    BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
+    // global longest-first order over all requests' items
+    std::vector<std::pair<int64_t, int2>> all;
+    for (int r = 0; r < R; ++r) {
+        const SweepJob& j = jobs[static_cast<size_t>(r)];
+        require(j.p.precision == BLTC_PRECISION_MIXED, "serving runs the mixed-precision sweep");
+        check_eval(j.L, j.bt, j.st, j.p, j.phi);
+        if (!j.L->plan.valid || j.L->plan.degree != j.p.degree)
+            throw Error(BLTC_ERR_STATE, "evaluate_multi: request has no work plan");
+        const Plan& pl = j.L->plan;
+        partials.emplace_back(ctx, pl.partial_len);
+        args.push_back(make_args(ctx, j.L, j.bt, j.st, j.p, partials.back().p, counter.p));
+        for (int64_t i = 0; i < pl.n_items; ++i)
+            all.push_back({pl.h_cost[static_cast<size_t>(i)], make_int2(r, static_cast<int>(i))});
+    }
+    std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int2>& x,
+                                                const std::pair<int64_t, int2>& y) { return x.first > y.first; });
+    // one persistent launch per kernel type present (each instantiation keeps its registers)
+    std::vector<int2> order[2];
+    for (const auto& pr : all) order[jobs[static_cast<size_t>(pr.second.x)].p.kernel == BLTC_KERNEL_YUKAWA].push_back(pr.second);
+    DBuf<SweepArgs> d_args(ctx, R);
+    DBuf<int2> d_order(ctx, static_cast<int64_t>(all.size()));
+    DBuf<unsigned int> counter2(ctx, 1);
+    BLTC_CUDA(cudaMemsetAsync(counter2.p, 0, sizeof(unsigned int), s));
+    BLTC_CUDA(cudaMemcpyAsync(d_args.p, args.data(), sizeof(SweepArgs) * R, cudaMemcpyHostToDevice, s));
+    if (!order[0].empty())
+        BLTC_CUDA(cudaMemcpyAsync(d_order.p, order[0].data(), sizeof(int2) * order[0].size(), cudaMemcpyHostToDevice, s));
+    if (!order[1].empty())
+        BLTC_CUDA(cudaMemcpyAsync(d_order.p + order[0].size(), order[1].data(), sizeof(int2) * order[1].size(),
+                                  cudaMemcpyHostToDevice, s));
+    // the host vectors must outlive the asynchronous copies
+    BLTC_CUDA(cudaStreamSynchronize(s));
+    const int64_t cap = kMinBlocks * static_cast<int64_t>(std::max(1, ctx->sm_count));
+    if (!order[0].empty()) {
+        const int total = static_cast<int>(order[0].size());
+        k_sweep_multi<BLTC_KERNEL_COULOMB><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, 0, s>>>(
+            d_args.p, d_order.p, total, counter.p); ++ctx->launches;
+        BLTC_LAUNCH_CHECK("sweep multi coulomb");
+    }
+    if (!order[1].empty()) {
+        const int total = static_cast<int>(order[1].size());
+        k_sweep_multi<BLTC_KERNEL_YUKAWA><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, 0, s>>>(
+            d_args.p, d_order.p + order[0].size(), total, counter2.p); ++ctx->launches;
+        BLTC_LAUNCH_CHECK("sweep multi yukawa");
+    }
+    for (int r = 0; r < R; ++r) {
+        const SweepJob& j = jobs[static_cast<size_t>(r)];
+        const Plan& pl = j.L->plan;
+        k_finalize<<<static_cast<unsigned>(j.L->n_batches), 256, 0, s>>>(
+            j.bt->leaves.p, j.bt->begin.p, j.bt->count.p, j.bt->perm.p, pl.n_chunks.p, pl.part_off.p,
+            partials[static_cast<size_t>(r)].p, j.phi); ++ctx->launches;
+        BLTC_LAUNCH_CHECK("finalize multi");
+    }
 }
 
 void interaction_counts(Context* ctx, const Lists* L, int64_t* n_dir, int64_t* n_app) {

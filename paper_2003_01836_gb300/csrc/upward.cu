@@ -64,9 +64,18 @@ __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
     const bool active = tid < pairs * G;
     const int p = tid % pairs, g = tid / pairs;
     const int k1 = p / np1, k2 = p % np1;
-    F acc[kMaxNp1];
+    // Per-thread sums over its particles: blocks of the tile summed in F, folded into a
+    // TwoSum (hi, lo) accumulator so FP32 rounding does not grow with the particle count.
+    F acc[kMaxNp1], lo_acc[kMaxNp1];
 #pragma unroll
-    for (int k = 0; k < kMaxNp1; ++k) acc[k] = F(0);
+    for (int k = 0; k < kMaxNp1; ++k) acc[k] = lo_acc[k] = F(0);
+    // the 3(n+1) Chebyshev points of this cluster, once per block
+    __shared__ double s_pts[3 * kMaxNp1];
+    if (tid < 3 * np1) {
+        const int d = tid / np1, k = tid - d * np1;
+        s_pts[tid] = cheb_point(a.cheb_t, k, n, d == 0 ? lo[0] : (d == 1 ? lo[1] : lo[2]),
+                                d == 0 ? hi[0] : (d == 1 ? hi[1] : hi[2]));
+    }
 
     for (int j0 = it.y; j0 < it.z; j0 += kTile) {
         const int m = min(kTile, it.z - j0);
@@ -76,17 +85,19 @@ __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
             if (j < m) {
                 const int pos = j0 + j;
                 const double yv = d == 0 ? a.px[pos] : (d == 1 ? a.py[pos] : a.pz[pos]);
-                const double lod = d == 0 ? lo[0] : (d == 1 ? lo[1] : lo[2]);
-                const double hid = d == 0 ? hi[0] : (d == 1 ? hi[1] : hi[2]);
+                const double* pts = s_pts + d * np1;
                 const double qv = d == 0 ? a.pq[pos] : 1.0;
                 double dk[kMaxNp1];
                 int hit = -1;
 #pragma unroll
                 for (int k = 0; k < kMaxNp1; ++k) {
                     if (k < np1) {
-                        dk[k] = yv - cheb_point(a.cheb_t, k, n, lod, hid);
-                        bool h = fabs(dk[k]) < 2.2250738585072014e-308;
-                        if (sizeof(F) == 4) h = h || fabsf(static_cast<float>(dk[k])) < 1.17549435e-38f;
+                        dk[k] = yv - pts[k];
+                        // FP64: |y - s_k| < DBL_MIN.  Mixed: the FP32 difference underflows
+                        // (|fp32(y - s_k)| < FLT_MIN), a superset changing L by < 1e-29.
+                        const bool h = sizeof(F) == 4
+                                           ? fabsf(__double2float_rn(dk[k])) < 1.17549435e-38f
+                                           : fabs(dk[k]) < 2.2250738585072014e-308;
                         if (h && hit < 0) hit = k;
                     }
                 }
@@ -97,16 +108,25 @@ __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
                         if (k < np1) row[k * stride] = k == hit ? F(qv) : F(0);
                 } else {
                     F raw[kMaxNp1];
-                    F den = F(0);
+                    F den = F(0), den_lo = F(0);
 #pragma unroll
                     for (int k = 0; k < kMaxNp1; ++k) {
                         if (k < np1) {
                             const F w = ((k == 0 || k == n) ? F(0.5) : F(1)) * ((k & 1) ? F(-1) : F(1));
                             raw[k] = w / F(dk[k]);
-                            den += raw[k];
+                            if (sizeof(F) == 4) {
+                                // the barycentric denominator by TwoSum: its terms alternate
+                                // in sign, and a plain FP32 sum loses digits to cancellation
+                                const F s = den + raw[k];
+                                const F bb = s - den;
+                                den_lo += (den - (s - bb)) + (raw[k] - bb);
+                                den = s;
+                            } else {
+                                den += raw[k];
+                            }
                         }
                     }
-                    const F scale = F(qv) / den;
+                    const F scale = F(qv) / (den + den_lo);
 #pragma unroll
                     for (int k = 0; k < kMaxNp1; ++k)
                         if (k < np1) row[k * stride] = raw[k] * scale;
@@ -118,11 +138,32 @@ __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
             const F* f0 = fac + k1 * stride;
             const F* f1 = fac + (np1 + k2) * stride;
             const F* f2 = fac + 2 * np1 * stride;
-            for (int j = g; j < m; j += G) {
-                const F a12 = f0[j] * f1[j];
+            if constexpr (sizeof(F) == 4) {
+                F blk[kMaxNp1];
 #pragma unroll
-                for (int k = 0; k < kMaxNp1; ++k)
-                    if (k < np1) acc[k] += a12 * f2[k * stride + j];
+                for (int k = 0; k < kMaxNp1; ++k) blk[k] = F(0);
+                for (int j = g; j < m; j += G) {
+                    const F a12 = f0[j] * f1[j];
+#pragma unroll
+                    for (int k = 0; k < kMaxNp1; ++k)
+                        if (k < np1) blk[k] += a12 * f2[k * stride + j];
+                }
+#pragma unroll
+                for (int k = 0; k < kMaxNp1; ++k) {
+                    if (k < np1) {
+                        const F s = acc[k] + blk[k];
+                        const F bb = s - acc[k];
+                        lo_acc[k] += (acc[k] - (s - bb)) + (blk[k] - bb);
+                        acc[k] = s;
+                    }
+                }
+            } else {
+                for (int j = g; j < m; j += G) {
+                    const F a12 = f0[j] * f1[j];
+#pragma unroll
+                    for (int k = 0; k < kMaxNp1; ++k)
+                        if (k < np1) acc[k] += a12 * f2[k * stride + j];
+                }
             }
         }
     }
@@ -132,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
     if (active) {
 #pragma unroll
         for (int k = 0; k < kMaxNp1; ++k)
-            if (k < np1) red[g * P + p * np1 + k] = acc[k];
+            if (k < np1) red[g * P + p * np1 + k] = acc[k] + lo_acc[k];
     }
     __syncthreads();
     double* out = a.partial + static_cast<int64_t>(blockIdx.x) * P;

@@ -229,6 +229,28 @@ def test_degree16_sampled(gpu):
     assert_close_abs(got64, gotmx, np.abs(got64).max() * np.ones_like(got64), MIXED_REL2, 1e-3, "n=16 mixed")
 
 
+def test_close_pairs_mixed(gpu):
+    # Near-duplicates 1e-7..1e-5 apart: the FP32 batch-relative coordinates cannot resolve
+    # them, so the mixed near field must recompute such pairs in FP64.
+    rng = np.random.default_rng(4)
+    x, y, z, q = system("cube", 200000, 77)
+    k = 2000
+    pick = rng.choice(len(x), k, replace=False)
+    d = rng.normal(size=(3, k))
+    d *= (10 ** rng.uniform(-7, -5, k)) / np.linalg.norm(d, axis=0)
+    x = np.concatenate([x, x[pick] + d[0]])
+    y = np.concatenate([y, y[pick] + d[1]])
+    z = np.concatenate([z, z[pick] + d[2]])
+    q = np.concatenate([q, rng.uniform(-1, 1, k)])
+    got64 = gpu_solve(gpu, x, y, z, q, b.params(6, 0.7, 1000, precision=b.BLTC_PRECISION_FP64))
+    gotmx = gpu_solve(gpu, x, y, z, q, b.params(6, 0.7, 1000))
+    e = oracle.rel_err(got64, gotmx)
+    assert e <= MIXED_REL2, e
+    # per target, relative to its own potential (or the rms, where the potential cancels)
+    scale = np.maximum(np.abs(got64), np.sqrt(np.mean(got64 ** 2)))
+    assert np.max(np.abs(gotmx - got64) / scale) < 2e-5
+
+
 def test_theta_zero_is_direct_sum(gpu):
     x, y, z, q = system("cube", 6000, 99)
     pts = np.stack([x, y, z])

@@ -1,0 +1,109 @@
+"""The serving runtime (continuous batching): requests of uneven size and parameters are
+admitted by an HBM budget, prepared by setup workers and swept together; each result must
+be bit-identical to bltc_solve of the same request alone, and the runtime's memory must
+stay within its budget."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2003_01836_gb300 as b
+from gpu_helpers import gpu_solve, system
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(k, seed, nmax_exp=5.0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(k):
+        n = int(round(10 ** rng.uniform(3.0, nmax_exp)))
+        kind = "cube" if rng.random() < 0.5 else "plummer"
+        ker = int(rng.random() < 0.5)
+        kappa = float(rng.uniform(0.1, 1.0)) if ker else 0.0
+        theta = float(rng.uniform(0.5, 0.8))
+        deg = int(rng.choice([4, 6, 8, 10]))
+        leaf = int(rng.choice([500, 1000, 2000]))
+        x, y, z, q = system(kind, n, 20031840 + 10000 * i + seed)
+        out.append((x, y, z, q, b.params(deg, theta, leaf, leaf, ker, kappa, b.BLTC_PRECISION_MIXED)))
+    return out
+
+
+def test_served_results_equal_solo(gpu):
+    reqs = _requests(24, 1)
+    solo = [gpu_solve(gpu, *r) for r in reqs]
+    srv = b.Server(0, setup_workers=3, max_batch=16)
+    try:
+        tickets = [srv.submit(*r) for r in reqs]
+        outs = [srv.wait(t) for t in tickets]
+        for i, ((st, phi, info), ref) in enumerate(zip(outs, solo)):
+            assert st == b.BLTC_OK, (i, st)
+            assert np.array_equal(phi, ref), f"request {i} differs from its solo solve"
+            assert info["t_submit"] <= info["t_admit"] <= info["t_ready"] <= info["t_done"]
+        s = srv.stats()
+        assert s["completed"] == 24 and s["failed"] == 0
+        assert s["max_batch"] > 1, "requests were never swept together"
+        assert s["peak_live_bytes"] <= s["budget_bytes"]
+        assert s["live_bytes"] == 0 and s["reserved_bytes"] == 0
+    finally:
+        srv.close()
+
+
+def test_served_small_requests_match_oracle(gpu):
+    reqs = [r for r in _requests(10, 2, nmax_exp=3.7)][:6]
+    srv = b.Server(0, setup_workers=2, max_batch=8)
+    try:
+        tickets = [srv.submit(*r) for r in reqs]
+        for (x, y, z, q, p), t in zip(reqs, tickets):
+            st, phi, _ = srv.wait(t)
+            assert st == b.BLTC_OK
+            ref, _, _ = oracle.bltc(x, y, z, q, p.theta, p.degree, p.leaf_size, p.batch_size,
+                                    p.kernel, p.kappa)
+            assert oracle.rel_err(ref, phi) <= 1e-6
+    finally:
+        srv.close()
+
+
+def test_budget_admission_and_cancel(gpu):
+    reqs = _requests(8, 3, nmax_exp=4.5)
+    # a budget that holds about one request at a time: admission serialises them
+    big = max(400 * r[0].shape[0] for r in reqs) + (40 << 20)
+    srv = b.Server(0, setup_workers=2, max_batch=8, hbm_budget_bytes=big * 1.3)
+    try:
+        tickets = [srv.submit(*r) for r in reqs]
+        cancelled = False
+        try:
+            srv.cancel(tickets[-1])
+            cancelled = True
+        except b.BltcError as e:
+            assert e.status == b.BLTC_ERR_STATE       # already admitted
+        for i, t in enumerate(tickets):
+            st, phi, info = srv.wait(t)
+            if i == len(tickets) - 1 and cancelled:
+                assert st == b.BLTC_ERR_CANCELLED
+                continue
+            assert st == b.BLTC_OK
+            assert np.array_equal(phi, gpu_solve(gpu, *reqs[i]))
+        s = srv.stats()
+        assert s["peak_reserved_bytes"] <= s["budget_bytes"]
+        assert s["peak_live_bytes"] <= s["budget_bytes"]
+        # a request larger than the whole budget is refused at submission
+        x, y, z, q = system("cube", 2_000_000, 5)
+        with pytest.raises(b.BltcError) as e:
+            srv.submit(x, y, z, q, b.params(8, 0.7, 2000))
+        assert e.value.status == b.BLTC_ERR_OOM
+    finally:
+        srv.close()
+
+
+def test_submit_rejects_bad_parameters(gpu):
+    srv = b.Server(0, setup_workers=1, max_batch=2)
+    try:
+        x, y, z, q = system("cube", 100, 1)
+        for bad in (b.params(0, 0.7, 10), b.params(8, 1.2, 10), b.params(8, 0.7, 10, precision=0)):
+            with pytest.raises(b.BltcError) as e:
+                srv.submit(x, y, z, q, bad)
+            assert e.value.status == b.BLTC_ERR_ARG
+        st, _ = b.bltc_server_wait(srv.h, 12345)    # unknown ticket
+        assert st == b.BLTC_ERR_ARG
+    finally:
+        srv.close()
