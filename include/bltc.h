@@ -230,6 +230,27 @@ bltc_status bltc_direct_sum(bltc_context* ctx, const double* tx, const double* t
                             const double* sz, const double* sq, int64_t ns,
                             const bltc_params* params, double* phi);
 
+/* bltc_direct_sum for callers that cannot allocate device memory: applications whose device
+ * heap belongs to another allocator (a host framework's pool, a fixed arena) and that may
+ * not call cudaMalloc or free memory behind it.  This entry point allocates nothing: the
+ * per-split partial sums go to a fixed scratch array of 64 MiB (8,388,608 doubles) compiled
+ * into the library, which every GPU that loads the library holds until the process exits.
+ * No counterpart in the paper.
+ *   - Same arguments, results and tolerances as bltc_direct_sum; the caller still passes
+ *     the inputs and phi.  nt must be at most 8,388,608 (else BLTC_ERR_ARG); the number of
+ *     source splits is limited so that splits * nt partial sums fit the scratch.
+ *   - The first call on a device looks up the scratch's device address once (with that
+ *     device current); make that first call before any stream capture.
+ *   - Every call on a device shares the one scratch array: calls that overlap on the GPU
+ *     (two streams, or two contexts at once) race and corrupt each other's sums; serialise
+ *     them.  The array keeps the last call's contents; every partial sum a call reads is
+ *     written by that same call, so nothing needs clearing.
+ * Errors: ARG, CUDA. */
+bltc_status bltc_direct_sum_noalloc(bltc_context* ctx, const double* tx, const double* ty,
+                                    const double* tz, int64_t nt, const double* sx,
+                                    const double* sy, const double* sz, const double* sq,
+                                    int64_t ns, const bltc_params* params, double* phi);
+
 /* ---- serving: continuous batching of many requests on one GPU -------------------- */
 /* Not in the paper (which runs one system per rank); the runtime that keeps the GPU busy
  * with a stream of independent particle systems of uneven size.  Each request is the whole

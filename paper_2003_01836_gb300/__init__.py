@@ -118,6 +118,8 @@ _SIGNATURES = {
     "bltc_solve_host": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_direct_sum": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                         ctypes.c_int),
+    "bltc_direct_sum_noalloc": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
+                                ctypes.c_int),
     "bltc_autotune": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                        ctypes.c_int32, _P, _vp], ctypes.c_int),
     "bltc_server_create": ([ctypes.POINTER(bltc_server_config), _pp], ctypes.c_int),
@@ -473,6 +475,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def bltc_direct_sum_noalloc(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):
+    """bltc_direct_sum without any device allocation (fixed 64 MiB library scratch; calls
+    on one device must not overlap on the GPU; at most 8,388,608 targets)."""
+    _stream(ctx)
+    _check(ctx, lib().bltc_direct_sum_noalloc(ctx, _ptr(tx), _ptr(ty), _ptr(tz), tx.numel(),
+                                              _ptr(sx), _ptr(sy), _ptr(sz), _ptr(sq), sx.numel(),
+                                              ctypes.byref(p), _ptr(phi)))
 
 
 # ---- convenience owner of a context ----------------------------------------------------

@@ -478,6 +478,23 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
     });
 }
 
+bltc_status bltc_direct_sum_noalloc(bltc_context* ctx, const double* tx, const double* ty,
+                                    const double* tz, int64_t nt, const double* sx, const double* sy,
+                                    const double* sz, const double* sq, int64_t ns,
+                                    const bltc_params* params, double* phi) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        require(params != nullptr, "params is NULL");
+        require(params->kernel == BLTC_KERNEL_COULOMB || params->kernel == BLTC_KERNEL_YUKAWA,
+                "unknown kernel");
+        require(params->kernel != BLTC_KERNEL_YUKAWA || (std::isfinite(params->kappa) && params->kappa >= 0.0),
+                "kappa must be finite and >= 0");
+        require(params->precision == BLTC_PRECISION_FP64 || params->precision == BLTC_PRECISION_MIXED,
+                "unknown precision");
+        direct_sum_noalloc(&ctx->c, tx, ty, tz, nt, sx, sy, sz, sq, ns, *params, phi);
+    });
+}
+
 bltc_status bltc_direct_sum(bltc_context* ctx, const double* tx, const double* ty, const double* tz,
                             int64_t nt, const double* sx, const double* sy, const double* sz,
                             const double* sq, int64_t ns, const bltc_params* params, double* phi) {

@@ -8,6 +8,7 @@
 // in order, so the result does not depend on scheduling.  MIXED evaluates in FP32 on the
 // coordinates rounded once from FP64, sums each staged tile in FP32 and tiles in FP64.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -159,6 +160,30 @@ __global__ void k_direct_reduce(const double* __restrict__ partial, int64_t nt, 
     }
 }
 
+// Scratch of bltc_direct_sum_noalloc: the per-split partial sums live in this fixed
+// file-scope array instead of memory from an allocator.  Every GPU that loads the library
+// holds it (64 MiB) until the process exits.
+constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 23;
+__device__ __align__(256) double g_direct_scratch[kNoAllocScratchDoubles];
+
+// Device address of g_direct_scratch on `device`, looked up once per device with that device
+// current (host code must not use the symbol itself as a device pointer).
+double* direct_scratch_address(int device) {
+    static std::mutex mu;
+    static double* addr[256] = {};
+    if (device < 0 || device >= 256) throw Error(BLTC_ERR_ARG, "direct noalloc: device out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_direct_scratch);
+        if (e != cudaSuccess)
+            throw Error(BLTC_ERR_CUDA, std::string("cudaGetSymbolAddress(g_direct_scratch): ") +
+                                           cudaGetErrorString(e));
+        addr[device] = static_cast<double*>(p);
+    }
+    return addr[device];
+}
+
 }  // namespace
 
 void direct_sum(Context* ctx, const double* tx, const double* ty, const double* tz, int64_t nt,
@@ -200,6 +225,48 @@ void direct_sum(Context* ctx, const double* tx, const double* ty, const double* 
     BLTC_LAUNCH_CHECK("direct");
     k_direct_reduce<<<grid_for(nt, 256, 4096), 256, 0, s>>>(partial.p, nt, static_cast<int>(splits), phi); ++ctx->launches;
     BLTC_LAUNCH_CHECK("direct reduce");
+}
+
+void direct_sum_noalloc(Context* ctx, const double* tx, const double* ty, const double* tz,
+                        int64_t nt, const double* sx, const double* sy, const double* sz,
+                        const double* sq, int64_t ns, const bltc_params& p, double* phi) {
+    require(nt >= 1 && ns >= 1, "direct noalloc: nt and ns must be >= 1");
+    require(tx && ty && tz && sx && sy && sz && sq && phi, "direct noalloc: NULL pointer");
+    require(nt <= kNoAllocScratchDoubles,
+            "direct noalloc: nt exceeds the scratch capacity of 8388608 targets");
+    double* scratch = direct_scratch_address(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const bool mixed = p.precision == BLTC_PRECISION_MIXED;
+    const int T = mixed ? 8 : 4;
+    const int64_t tiles = ceil_div(nt, static_cast<int64_t>(kThreads) * T);
+    const int64_t want = 4 * static_cast<int64_t>(std::max(1, ctx->sm_count));
+    const int64_t tile_src = mixed ? kTile32 : kTile64;
+    // as many source splits as the fixed scratch holds (splits * nt partial sums)
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, tiles), ceil_div(ns, tile_src)));
+    splits = std::min<int64_t>({splits, int64_t(65535), kNoAllocScratchDoubles / nt});
+    const int64_t per = ceil_div(ceil_div(ns, splits), tile_src) * tile_src;
+    splits = ceil_div(ns, per);
+    DirectArgs a{tx, ty, tz, sx, sy, sz, sq, nt, ns, per, scratch, 0.0, 0.f};
+    const double kappa = p.kernel == BLTC_KERNEL_YUKAWA ? p.kappa : 0.0;
+    a.kappa = kappa;
+    a.neg_kappa_log2e = static_cast<float>(-kappa * 1.4426950408889634);
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(splits));
+    if (mixed) {
+        if (p.kernel == BLTC_KERNEL_YUKAWA)
+            k_direct_mixed<BLTC_KERNEL_YUKAWA, 8><<<grid, kThreads, 0, s>>>(a);
+        else
+            k_direct_mixed<BLTC_KERNEL_COULOMB, 8><<<grid, kThreads, 0, s>>>(a);
+    } else {
+        if (p.kernel == BLTC_KERNEL_YUKAWA)
+            k_direct_fp64<BLTC_KERNEL_YUKAWA, 4><<<grid, kThreads, 0, s>>>(a);
+        else
+            k_direct_fp64<BLTC_KERNEL_COULOMB, 4><<<grid, kThreads, 0, s>>>(a);
+    }
+    ++ctx->launches;
+    BLTC_LAUNCH_CHECK("direct noalloc");
+    k_direct_reduce<<<grid_for(nt, 256, 4096), 256, 0, s>>>(scratch, nt, static_cast<int>(splits), phi);
+    ++ctx->launches;
+    BLTC_LAUNCH_CHECK("direct noalloc reduce");
 }
 
 }  // namespace bltc

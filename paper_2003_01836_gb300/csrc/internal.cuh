@@ -190,6 +190,11 @@ void direct_sum(Context* ctx, const double* tx, const double* ty, const double* 
                 int64_t nt, const double* sx, const double* sy, const double* sz,
                 const double* sq, int64_t ns, const bltc_params& p, double* phi);
 
+// bltc_direct_sum without any allocation: partial sums in a fixed file-scope device array.
+void direct_sum_noalloc(Context* ctx, const double* tx, const double* ty, const double* tz,
+                        int64_t nt, const double* sx, const double* sy, const double* sz,
+                        const double* sq, int64_t ns, const bltc_params& p, double* phi);
+
 // ---- device-wide exclusive scan (scan.cu) -------------------------------------------
 // out[i] = sum_{j<i} in[i]; *total (device, may be null) = sum of all.
 void exclusive_scan_i32(Context* ctx, const int32_t* in, int32_t* out, int64_t n,
