@@ -16,6 +16,7 @@
 // Only clusters that some batch approximates need modified charges (a cluster's charges
 // do not depend on which batches use it).
 #include <algorithm>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -210,14 +211,15 @@ __global__ void k_mark_by_size(const int32_t* __restrict__ count, int64_t m, int
 }
 
 __global__ void k_slots(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
-                        const int32_t* __restrict__ count, int64_t m, int32_t* qslot,
-                        int32_t* slot_node, int32_t* slot_items) {
+                        const int32_t* __restrict__ count, const int32_t* __restrict__ nch,
+                        int64_t m, int32_t* qslot, int32_t* slot_node, int32_t* slot_items) {
     int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (v >= m) return;
     if (flag[v]) {
         qslot[v] = pos[v];
         slot_node[pos[v]] = static_cast<int32_t>(v);
-        slot_items[pos[v]] = (count[v] + kItem - 1) / kItem;
+        // particles are summed only at the leaves; parents come from their children (M2M)
+        slot_items[pos[v]] = nch[v] == 0 ? (count[v] + kItem - 1) / kItem : 0;
     } else {
         qslot[v] = -1;
     }
@@ -230,11 +232,139 @@ __global__ void k_items(const int32_t* __restrict__ slot_node,
     if (s >= n_slots) return;
     const int v = slot_node[s];
     const int b = begin[v], c = count[v];
-    for (int i = item0[s], p0 = b; p0 < b + c; ++i, p0 += kItem)
+    // a slot owns items item0[s] .. item0[s+1]-1: none for internal nodes (built by M2M)
+    const int i1 = item0[s + 1];
+    for (int i = item0[s], p0 = b; i < i1; ++i, p0 += kItem)
         items[i] = make_int4(static_cast<int>(s), p0, min(b + c, p0 + kItem), 0);
 }
 
 __global__ void k_append_total(int32_t* off, int64_t n, const int32_t* total) { off[n] = *total; }
+
+// Clusters whose modified charges the M2M pass needs: the marked ones and, level by level,
+// every descendant of a marked one (a parent's charges are built from all of its children).
+__global__ void k_propagate(const int32_t* __restrict__ level, const int32_t* __restrict__ parent,
+                            int64_t m, int L, int32_t* flag) {
+    int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v < m && level[v] == L && flag[parent[v]]) flag[v] = 1;
+}
+
+// Marked internal nodes grouped by level (order within a level is irrelevant).
+__global__ void k_level_hist(const int32_t* __restrict__ flag, const int32_t* __restrict__ nch,
+                             const int32_t* __restrict__ level, int64_t m, int32_t* hist) {
+    int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v < m && flag[v] && nch[v] > 0) atomicAdd(&hist[level[v]], 1);
+}
+
+__global__ void k_level_fill(const int32_t* __restrict__ flag, const int32_t* __restrict__ nch,
+                             const int32_t* __restrict__ level, int64_t m,
+                             const int32_t* __restrict__ level_off, int32_t* cursor, int32_t* list) {
+    int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v < m && flag[v] && nch[v] > 0) {
+        const int L = level[v];
+        list[level_off[L] + atomicAdd(&cursor[L], 1)] = static_cast<int32_t>(v);
+    }
+}
+
+struct M2MArgs {
+    const int32_t* nch;
+    const int32_t* child;
+    const int32_t* qslot;
+    const double* lo;
+    const double* hi;
+    const double* cheb_t;
+    double* qhat64;
+    float* qhat32;
+    int np1;
+};
+
+// Exact transfer of the children's modified charges to their parent (NEXT to Eq. 12: the
+// parent's Lagrange polynomials L^P_k have degree n in each variable, so a child's tensor
+// interpolant reproduces them exactly and
+//   qhat^P_k = sum_children sum_k' L^P_k1(s^c_k'1) L^P_k2(s^c_k'2) L^P_k3(s^c_k'3) qhat^c_k').
+// One block per parent: for each child, the three (n+1)x(n+1) matrices T_l[k][k'] =
+// L^P_k(s^c_k'l) (barycentric form, exact hits as in Sec. II-C), then three mode products.
+// FP64 throughout.
+__global__ void __launch_bounds__(256) k_m2m(M2MArgs a, const int32_t* __restrict__ nodes) {
+    extern __shared__ __align__(16) double m2m_smem[];
+    const int v = nodes[blockIdx.x];
+    const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1, n2 = np1 * np1;
+    double* A = m2m_smem;            // child charges, then the second mode product
+    double* Bm = A + P;              // first mode product
+    double* out = Bm + P;            // the parent's charges
+    double* T = out + P;             // [3][np1][np1]
+    double* sp = T + 3 * n2;         // parent points [3][np1]
+    const int tid = threadIdx.x;
+    if (tid < 3 * np1) {
+        const int d = tid / np1, k = tid - d * np1;
+        sp[tid] = cheb_point(a.cheb_t, k, n, a.lo[3 * v + d], a.hi[3 * v + d]);
+    }
+    for (int i = tid; i < P; i += blockDim.x) out[i] = 0.0;
+    const int nc = a.nch[v];
+    for (int ci = 0; ci < nc; ++ci) {
+        const int c = a.child[8 * v + ci];
+        __syncthreads();
+        const double* qc = a.qhat64 + static_cast<int64_t>(a.qslot[c]) * P;
+        for (int i = tid; i < P; i += blockDim.x) A[i] = qc[i];
+        if (tid < 3 * np1) {
+            // column k' of T_d: the parent's 1-D Lagrange values at the child's point s^c_k'
+            const int d = tid / np1, kp = tid - d * np1;
+            const double y = cheb_point(a.cheb_t, kp, n, a.lo[3 * c + d], a.hi[3 * c + d]);
+            const double* s = sp + d * np1;
+            double* col = T + d * n2 + kp;            // T_d[k][kp] at col[k * np1]
+            int hit = -1;
+            for (int k = 0; k < np1; ++k)
+                if (hit < 0 && fabs(y - s[k]) < 2.2250738585072014e-308) hit = k;
+            if (hit >= 0) {
+                for (int k = 0; k < np1; ++k) col[k * np1] = k == hit ? 1.0 : 0.0;
+            } else {
+                double den = 0.0;
+                for (int k = 0; k < np1; ++k) {
+                    const double w = ((k == 0 || k == n) ? 0.5 : 1.0) * ((k & 1) ? -1.0 : 1.0);
+                    den += w / (y - s[k]);
+                }
+                for (int k = 0; k < np1; ++k) {
+                    const double w = ((k == 0 || k == n) ? 0.5 : 1.0) * ((k & 1) ? -1.0 : 1.0);
+                    col[k * np1] = (w / (y - s[k])) / den;
+                }
+            }
+        }
+        __syncthreads();
+        // B[k1,k2',k3'] = sum_k1' T1[k1][k1'] A[k1',k2',k3']
+        for (int i = tid; i < P; i += blockDim.x) {
+            const int k1 = i / n2, r = i - k1 * n2;
+            double acc = 0.0;
+            for (int j = 0; j < np1; ++j) acc += T[k1 * np1 + j] * A[j * n2 + r];
+            Bm[i] = acc;
+        }
+        __syncthreads();
+        // C[k1,k2,k3'] = sum_k2' T2[k2][k2'] B[k1,k2',k3']   (into A)
+        for (int i = tid; i < P; i += blockDim.x) {
+            const int k1 = i / n2, r = i - k1 * n2, k2 = r / np1, k3 = r - k2 * np1;
+            double acc = 0.0;
+            for (int j = 0; j < np1; ++j) acc += T[n2 + k2 * np1 + j] * Bm[k1 * n2 + j * np1 + k3];
+            A[i] = acc;
+        }
+        __syncthreads();
+        // out[k1,k2,k3] += sum_k3' T3[k3][k3'] C[k1,k2,k3']
+        for (int i = tid; i < P; i += blockDim.x) {
+            const int k3 = i % np1, base = i - k3;
+            double acc = 0.0;
+            for (int j = 0; j < np1; ++j) acc += T[2 * n2 + k3 * np1 + j] * A[base + j];
+            out[i] += acc;
+        }
+    }
+    __syncthreads();
+    double* q = a.qhat64 + static_cast<int64_t>(a.qslot[v]) * P;
+    for (int i = tid; i < P; i += blockDim.x) {
+        q[i] = out[i];
+        if (a.qhat32) a.qhat32[static_cast<int64_t>(a.qslot[v]) * P + i] = static_cast<float>(out[i]);
+    }
+}
+
+size_t m2m_smem_bytes(int np1) {
+    const size_t P = static_cast<size_t>(np1) * np1 * np1;
+    return sizeof(double) * (3 * P + 3 * static_cast<size_t>(np1) * np1 + 3 * np1);
+}
 
 template <typename F>
 size_t upward_smem(int np1) {
@@ -271,6 +401,10 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
         k_mark_by_size<<<grid_for(m, 256), 256, 0, s>>>(st->count.p, m, P, flag.p); ++ctx->launches;
     }
     BLTC_LAUNCH_CHECK("upward mark");
+    for (int L = 1; L < st->n_levels; ++L) {
+        k_propagate<<<grid_for(m, 256), 256, 0, s>>>(st->level.p, st->parent.p, m, L, flag.p); ++ctx->launches;
+    }
+    BLTC_LAUNCH_CHECK("upward propagate");
     exclusive_scan_i32(ctx, flag.p, pos.p, m, tot.p);
     const int32_t n_slots = *reinterpret_cast<const int32_t*>(ctx->read_words(tot.p, 1));
 
@@ -284,14 +418,14 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
                      ? DBuf<float>(ctx, static_cast<int64_t>(n_slots) * P)
                      : DBuf<float>();
     DBuf<int32_t> slot_node(ctx, n_slots), slot_items(ctx, n_slots), item0(ctx, n_slots + 1);
-    k_slots<<<grid_for(m, 256), 256, 0, s>>>(flag.p, pos.p, st->count.p, m, st->qslot.p,
+    k_slots<<<grid_for(m, 256), 256, 0, s>>>(flag.p, pos.p, st->count.p, st->nch.p, m, st->qslot.p,
                                              slot_node.p, slot_items.p); ++ctx->launches;
     BLTC_LAUNCH_CHECK("upward slots");
     if (n_slots == 0) return;
     exclusive_scan_i32(ctx, slot_items.p, item0.p, n_slots, tot.p + 1);
     k_append_total<<<1, 1, 0, s>>>(item0.p, n_slots, tot.p + 1); ++ctx->launches;
     const int32_t n_items = reinterpret_cast<const int32_t*>(ctx->read_words(tot.p, 1))[1];
-    DBuf<int4> items(ctx, n_items);
+    DBuf<int4> items(ctx, std::max<int32_t>(n_items, 1));
     k_items<<<grid_for(n_slots, 128), 128, 0, s>>>(slot_node.p, item0.p, st->begin.p,
                                                    st->count.p, n_slots, items.p); ++ctx->launches;
     DBuf<double> partial(ctx, static_cast<int64_t>(n_items) * P);
@@ -310,24 +444,55 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
     a.items = items.p;
     a.partial = partial.p;
     a.np1 = np1;
-    if (precision == BLTC_PRECISION_MIXED) {
-        const size_t sm = upward_smem<float>(np1);
-        BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<float>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sm)));
-        k_upward_partial<float><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
-    } else {
-        const size_t sm = upward_smem<double>(np1);
-        BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sm)));
-        k_upward_partial<double><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
+    if (n_items > 0) {
+        if (precision == BLTC_PRECISION_MIXED) {
+            const size_t sm = upward_smem<float>(np1);
+            BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<float>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(sm)));
+            k_upward_partial<float><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
+        } else {
+            const size_t sm = upward_smem<double>(np1);
+            BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<double>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(sm)));
+            k_upward_partial<double><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
+        }
+        BLTC_LAUNCH_CHECK("upward partial");
     }
-    BLTC_LAUNCH_CHECK("upward partial");
     k_upward_reduce<<<n_slots, 256, 0, s>>>(partial.p, item0.p, P, st->qhat64.p,
                                              precision == BLTC_PRECISION_MIXED ? st->qhat32.p
                                                                                : nullptr); ++ctx->launches;
     BLTC_LAUNCH_CHECK("upward reduce");
+    // M2M: marked internal nodes, deepest level first
+    const int nl = st->n_levels;
+    if (nl > 1) {
+        DBuf<int32_t> hist(ctx, 2 * nl + 1), list(ctx, m);
+        BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * (2 * nl + 1), s));
+        k_level_hist<<<grid_for(m, 256), 256, 0, s>>>(flag.p, st->nch.p, st->level.p, m, hist.p); ++ctx->launches;
+        std::vector<int32_t> h(static_cast<size_t>(nl));
+        BLTC_CUDA(cudaMemcpyAsync(h.data(), hist.p, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, s));
+        BLTC_CUDA(cudaStreamSynchronize(s));
+        std::vector<int32_t> off(static_cast<size_t>(nl) + 1, 0);
+        for (int L = 0; L < nl; ++L) off[L + 1] = off[L] + h[L];
+        if (off[nl] > 0) {
+            BLTC_CUDA(cudaMemcpyAsync(hist.p + nl, off.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, s));
+            BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * nl, s));
+            k_level_fill<<<grid_for(m, 256), 256, 0, s>>>(flag.p, st->nch.p, st->level.p, m, hist.p + nl,
+                                                          hist.p, list.p); ++ctx->launches;
+            BLTC_CUDA(cudaStreamSynchronize(s));     // `off` lives on the host stack
+            M2MArgs ma{st->nch.p, st->child.p, st->qslot.p, st->lo.p, st->hi.p, a.cheb_t, st->qhat64.p,
+                       precision == BLTC_PRECISION_MIXED ? st->qhat32.p : nullptr, np1};
+            const size_t sm = m2m_smem_bytes(np1);
+            BLTC_CUDA(cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(sm)));
+            for (int L = nl - 1; L >= 0; --L) {
+                if (h[L] == 0) continue;
+                k_m2m<<<h[L], 256, sm, s>>>(ma, list.p + off[L]); ++ctx->launches;
+            }
+            BLTC_LAUNCH_CHECK("upward m2m");
+        }
+    }
 }
 
 }  // namespace bltc
