@@ -87,6 +87,11 @@ def _load():
                                     c.c_int32, c.c_int32, c.c_int32, c.c_double, c.c_int32,
                                     c.c_void_p, c.c_int64, _f64, c.c_void_p, _f64]
         lib.oracle_bltc.restype = c.c_int
+        lib.oracle_bltc_ts.argtypes = [_f64, _f64, _f64, c.c_int64, _f64, _f64, _f64, _f64,
+                                       c.c_int64, c.c_double, c.c_int32, c.c_int32, c.c_int32,
+                                       c.c_int32, c.c_double, c.c_int32, c.c_void_p, c.c_int64,
+                                       _f64, c.c_void_p, _f64]
+        lib.oracle_bltc_ts.restype = c.c_int
         lib.oracle_max_threads.restype = c.c_int
         _lib = lib
         return lib
@@ -233,6 +238,30 @@ def bltc(x, y, z, q, theta, degree, leaf_size, batch_size, kernel=KERNEL_COULOMB
                          None if phi_abs is None else phi_abs.ctypes.data, tm)
     if rc:
         raise ValueError(f"oracle_bltc failed ({rc})")
+    return phi, phi_abs, {"setup": tm[0], "precompute": tm[1], "compute": tm[2]}
+
+
+def bltc_ts(targets, sources, q, theta, degree, leaf_size, batch_size,
+            kernel=KERNEL_COULOMB, kappa=0.0, threads=0, batches=None, with_abs=False):
+    """Algorithm 1 for distinct target and source sets: ``targets`` = (tx, ty, tz),
+    ``sources`` = (sx, sy, sz) with charges ``q``.  Source tree with ``leaf_size``, target
+    batch tree with ``batch_size``.  Returns (phi[nt], phi_abs or None, timings)."""
+    lib = _load()
+    tx, ty, tz = (_c(a) for a in targets)
+    sx, sy, sz = (_c(a) for a in sources)
+    q = _c(q)
+    nt, ns = tx.shape[0], sx.shape[0]
+    phi = np.empty(nt)
+    phi_abs = np.empty(nt) if with_abs else None
+    tm = np.zeros(3)
+    sub = None if batches is None else _c(batches, np.int64)
+    rc = lib.oracle_bltc_ts(tx, ty, tz, nt, sx, sy, sz, q, ns, float(theta), int(degree),
+                            int(leaf_size), int(batch_size), int(kernel), float(kappa),
+                            int(threads), None if sub is None else sub.ctypes.data,
+                            0 if sub is None else sub.shape[0], phi,
+                            None if phi_abs is None else phi_abs.ctypes.data, tm)
+    if rc:
+        raise ValueError(f"oracle_bltc_ts failed ({rc})")
     return phi, phi_abs, {"setup": tm[0], "precompute": tm[1], "compute": tm[2]}
 
 

@@ -601,24 +601,27 @@ static double now_seconds(void)
 #endif
 }
 
-/* Algorithm 1.  Targets and sources are the same particles (x, y, z, q), as in all of the
- * paper's runs.  The source tree uses leaf_size (N_L) and the batch tree batch_size (N_B).
- * If batch_subset is non-NULL, only those batches (indices into the DFS-ordered leaves of
- * the batch tree) are evaluated; phi of the other targets is left at 0.  timings receives
- * setup (trees), precompute (modified charges) and compute seconds. */
-int oracle_bltc(const double* x, const double* y, const double* z, const double* q, int64_t n,
-                double theta, int32_t degree, int32_t leaf_size, int32_t batch_size,
-                int32_t kernel, double kappa, int32_t threads, const int64_t* batch_subset,
-                int64_t n_subset, double* phi, double* phi_abs, double* timings)
+/* Algorithm 1 for nt targets (tx, ty, tz) and ns sources (sx, sy, sz, sq), which may be
+ * different particle sets (Sec. II: the method needs only the target and source
+ * positions).  The source tree uses leaf_size (N_L), the batch tree of the targets
+ * batch_size (N_B).  If batch_subset is non-NULL, only those batches (indices into the
+ * DFS-ordered leaves of the batch tree) are evaluated; phi of the other targets is left at 0.
+ * timings receives setup (trees), precompute (modified charges) and compute seconds. */
+int oracle_bltc_ts(const double* tx, const double* ty, const double* tz, int64_t nt,
+                   const double* sx, const double* sy, const double* sz, const double* sq,
+                   int64_t ns, double theta, int32_t degree, int32_t leaf_size,
+                   int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
+                   const int64_t* batch_subset, int64_t n_subset, double* phi, double* phi_abs,
+                   double* timings)
 {
-    if (n < 1 || degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
+    if (nt < 1 || ns < 1 || degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
 #endif
     double t0 = now_seconds();
     oracle_tree *st = NULL, *bt = NULL;
-    if (oracle_tree_build(x, y, z, n, leaf_size, &st)) return -2;
-    if (oracle_tree_build(x, y, z, n, batch_size, &bt)) {
+    if (oracle_tree_build(sx, sy, sz, ns, leaf_size, &st)) return -2;
+    if (oracle_tree_build(tx, ty, tz, nt, batch_size, &bt)) {
         oracle_tree_free(st);
         return -2;
     }
@@ -630,13 +633,13 @@ int oracle_bltc(const double* x, const double* y, const double* z, const double*
         oracle_tree_free(bt);
         return -2;
     }
-    oracle_modified_charges(st, x, y, z, q, degree, threads, qhat);
+    oracle_modified_charges(st, sx, sy, sz, sq, degree, threads, qhat);
     double t2 = now_seconds();
 
     int64_t nb = collect_leaves(bt, NULL);
     int64_t* leaves = (int64_t*)malloc((size_t)nb * sizeof(int64_t));
     collect_leaves(bt, leaves);
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t i = 0; i < nt; ++i) {
         phi[i] = 0.0;
         if (phi_abs) phi_abs[i] = 0.0;
     }
@@ -653,13 +656,13 @@ int oracle_bltc(const double* x, const double* y, const double* z, const double*
         memset(&c, 0, sizeof(c));
         c.bt = bt;
         c.st = st;
-        c.tx = x;
-        c.ty = y;
-        c.tz = z;
-        c.sx = x;
-        c.sy = y;
-        c.sz = z;
-        c.sq = q;
+        c.tx = tx;
+        c.ty = ty;
+        c.tz = tz;
+        c.sx = sx;
+        c.sy = sy;
+        c.sz = sz;
+        c.sq = sq;
         c.qhat = qhat;
         c.theta = theta;
         c.kappa = kappa;
@@ -681,6 +684,16 @@ int oracle_bltc(const double* x, const double* y, const double* z, const double*
     oracle_tree_free(st);
     oracle_tree_free(bt);
     return bad ? -1 : 0;
+}
+
+/* Algorithm 1 with targets = sources (x, y, z, q), as in all of the paper's runs. */
+int oracle_bltc(const double* x, const double* y, const double* z, const double* q, int64_t n,
+                double theta, int32_t degree, int32_t leaf_size, int32_t batch_size,
+                int32_t kernel, double kappa, int32_t threads, const int64_t* batch_subset,
+                int64_t n_subset, double* phi, double* phi_abs, double* timings)
+{
+    return oracle_bltc_ts(x, y, z, n, x, y, z, q, n, theta, degree, leaf_size, batch_size,
+                          kernel, kappa, threads, batch_subset, n_subset, phi, phi_abs, timings);
 }
 
 int oracle_max_threads(void)

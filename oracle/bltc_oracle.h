@@ -57,6 +57,14 @@ int oracle_bltc(const double* x, const double* y, const double* z, const double*
                 int32_t kernel, double kappa, int32_t threads, const int64_t* batch_subset,
                 int64_t n_subset, double* phi, double* phi_abs, double* timings);
 
+/* Algorithm 1 for distinct target and source sets (nt targets, ns sources). */
+int oracle_bltc_ts(const double* tx, const double* ty, const double* tz, int64_t nt,
+                   const double* sx, const double* sy, const double* sz, const double* sq,
+                   int64_t ns, double theta, int32_t degree, int32_t leaf_size,
+                   int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
+                   const int64_t* batch_subset, int64_t n_subset, double* phi, double* phi_abs,
+                   double* timings);
+
 int oracle_max_threads(void);
 
 #ifdef __cplusplus

@@ -406,3 +406,67 @@ def test_batch_subset_matches_full_run():
         B = bt.leaves[b]
         idx = bt.perm[bt.begin[B]:bt.begin[B] + bt.count[B]]
         assert np.array_equal(sub[idx], full[idx])
+
+
+# ---------------------------------------------------------------------------------------
+# Distinct target and source sets (Sec. II: only target and source positions enter)
+# ---------------------------------------------------------------------------------------
+
+def _targets_and_sources(nt, ns, seed=20031851):
+    """Sources in [-1, 1]^3; targets in a larger, shifted box (some far from every source,
+    some inside the source cloud) plus every 50th source position exactly (r^2 == 0 pairs)."""
+    sx, sy, sz, q = inputs.uniform_cube(ns, seed)
+    tx, ty, tz, _ = inputs.uniform_cube(nt, seed + 1)
+    tx, ty, tz = 1.5 * tx + 0.75, 1.5 * ty, 1.5 * tz - 0.25
+    tx = np.concatenate([tx, sx[::50]])
+    ty = np.concatenate([ty, sy[::50]])
+    tz = np.concatenate([tz, sz[::50]])
+    return (tx, ty, tz), (sx, sy, sz), q
+
+
+def test_ts_same_sets_equal_bltc_bitwise():
+    x, y, z, q = _system(3000)
+    a, _, _ = oracle.bltc(x, y, z, q, 0.7, 4, 200, 150)
+    b, _, _ = oracle.bltc_ts((x, y, z), (x, y, z), q, 0.7, 4, 200, 150)
+    assert np.array_equal(a, b)
+
+
+def test_ts_theta_zero_equals_direct_sum():
+    T, S, q = _targets_and_sources(2500, 4000)
+    phi, _, _ = oracle.bltc_ts(T, S, q, 0.0, 4, 300, 170)
+    ref = oracle.direct_sum(np.stack(T), np.stack(S), q)
+    assert oracle.rel_err(ref, phi) < 1e-14
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_ts_polynomial_kernel_is_exact(n):
+    T, S, q = _targets_and_sources(3000, 5000, 20031853)
+    phi, _, _ = oracle.bltc_ts(T, S, q, 0.7, n, 150, 220, oracle.KERNEL_POLY)
+    ref, ref_abs = oracle.direct_sum(np.stack(T), np.stack(S), q, oracle.KERNEL_POLY, 0.0, n,
+                                     with_abs=True)
+    assert np.max(np.abs(phi - ref) / ref_abs) < 1e-12
+    bt, st = oracle.Tree(*T, 220), oracle.Tree(*S, 150)
+    assert len(oracle.lists(bt, st, 0.7, n)["approx_ids"]) > 0
+
+
+def test_ts_lists_cover_every_pair_exactly_once():
+    T, S, _ = _targets_and_sources(2000, 6000, 20031855)
+    st, bt = oracle.Tree(*S, 200), oracle.Tree(*T, 130)
+    for theta, n in [(0.7, 4), (0.9, 2)]:
+        L = oracle.lists(bt, st, theta, n)
+        for b_i in range(len(bt.leaves)):
+            cover = np.zeros(len(S[0]), np.int64)
+            for key in ("approx", "direct"):
+                for C in L[key + "_ids"][L[key + "_off"][b_i]:L[key + "_off"][b_i + 1]]:
+                    cover[st.begin[C]:st.begin[C] + st.count[C]] += 1
+            assert (cover == 1).all(), (theta, n, b_i)
+        assert len(L["approx_ids"]) > 0
+
+
+def test_ts_error_band_and_decay():
+    # the approximation error for separate sets behaves as for targets = sources (Sec. IV)
+    T, S, q = _targets_and_sources(3000, 20000, 20031857)
+    ref = oracle.direct_sum(np.stack(T), np.stack(S), q)
+    errs = [oracle.rel_err(ref, oracle.bltc_ts(T, S, q, 0.7, n, 300, 300)[0]) for n in (1, 3, 5, 7)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert 1e-9 < errs[2] < 1e-4 and errs[0] > 1e-4, errs
