@@ -199,6 +199,18 @@ bltc_status bltc_evaluate(bltc_context* ctx, const bltc_lists* lists, const bltc
 bltc_status bltc_solve(bltc_context* ctx, const double* x, const double* y, const double* z,
                        const double* q, int64_t n, const bltc_params* params, double* phi);
 
+/* Algorithm 1 for distinct target and source sets (Sec. II: the treecode needs only target
+ * and source positions; the paper's runs use targets = sources).  nt targets (tx, ty, tz),
+ * ns sources (sx, sy, sz) with charges sq, all DEVICE pointers owned by the caller.  Builds
+ * the source tree with params->leaf_size (N_L) and the batch tree of the targets with
+ * params->batch_size (N_B), then lists, modified charges and the sweeps; phi[nt] (device)
+ * receives the potentials in the caller's target order.  A target at exactly the position of
+ * a source skips that pair (r^2 == 0), as in bltc_solve.  Errors: as bltc_solve. */
+bltc_status bltc_solve_targets(bltc_context* ctx, const double* tx, const double* ty,
+                               const double* tz, int64_t nt, const double* sx, const double* sy,
+                               const double* sz, const double* sq, int64_t ns,
+                               const bltc_params* params, double* phi);
+
 /* bltc_solve for HOST buffers x, y, z, q, phi (pinned memory recommended): copies the
  * inputs to the device, solves, copies phi back.  Synchronizes.  Errors: as bltc_solve. */
 bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,
@@ -269,7 +281,10 @@ typedef struct bltc_server_config {
     int32_t device;           /* CUDA device */
     int32_t setup_workers;    /* host threads preparing requests, 1..64 */
     int32_t max_batch;        /* most requests merged into one sweep launch, >= 1 */
-    int32_t reserved;         /* must be 0 */
+    int32_t linger_us;        /* batching window, >= 0: with fewer than max_batch requests
+                               * ready while others are still being prepared, the engine
+                               * waits up to this many microseconds for them before it
+                               * launches (0: launch at once) */
     int64_t hbm_budget_bytes; /* device bytes admitted requests may reserve; 0 = 80% of free */
 } bltc_server_config;
 
@@ -306,6 +321,10 @@ bltc_status bltc_server_wait(bltc_server* server, uint64_t ticket, double timeou
  * (unknown ticket), STATE (already admitted). */
 bltc_status bltc_server_cancel(bltc_server* server, uint64_t ticket);
 bltc_status bltc_server_stats(bltc_server* server, bltc_server_counters* out);
+/* Copies the message of the most recently failed request (empty if none) into buf (len
+ * bytes, NUL-terminated, truncated to fit; buf may be NULL) and returns its full length, or
+ * -1 for a NULL server. */
+int64_t bltc_server_last_error(bltc_server* server, char* buf, int64_t len);
 /* Cancels queued requests, lets admitted ones finish, stops the threads. */
 void bltc_server_destroy(bltc_server* server);
 

@@ -61,7 +61,7 @@ def params(degree=8, theta=0.7, leaf_size=2000, batch_size=None, kernel=BLTC_KER
 
 class bltc_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("setup_workers", ctypes.c_int32),
-                ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("linger_us", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64)]
 
 
@@ -116,6 +116,8 @@ _SIGNATURES = {
     "bltc_evaluate": ([_vp, _vp, _vp, _vp, _P, _vp], ctypes.c_int),
     "bltc_solve": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_host": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
+    "bltc_solve_targets": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
+                           ctypes.c_int),
     "bltc_direct_sum": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                         ctypes.c_int),
     "bltc_direct_sum_noalloc": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
@@ -129,6 +131,7 @@ _SIGNATURES = {
                          ctypes.c_int),
     "bltc_server_cancel": ([_vp, ctypes.c_uint64], ctypes.c_int),
     "bltc_server_stats": ([_vp, ctypes.POINTER(bltc_server_counters)], ctypes.c_int),
+    "bltc_server_last_error": ([_vp, ctypes.c_char_p, _i64], _i64),
     "bltc_server_destroy": ([_vp], None),
 }
 
@@ -358,6 +361,14 @@ def bltc_solve(ctx, x, y, z, q, p: bltc_params, phi):
                                  ctypes.byref(p), _ptr(phi)))
 
 
+def bltc_solve_targets(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):
+    """Distinct target (tx, ty, tz) and source (sx, sy, sz, sq) sets; device tensors."""
+    _stream(ctx)
+    _check(ctx, lib().bltc_solve_targets(ctx, _ptr(tx), _ptr(ty), _ptr(tz), tx.numel(), _ptr(sx),
+                                         _ptr(sy), _ptr(sz), _ptr(sq), sx.numel(), ctypes.byref(p),
+                                         _ptr(phi)))
+
+
 def bltc_solve_host(ctx, x, y, z, q, p: bltc_params, phi):
     """Host buffers (numpy arrays or CPU tensors, pinned recommended)."""
     _stream(ctx)
@@ -391,8 +402,8 @@ def bltc_autotune(ctx, x, y, z, q, p: bltc_params, leaf=(500, 1000, 2000, 3000, 
 
 # ---- serving -------------------------------------------------------------------------
 
-def bltc_server_create(device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0):
-    cfg = bltc_server_config(int(device), int(setup_workers), int(max_batch), 0,
+def bltc_server_create(device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0, linger_us=0):
+    cfg = bltc_server_config(int(device), int(setup_workers), int(max_batch), int(linger_us),
                              int(hbm_budget_bytes))
     h = ctypes.c_void_p()
     st = lib().bltc_server_create(ctypes.byref(cfg), ctypes.byref(h))
@@ -432,6 +443,13 @@ def bltc_server_stats(server):
     return {k: getattr(c, k) for k, _ in bltc_server_counters._fields_}
 
 
+def bltc_server_last_error(server):
+    """Message of the most recently failed request ('' if none)."""
+    buf = ctypes.create_string_buffer(1024)
+    lib().bltc_server_last_error(server, buf, len(buf))
+    return buf.value.decode(errors="replace")
+
+
 def bltc_server_destroy(server):
     lib().bltc_server_destroy(server)
 
@@ -439,8 +457,8 @@ def bltc_server_destroy(server):
 class Server:
     """Owns a serving runtime; keeps each request's host arrays alive until it is waited."""
 
-    def __init__(self, device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0):
-        self.h = bltc_server_create(device, setup_workers, max_batch, hbm_budget_bytes)
+    def __init__(self, device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0, linger_us=0):
+        self.h = bltc_server_create(device, setup_workers, max_batch, hbm_budget_bytes, linger_us)
         self._keep = {}
 
     def submit(self, x, y, z, q, p, phi=None):
@@ -463,6 +481,9 @@ class Server:
 
     def stats(self):
         return bltc_server_stats(self.h)
+
+    def last_error(self):
+        return bltc_server_last_error(self.h)
 
     def close(self):
         if self.h:

@@ -127,6 +127,24 @@ static void solve_device(Context* c, const double* x, const double* y, const dou
     evaluate(c, &L, bt, &st, p, phi);
 }
 
+// Algorithm 1 for distinct target and source sets: the source tree (leaf_size, charges) and
+// the batch tree of the targets (batch_size, no charges) are built separately.
+static void solve_device_targets(Context* c, const double* tx, const double* ty, const double* tz,
+                                 int64_t nt, const double* sx, const double* sy, const double* sz,
+                                 const double* sq, int64_t ns, const bltc_params& p, double* phi) {
+    c->mark(Context::kStart);
+    Tree st, bt;
+    build_tree(c, sx, sy, sz, sq, ns, p.leaf_size, &st);
+    build_tree(c, tx, ty, tz, nullptr, nt, p.batch_size, &bt);
+    c->mark(Context::kTrees);
+    Lists L;
+    build_lists(c, &bt, &st, p.theta, p.degree, &L);
+    c->mark(Context::kLists);
+    compute_modified_charges(c, &st, &L, p.degree, p.precision);
+    c->mark(Context::kUpward);
+    evaluate(c, &L, &bt, &st, p, phi);
+}
+
 }  // namespace bltc
 
 using namespace bltc;
@@ -390,6 +408,18 @@ bltc_status bltc_solve(bltc_context* ctx, const double* x, const double* y, cons
         check_params(params);
         require(x && y && z && q && phi, "solve: NULL pointer");
         solve_device(&ctx->c, x, y, z, q, n, *params, phi);
+    });
+}
+
+bltc_status bltc_solve_targets(bltc_context* ctx, const double* tx, const double* ty,
+                               const double* tz, int64_t nt, const double* sx, const double* sy,
+                               const double* sz, const double* sq, int64_t ns,
+                               const bltc_params* params, double* phi) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(tx && ty && tz && sx && sy && sz && sq && phi, "solve_targets: NULL pointer");
+        solve_device_targets(&ctx->c, tx, ty, tz, nt, sx, sy, sz, sq, ns, *params, phi);
     });
 }
 
