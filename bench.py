@@ -417,7 +417,7 @@ def run_serving(args, dist: Dist):
                     time.sleep(0.0002)
                 st, _, info = srv.wait(tickets[i])
                 if st != b.BLTC_OK:
-                    raise RuntimeError(f"request {i} failed with status {st}")
+                    raise RuntimeError(f"request {i} failed with status {st}: {srv.last_error()}")
                 lat.append((info["t_done"] - info["t_submit"]) * 1e3)
             th.join()
             return time.perf_counter() - t0, np.array(lat)

@@ -80,6 +80,8 @@ struct Server {
     uint64_t next_ticket = 1;
     int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_cancelled = 0, n_launches = 0;
     int64_t max_batch_seen = 0;
+    int64_t preparing = 0;          // admitted, not yet ready or failed
+    std::string last_err;           // message of the most recent failed request
     bool stop = false;
     std::vector<std::thread> threads;
 };
@@ -147,6 +149,7 @@ static void finish(Server* s, ServerRequest* r, bltc_status st, const std::strin
     // caller holds s->mu
     r->status = st;
     r->err = err;
+    if (st != BLTC_OK && st != BLTC_ERR_CANCELLED) s->last_err = err;
     r->state = ServerRequest::kDone;
     r->t_done = now_s();
     s->in_use -= r->bytes;
@@ -202,6 +205,7 @@ static void worker_loop(Server* s, Context* c) {
             r->t_admit = now_s();
             s->in_use += r->bytes;
             s->peak_in_use = std::max(s->peak_in_use, s->in_use);
+            ++s->preparing;
         }
         std::string err;
         bltc_status st = BLTC_OK;
@@ -218,10 +222,13 @@ static void worker_loop(Server* s, Context* c) {
             cudaStreamSynchronize(c->stream);
             drop_device_state(r);
             std::lock_guard<std::mutex> lk(s->mu);
+            --s->preparing;
             finish(s, r, st, err);
+            s->cv.notify_all();
             continue;
         }
         std::lock_guard<std::mutex> lk(s->mu);
+        --s->preparing;
         r->state = ServerRequest::kReady;
         r->t_ready = now_s();
         s->ready.push_back(r);
@@ -238,6 +245,15 @@ static void engine_loop(Server* s) {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait(lk, [&] { return s->stop || !s->ready.empty(); });
             if (s->stop && s->ready.empty()) return;
+            if (s->cfg.linger_us > 0) {
+                // batching window: wait for requests still in preparation (or queued)
+                const auto until = std::chrono::steady_clock::now() +
+                                   std::chrono::microseconds(s->cfg.linger_us);
+                s->cv.wait_until(lk, until, [&] {
+                    return s->stop || static_cast<int>(s->ready.size()) >= s->cfg.max_batch ||
+                           (s->preparing == 0 && s->queued.empty());
+                });
+            }
             while (!s->ready.empty() && static_cast<int>(batch.size()) < s->cfg.max_batch) {
                 batch.push_back(s->ready.front());
                 s->ready.pop_front();
@@ -323,7 +339,7 @@ bltc_status bltc_server_create(const bltc_server_config* cfg, bltc_server** out)
     if (!cfg || !out) return BLTC_ERR_ARG;
     *out = nullptr;
     if (cfg->setup_workers < 1 || cfg->setup_workers > 64 || cfg->max_batch < 1 || cfg->hbm_budget_bytes < 0 ||
-        cfg->reserved != 0)
+        cfg->linger_us < 0)
         return BLTC_ERR_ARG;
     std::unique_ptr<bltc_server> h(new bltc_server());
     Server& s = h->s;
@@ -453,6 +469,19 @@ bltc_status bltc_server_stats(bltc_server* h, bltc_server_counters* out) {
     out->live_bytes = s.live.load();
     out->peak_live_bytes = s.peak_live.load();
     return BLTC_OK;
+}
+
+int64_t bltc_server_last_error(bltc_server* h, char* buf, int64_t len) {
+    if (!h) return -1;
+    Server& s = h->s;
+    std::lock_guard<std::mutex> lk(s.mu);
+    const int64_t n = static_cast<int64_t>(s.last_err.size());
+    if (buf && len > 0) {
+        const int64_t m = std::min<int64_t>(n, len - 1);
+        std::memcpy(buf, s.last_err.data(), static_cast<size_t>(m));
+        buf[m] = '\0';
+    }
+    return n;
 }
 
 void bltc_server_destroy(bltc_server* h) {

@@ -375,6 +375,16 @@ size_t upward_smem(int np1) {
     return std::max(a, b);
 }
 
+// Function attributes are per process, not per stream: threads preparing solves of
+// different degrees at once must not lower each other's shared-memory limit.  Every call
+// therefore sets the same value, the largest any degree needs.
+template <typename F>
+int upward_smem_max() {
+    size_t m = 0;
+    for (int np1 = 2; np1 <= BLTC_MAX_DEGREE + 1; ++np1) m = std::max(m, upward_smem<F>(np1));
+    return static_cast<int>(m);
+}
+
 }  // namespace
 
 void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int degree,
@@ -449,13 +459,13 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
             const size_t sm = upward_smem<float>(np1);
             BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<float>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(sm)));
+                                           upward_smem_max<float>()));
             k_upward_partial<float><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
         } else {
             const size_t sm = upward_smem<double>(np1);
             BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<double>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(sm)));
+                                           upward_smem_max<double>()));
             k_upward_partial<double><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
         }
         BLTC_LAUNCH_CHECK("upward partial");
@@ -485,7 +495,7 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
                        precision == BLTC_PRECISION_MIXED ? st->qhat32.p : nullptr, np1};
             const size_t sm = m2m_smem_bytes(np1);
             BLTC_CUDA(cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(sm)));
+                                           static_cast<int>(m2m_smem_bytes(BLTC_MAX_DEGREE + 1))));
             for (int L = nl - 1; L >= 0; --L) {
                 if (h[L] == 0) continue;
                 k_m2m<<<h[L], 256, sm, s>>>(ma, list.p + off[L]); ++ctx->launches;

@@ -31,7 +31,8 @@ def _requests(k, seed, nmax_exp=5.0):
 def test_served_results_equal_solo(gpu):
     reqs = _requests(24, 1)
     solo = [gpu_solve(gpu, *r) for r in reqs]
-    srv = b.Server(0, setup_workers=3, max_batch=16)
+    # a batching window long enough that requests prepared together are swept together
+    srv = b.Server(0, setup_workers=3, max_batch=16, linger_us=200_000)
     try:
         tickets = [srv.submit(*r) for r in reqs]
         outs = [srv.wait(t) for t in tickets]
@@ -105,5 +106,27 @@ def test_submit_rejects_bad_parameters(gpu):
             assert e.value.status == b.BLTC_ERR_ARG
         st, _ = b.bltc_server_wait(srv.h, 12345)    # unknown ticket
         assert st == b.BLTC_ERR_ARG
+    finally:
+        srv.close()
+
+
+def test_concurrent_setup_of_different_degrees(gpu):
+    # Setup workers prepare requests of very different degrees at the same time; the upward
+    # kernels' shared-memory limits must not be lowered by one worker while another launches.
+    reqs = []
+    for i in range(16):
+        deg = (2, 16, 10, 4)[i % 4]
+        n = 40000 if deg == 16 else 12000
+        x, y, z, q = system("cube" if i % 2 else "plummer", n, 20031890 + i)
+        reqs.append((x, y, z, q, b.params(deg, 0.6, 6000 if deg == 16 else 1000,
+                                          kernel=i % 2, kappa=0.5 if i % 2 else 0.0)))
+    srv = b.Server(0, setup_workers=6, max_batch=8)
+    try:
+        tickets = [srv.submit(*r) for r in reqs]
+        for t, r in zip(tickets, reqs):
+            st, phi, _ = srv.wait(t)
+            assert st == b.BLTC_OK, srv.last_error()
+            assert np.array_equal(phi, gpu_solve(gpu, *r))
+        assert srv.last_error() == ""
     finally:
         srv.close()
