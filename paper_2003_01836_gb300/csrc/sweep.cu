@@ -36,8 +36,7 @@ constexpr int kSrcTile32 = 2048;      // float4 sources per staged tile (32 KB)
 constexpr int kSrcTile64 = 1280;      // D4 sources per staged tile (40 KB)
 constexpr int kSmemBytes = 40960;     // also holds 3(n+1) + (n+1)^3 doubles for n <= 16
 constexpr int kItemsPerBlock = 16;    // work items per resident block (load balance)
-constexpr int kBlock = 32;            // near-field FP32 block folded into a TwoSum accumulator
-constexpr int kFarEmuPairs = 0;       // far-field target pairs per k3 step using rsqrt2_fma
+constexpr int kBlock = 32;            // terms summed in FP32 before a TwoSum fold
 
 struct SweepArgs {
     // target batches
@@ -121,20 +120,6 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// 1/sqrt(x) on the FMA pipe for two values: the magic-constant initial estimate of Lomont
-// ("Fast inverse square root", 2003) refined by three Newton-Raphson steps
-// y <- y (3/2 - (x/2) y^2), packed.  Used for a share of the far-field terms so that the SFU
-// and FMA pipes are loaded together; relative error within a few FP32 ulps for normal x.
-__device__ __forceinline__ float2 rsqrt2_fma(float2 x) {
-    const float2 nh = mul2(x, make_float2(-0.5f, -0.5f));
-    float2 y = make_float2(__int_as_float(0x5F375A86 - (__float_as_int(x.x) >> 1)),
-                           __int_as_float(0x5F375A86 - (__float_as_int(x.y) >> 1)));
-    const float2 c15 = make_float2(1.5f, 1.5f);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) y = mul2(y, fma2(nh, mul2(y, y), c15));
-    return y;
-}
-
 template <int KER>
 __device__ __forceinline__ float2 ri2_mixed(float2 r2, float nkl2e, bool skip_zero) {
     float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
@@ -200,7 +185,7 @@ __device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double c
 #pragma unroll
             for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
             float rmin = 3.0e38f;      // smallest non-zero r^2 this thread met in the block
-#pragma unroll 2
+#pragma unroll 4
             for (int j = jb; j < je; ++j) {
                 const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
                 const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
@@ -265,8 +250,8 @@ __device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double c
 // Far field (Eq. 11) of cluster C on its tensor grid of Chebyshev points (Eq. 8).  Shared
 // memory holds (s, s) pairs of the 3(n+1) point coordinates relative to the batch centre,
 // then (qhat, qhat) pairs of the (n+1)^3 modified charges.  Within a (k1, k2) row the
-// partial r^2 of a target is reused over the n+1 values of k3; each row is summed in FP32
-// and folded into a TwoSum accumulator.
+// partial r^2 of a target is reused over the n+1 values of k3; runs of rows holding about
+// kBlock terms are summed in FP32 and folded into a TwoSum accumulator.
 template <int KER>
 __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const Targets& tg,
                           double (&acc)[kT], float2* sm, int g, int G) {
@@ -291,31 +276,32 @@ __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const T
     float hi[kT], lo[kT];
 #pragma unroll
     for (int u = 0; u < kT; ++u) hi[u] = lo[u] = 0.f;
-    for (int row = g; row < np1 * np1; row += G) {
-        const int k1 = row / np1, k2 = row - k1 * np1;
-        const float2 sx = sxp[k1], sy = syp[k2];
-        float2 t[kH];
-#pragma unroll
-        for (int v = 0; v < kH; ++v) {
-            const float2 dx = add2(sx, tg.x[v]);
-            const float2 dy = add2(sy, tg.y[v]);
-            t[v] = fma2(dy, dy, mul2(dx, dx));
-        }
-        const float2* qrow = sq + row * np1;
+    // rows are summed in FP32 in runs of about kBlock terms, then folded by TwoSum
+    const int R = np1 * np1, run = max(1, kBlock / np1) * G;
+    for (int row0 = g; row0 < R; row0 += run) {
         float2 f[kH];
 #pragma unroll
         for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
-#pragma unroll 3
-        for (int k3 = 0; k3 < np1; ++k3) {
-            const float2 sz = szp[k3], q = qrow[k3];
+        for (int row = row0; row < min(R, row0 + run); row += G) {
+            const int k1 = row / np1, k2 = row - k1 * np1;
+            const float2 sx = sxp[k1], sy = syp[k2];
+            float2 t[kH];
 #pragma unroll
             for (int v = 0; v < kH; ++v) {
-                const float2 dz = add2(sz, tg.z[v]);
-                const float2 r2 = fma2(dz, dz, t[v]);
-                if (KER == BLTC_KERNEL_COULOMB && v >= kH - kFarEmuPairs)
-                    f[v] = fma2(q, rsqrt2_fma(r2), f[v]);
-                else
+                const float2 dx = add2(sx, tg.x[v]);
+                const float2 dy = add2(sy, tg.y[v]);
+                t[v] = fma2(dy, dy, mul2(dx, dx));
+            }
+            const float2* qrow = sq + row * np1;
+#pragma unroll 9
+            for (int k3 = 0; k3 < np1; ++k3) {
+                const float2 sz = szp[k3], q = qrow[k3];
+#pragma unroll
+                for (int v = 0; v < kH; ++v) {
+                    const float2 dz = add2(sz, tg.z[v]);
+                    const float2 r2 = fma2(dz, dz, t[v]);
                     f[v] = fma2(q, ri2_mixed<KER>(r2, a.neg_kappa_log2e, false), f[v]);
+                }
             }
         }
 #pragma unroll
