@@ -139,6 +139,10 @@ __device__ __forceinline__ float2 ri2_mixed(float2 r2, float nkl2e, bool skip_ze
 constexpr int kT = 8;                 // targets per thread (even)
 constexpr int kH = kT / 2;
 constexpr int kMinBlocks = 2;         // resident blocks per SM the register budget must allow
+// Dynamic shared memory of the mixed sweep: the staging area, then each thread's kT FP64
+// partial potentials ([kT][kThreads], touched once per cluster or tile), which would
+// otherwise hold 16 registers through the inner loops.
+constexpr int kMixedSmem = kSmemBytes + kThreads * kT * static_cast<int>(sizeof(double));
 struct Targets {
     float2 x[kH], y[kH], z[kH];
 };
@@ -159,7 +163,7 @@ __device__ __forceinline__ int groups_for(int nb) {
 // TwoSum accumulator, then into FP64 per staged tile.
 template <int KER, bool SEL, bool CHECK>
 __device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double cb[3], const Targets& tg,
-                           double (&acc)[kT], float4* sm, int g, int G, int tb, int nb, int t0,
+                           double* acc, float4* sm, int g, int G, int tb, int nb, int t0,
                            int l, int tpg) {
     constexpr int kTile = kSrcTile32 / 2;
     const int cs = a.s_begin[C], nc = a.s_count[C];
@@ -243,7 +247,7 @@ __device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double c
             }
         }
 #pragma unroll
-        for (int u = 0; u < kT; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
+        for (int u = 0; u < kT; ++u) acc[u * kThreads] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
     }
 }
 
@@ -254,7 +258,7 @@ __device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double c
 // kBlock terms are summed in FP32 and folded into a TwoSum accumulator.
 template <int KER>
 __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const Targets& tg,
-                          double (&acc)[kT], float2* sm, int g, int G) {
+                          double* acc, float2* sm, int g, int G) {
     const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1;
     const float* qh = a.qhat32 + static_cast<int64_t>(a.qslot[C]) * P;
     __syncthreads();
@@ -311,7 +315,7 @@ __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const T
         }
     }
 #pragma unroll
-    for (int u = 0; u < kT; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
+    for (int u = 0; u < kT; ++u) acc[u * kThreads] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
 }
 
 template <int KER>
@@ -327,7 +331,7 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
     const int g = static_cast<int>(threadIdx.x) / tpg, l = static_cast<int>(threadIdx.x) - g * tpg;
     for (int t0 = 0; t0 < nb; t0 += tpg * kT) {
         Targets tg;
-        double acc[kT];
+        double* acc = reinterpret_cast<double*>(reinterpret_cast<char*>(sm) + kSmemBytes) + threadIdx.x;  // [u * kThreads]
 #pragma unroll
         for (int u = 0; u < kT; ++u) {
             const int t = min(t0 + l + tpg * u, nb - 1);
@@ -343,7 +347,7 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
                 tg.y[u / 2].x = ny;
                 tg.z[u / 2].x = nz;
             }
-            acc[u] = 0.0;
+            acc[u * kThreads] = 0.0;
         }
         for (int e = it.y; e < it.z; ++e) {
             if (e < na)
@@ -363,14 +367,14 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
 #pragma unroll
             for (int u = 0; u < kT; ++u) {
                 const int t = t0 + l + tpg * u;
-                if (t < nb) out[t] = acc[u];
+                if (t < nb) out[t] = acc[u * kThreads];
             }
         } else {
             // add the groups' partials in group order
             double* red = reinterpret_cast<double*>(sm);   // [G][tpg * kT]
             __syncthreads();
 #pragma unroll
-            for (int u = 0; u < kT; ++u) red[g * tpg * kT + u * tpg + l] = acc[u];
+            for (int u = 0; u < kT; ++u) red[g * tpg * kT + u * tpg + l] = acc[u * kThreads];
             __syncthreads();
             for (int i = threadIdx.x; i < tpg * kT; i += kThreads) {
                 double s2 = red[i];
@@ -384,7 +388,8 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
 
 template <int KER>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_mixed(SweepArgs a) {
-    __shared__ __align__(16) float4 sm[kSmemBytes / sizeof(float4)];
+    extern __shared__ __align__(16) float4 sm_dyn[];
+    float4* sm = sm_dyn;
     __shared__ int s_item;
     for (;;) {
         __syncthreads();
@@ -404,7 +409,8 @@ template <int KER>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_multi(const SweepArgs* __restrict__ reqs,
                                                              const int2* __restrict__ order,
                                                              int total, unsigned int* counter) {
-    __shared__ __align__(16) float4 sm[kSmemBytes / sizeof(float4)];
+    extern __shared__ __align__(16) float4 sm_dyn[];
+    float4* sm = sm_dyn;
     __shared__ __align__(16) SweepArgs s_a;
     __shared__ int s_item;
     int cur = -1;
@@ -867,9 +873,13 @@ void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc
     if (pl.n_items > 0) {
         if (p.precision == BLTC_PRECISION_MIXED) {
             if (p.kernel == BLTC_KERNEL_YUKAWA) {
-                k_sweep_mixed<BLTC_KERNEL_YUKAWA><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+                BLTC_CUDA(cudaFuncSetAttribute(k_sweep_mixed<BLTC_KERNEL_YUKAWA>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+                k_sweep_mixed<BLTC_KERNEL_YUKAWA><<<grid, kThreads, kMixedSmem, s>>>(a); ++ctx->launches;
             } else {
-                k_sweep_mixed<BLTC_KERNEL_COULOMB><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+                BLTC_CUDA(cudaFuncSetAttribute(k_sweep_mixed<BLTC_KERNEL_COULOMB>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+                k_sweep_mixed<BLTC_KERNEL_COULOMB><<<grid, kThreads, kMixedSmem, s>>>(a); ++ctx->launches;
             }
         } else {
             if (p.kernel == BLTC_KERNEL_YUKAWA) {
@@ -932,13 +942,17 @@ void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
     const int64_t cap = kMinBlocks * static_cast<int64_t>(std::max(1, ctx->sm_count));
     if (!order[0].empty()) {
         const int total = static_cast<int>(order[0].size());
-        k_sweep_multi<BLTC_KERNEL_COULOMB><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, 0, s>>>(
+        BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_COULOMB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+        k_sweep_multi<BLTC_KERNEL_COULOMB><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, kMixedSmem, s>>>(
             d_args.p, d_order.p, total, counter.p); ++ctx->launches;
         BLTC_LAUNCH_CHECK("sweep multi coulomb");
     }
     if (!order[1].empty()) {
         const int total = static_cast<int>(order[1].size());
-        k_sweep_multi<BLTC_KERNEL_YUKAWA><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, 0, s>>>(
+        BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_YUKAWA>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+        k_sweep_multi<BLTC_KERNEL_YUKAWA><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, kMixedSmem, s>>>(
             d_args.p, d_order.p + order[0].size(), total, counter2.p); ++ctx->launches;
         BLTC_LAUNCH_CHECK("sweep multi yukawa");
     }
