@@ -166,6 +166,14 @@ bltc_status bltc_lists_export(bltc_context* ctx, const bltc_lists* lists, int64_
  * direct list and N_B * (n+1)^3 for the approximation list.  Synchronizes. */
 bltc_status bltc_stats(bltc_context* ctx, const bltc_lists* lists,
                        int64_t* n_direct_interactions, int64_t* n_approx_interactions);
+/* Kernel evaluations bltc_evaluate performs for these lists with params->degree and
+ * params->precision: the N_B * (n+1)^3 approximation terms plus the direct terms, where in
+ * MIXED precision with batches = sources a leaf pair that is in each other's direct list
+ * (a mutual pair) is evaluated once for both of its batches (Eq. 1 is symmetric in i, j for
+ * the Coulomb and Yukawa kernels).  Not in the paper.  Builds the work plan if needed.
+ * Synchronizes.  Errors: ARG, CUDA. */
+bltc_status bltc_evaluations(bltc_context* ctx, bltc_lists* lists, const bltc_params* params,
+                             int64_t* n_evaluations);
 
 /* ---- A2: modified charges (Eq. 12; Eq. 14-15; exact hits, Sec. II-C) --------------- */
 
@@ -189,7 +197,9 @@ bltc_status bltc_modified_charges_export(bltc_context* ctx, const bltc_tree* sou
  * phi[n_targets] in the caller's original target order.  Needs bltc_modified_charges for
  * the same degree and precision.  Runs the far/near sweep as one persistent launch over a
  * work queue of (batch, list range) items, then sums each target's per-item partials in a
- * fixed order (deterministic).  Errors: ARG, STATE, OOM, CUDA. */
+ * fixed order (deterministic).  In MIXED precision with batches == sources, a leaf pair in
+ * each other's direct list is evaluated once for both batches (G is symmetric); see
+ * bltc_evaluations.  Errors: ARG, STATE, OOM, CUDA. */
 bltc_status bltc_evaluate(bltc_context* ctx, const bltc_lists* lists, const bltc_tree* batches,
                           const bltc_tree* sources, const bltc_params* params, double* phi);
 

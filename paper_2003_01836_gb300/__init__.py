@@ -111,6 +111,7 @@ _SIGNATURES = {
     "bltc_lists_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "bltc_lists_export": ([_vp] * 6, ctypes.c_int),
     "bltc_stats": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "bltc_evaluations": ([_vp, _vp, _P, _vp], ctypes.c_int),
     "bltc_modified_charges": ([_vp, _vp, _vp, _P], ctypes.c_int),
     "bltc_modified_charges_export": ([_vp, _vp, _vp], ctypes.c_int),
     "bltc_evaluate": ([_vp, _vp, _vp, _vp, _P, _vp], ctypes.c_int),
@@ -335,6 +336,14 @@ def bltc_stats(ctx, lists):
     d, a = ctypes.c_int64(), ctypes.c_int64()
     _check(ctx, lib().bltc_stats(ctx, lists, ctypes.byref(d), ctypes.byref(a)))
     return {"direct": d.value, "approx": a.value}
+
+
+def bltc_evaluations(ctx, lists, p: bltc_params):
+    """Kernel evaluations of bltc_evaluate for these lists and parameters."""
+    _stream(ctx)
+    n = ctypes.c_int64()
+    _check(ctx, lib().bltc_evaluations(ctx, lists, ctypes.byref(p), ctypes.byref(n)))
+    return n.value
 
 
 def bltc_modified_charges(ctx, sources, lists, p: bltc_params):

@@ -366,6 +366,15 @@ bltc_status bltc_stats(bltc_context* ctx, const bltc_lists* lists, int64_t* n_di
     return guarded(ctx, [&] { interaction_counts(&ctx->c, &lists->l, n_direct_interactions, n_approx_interactions); });
 }
 
+bltc_status bltc_evaluations(bltc_context* ctx, bltc_lists* lists, const bltc_params* params,
+                             int64_t* n_evaluations) {
+    if (!ctx || !lists || !n_evaluations) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        *n_evaluations = plan_evaluations(&ctx->c, &lists->l, params->degree, params->precision);
+    });
+}
+
 bltc_status bltc_modified_charges(bltc_context* ctx, bltc_tree* sources, const bltc_lists* lists,
                                   const bltc_params* params) {
     if (!ctx || !sources) return BLTC_ERR_ARG;

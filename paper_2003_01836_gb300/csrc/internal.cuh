@@ -140,12 +140,16 @@ struct Tree {
 struct Plan {
     bool valid = false;
     int degree = -1;
+    bool mutual = false;              // mutual leaf pairs evaluated once (mixed, batches = sources)
+    int64_t mpart_len = 0;            // doubles of mutual rows
+    DBuf<int64_t> dir_moff;           // per direct entry: its mutual row in mpart, or -1
     int64_t n_items = 0;
     int64_t partial_len = 0;
     DBuf<int4> items;                 // {batch, e0, e1, chunk}
     DBuf<int64_t> part_off;           // per batch: first partial
     DBuf<int32_t> n_chunks;           // per batch
-    DBuf<uint8_t> dir_sel;            // per direct entry: self-pair test needed (mixed sweep)
+    DBuf<uint8_t> dir_sel;            // per direct entry: bit 0 self-pair test, bit 1 close-pair
+                                      // check, bit 2 mutual owner, bit 3 mutual partner (skip)
     DBuf<float> dir_tau2;             // per direct entry: r^2 below which pairs are redone in FP64
     std::vector<int64_t> h_cost;      // host copy of the items' interaction counts (queue order)
 };
@@ -173,8 +177,11 @@ void evaluate(Context* ctx, Lists* lists, const Tree* bt, const Tree* st,
               const bltc_params& p, double* phi);
 void interaction_counts(Context* ctx, const Lists* lists, int64_t* n_dir, int64_t* n_app);
 // Work plan of a list set (items, partial layout, self-pair flags); built once per degree.
-void build_plan(Context* ctx, Lists* L, int degree);
-void prepare_plan(Context* ctx, Lists* L, int degree);
+void build_plan(Context* ctx, Lists* L, int degree, bool mutual);
+// The plan for an evaluation in `precision` (mutual pairs for MIXED with batches = sources).
+void prepare_plan(Context* ctx, Lists* L, int degree, int precision);
+// Kernel evaluations the sweep performs for that plan (mutual pairs counted once).
+int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision);
 // One request of a multi-request sweep: its lists, trees, parameters and device phi.
 struct SweepJob {
     Lists* L;

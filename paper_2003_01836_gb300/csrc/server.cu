@@ -183,7 +183,7 @@ static void prepare(Context* c, ServerRequest* r) {
     r->L.reset(new Lists());
     build_lists(c, bt, r->st.get(), r->p.theta, r->p.degree, r->L.get());
     compute_modified_charges(c, r->st.get(), r->L.get(), r->p.degree, r->p.precision);
-    prepare_plan(c, r->L.get(), r->p.degree);
+    prepare_plan(c, r->L.get(), r->p.degree, r->p.precision);
     BLTC_CUDA(cudaEventCreateWithFlags(&r->ready_ev, cudaEventDisableTiming));
     BLTC_CUDA(cudaEventRecord(r->ready_ev, c->stream));
 }

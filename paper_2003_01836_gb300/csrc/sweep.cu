@@ -63,6 +63,8 @@ struct SweepArgs {
     const int32_t* dir_ids;
     const uint8_t* dir_sel;    // per direct entry: bit 0 = r^2 == 0 possible, bit 1 = close pairs possible
     const float* dir_tau2;     // per direct entry: pairs closer than this (r^2) are redone in FP64
+    const int64_t* dir_moff;   // per direct entry: offset of its mutual row in mpart, or -1
+    double* mpart;             // mutual rows: potentials a batch's particles induce on a partner's
     const int4* items;
     const int64_t* part_off;
     double* partials;
@@ -142,7 +144,11 @@ constexpr int kMinBlocks = 2;         // resident blocks per SM the register bud
 // Dynamic shared memory of the mixed sweep: the staging area, then each thread's kT FP64
 // partial potentials ([kT][kThreads], touched once per cluster or tile), which would
 // otherwise hold 16 registers through the inner loops.
-constexpr int kMixedSmem = kSmemBytes + kThreads * kT * static_cast<int>(sizeof(double));
+constexpr int kNearTile = kSrcTile32 / 2;    // sources per staged near-field tile
+// then, for mutual pairs, one FP32 slot per warp and staged source: [warp][kNearTile]
+constexpr int kAccBytes = kThreads * kT * static_cast<int>(sizeof(double));
+constexpr int kMixedSmem = kSmemBytes + kAccBytes + (kThreads / 32) * kNearTile * static_cast<int>(sizeof(float));
+constexpr uint8_t kSelZero = 1, kSelClose = 2, kSelMutual = 4, kSelSkip = 8;
 struct Targets {
     float2 x[kH], y[kH], z[kH];
 };
@@ -165,7 +171,7 @@ template <int KER, bool SEL, bool CHECK>
 __device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double cb[3], const Targets& tg,
                            double* acc, float4* sm, int g, int G, int tb, int nb, int t0,
                            int l, int tpg) {
-    constexpr int kTile = kSrcTile32 / 2;
+    constexpr int kTile = kNearTile;
     const int cs = a.s_begin[C], nc = a.s_count[C];
     for (int j0 = 0; j0 < nc; j0 += kTile) {
         const int m = min(kTile, nc - j0);
@@ -248,6 +254,165 @@ __device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double c
         }
 #pragma unroll
         for (int u = 0; u < kT; ++u) acc[u * kThreads] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
+    }
+}
+
+// Sum over the 32 lanes of eight values per lane, v[s] for sources s = 0..7, by recursive
+// halving: 4 + 2 + 1 exchanges leave lane l with the sum over eight lanes of source l >> 2,
+// two more complete it.  Nine shuffles instead of 40; the order of the additions is fixed.
+__device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
+    const unsigned full = 0xffffffffu;
+    const bool h4 = (lane >> 4) & 1, h3 = (lane >> 3) & 1, h2 = (lane >> 2) & 1;
+    float w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = h4 ? v[i] : v[i + 4];
+        const float keep = h4 ? v[i + 4] : v[i];
+        w[i] = keep + __shfl_xor_sync(full, send, 16);
+    }
+    float x[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = h3 ? w[i] : w[i + 2];
+        const float keep = h3 ? w[i + 2] : w[i];
+        x[i] = keep + __shfl_xor_sync(full, send, 8);
+    }
+    float y = (h2 ? x[1] : x[0]) + __shfl_xor_sync(full, h2 ? x[0] : x[1], 4);
+    y += __shfl_xor_sync(full, y, 1);
+    y += __shfl_xor_sync(full, y, 2);
+    return y;
+}
+
+// Near field of a mutual pair: batch B (the targets) and leaf C are each in the other's
+// direct list and are the same particles as sources and targets, so one evaluation of
+// G(x_i, y_j) serves both phi_i += G q_j (as in near_mixed) and phi_j += G q_i (Eq. 9 for C's
+// own batch, whose list entry for B is skipped).  The second sum runs over B's targets,
+// which sit in different lanes: per source, each lane adds its 8 targets' q_i G in FP32, the
+// warp adds its lanes (warp_sum8), and after the tile the group's warps are added in warp
+// order into C's mutual row (FP64), so the result does not depend on scheduling.
+template <int KER, bool SEL, bool CHECK>
+__device__ void near_mutual(const SweepArgs& a, int C, float tau2, const double cb[3], const Targets& tg,
+                            double* acc, float4* sm, float* sbuf, double* mrow, int g, int G, int tb,
+                            int nb, int t0, int l, int tpg) {
+    constexpr int kTile = kNearTile;
+    const int cs = a.s_begin[C], nc = a.s_count[C];
+    const int lane = static_cast<int>(threadIdx.x) & 31, warp = static_cast<int>(threadIdx.x) >> 5;
+    const int wpg = tpg >> 5;                            // warps per group
+    // this thread's target charges (0 for the padding slots past the batch)
+    float2 qt[kH];
+#pragma unroll
+    for (int u = 0; u < kT; ++u) {
+        const int t = t0 + l + tpg * u;
+        const float qv = t < nb ? __double2float_rn(a.sq[tb + t]) : 0.f;
+        if (u & 1) qt[u / 2].y = qv; else qt[u / 2].x = qv;
+    }
+    for (int j0 = 0; j0 < nc; j0 += kTile) {
+        const int m = min(kTile, nc - j0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kThreads) {
+            const int p = cs + j0 + j;
+            const float sx = __double2float_rn(a.sx[p] - cb[0]);
+            const float sy = __double2float_rn(a.sy[p] - cb[1]);
+            const float sz = __double2float_rn(a.sz[p] - cb[2]);
+            const float sq = __double2float_rn(a.sq[p]);
+            sm[2 * j] = make_float4(sx, sx, sy, sy);
+            sm[2 * j + 1] = make_float4(sz, sz, sq, sq);
+        }
+        __syncthreads();
+        float hi[kT], lo[kT];
+#pragma unroll
+        for (int u = 0; u < kT; ++u) hi[u] = lo[u] = 0.f;
+        for (int jb = g * kBlock; jb < m; jb += G * kBlock) {
+            const int je = min(jb + kBlock, m);
+            float2 f[kH];
+#pragma unroll
+            for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
+            float rmin = 3.0e38f;
+            for (int j8 = jb; j8 < je; j8 += 8) {
+                float gs[8];
+#pragma unroll
+                for (int s8 = 0; s8 < 8; ++s8) {
+                    gs[s8] = 0.f;
+                    if (j8 + s8 < je) {
+                        const float4 p0 = sm[2 * (j8 + s8)], p1 = sm[2 * (j8 + s8) + 1];
+                        const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
+                        const float2 sz = make_float2(p1.x, p1.y), sq = make_float2(p1.z, p1.w);
+                        float2 g2 = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int v = 0; v < kH; ++v) {
+                            const float2 dx = add2(sx, tg.x[v]);
+                            const float2 dy = add2(sy, tg.y[v]);
+                            const float2 dz = add2(sz, tg.z[v]);
+                            const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                            if (CHECK) {
+                                if (SEL) {
+                                    rmin = fminf(rmin, r2.x > 0.f ? r2.x : 3.0e38f);
+                                    rmin = fminf(rmin, r2.y > 0.f ? r2.y : 3.0e38f);
+                                } else {
+                                    rmin = fminf(rmin, fminf(r2.x, r2.y));
+                                }
+                            }
+                            const float2 ri = ri2_mixed<KER>(r2, a.neg_kappa_log2e, SEL);
+                            f[v] = fma2(sq, ri, f[v]);
+                            g2 = fma2(qt[v], ri, g2);
+                        }
+                        gs[s8] = g2.x + g2.y;
+                    }
+                }
+                const float wsum = warp_sum8(gs, lane);
+                if ((lane & 3) == 0 && j8 + (lane >> 2) < je) sbuf[warp * kTile + j8 + (lane >> 2)] = wsum;
+            }
+#pragma unroll
+            for (int v = 0; v < kH; ++v) {
+                two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
+                two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
+            }
+            if (CHECK && __any_sync(0xffffffffu, rmin < tau2)) {
+                // Close pairs (see near_mixed), recomputed from FP64 coordinates for both
+                // sides; the warp takes this branch together so the source-side corrections
+                // can be added across lanes in a fixed order.
+                for (int j = jb; j < je; ++j) {
+                    const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
+                    const int ps = cs + j0 + j;
+                    float cj = 0.f;
+#pragma unroll
+                    for (int u = 0; u < kT; ++u) {
+                        const float2 ptx = tg.x[u / 2], pty = tg.y[u / 2], ptz = tg.z[u / 2];
+                        const float dx = p0.x + ((u & 1) ? ptx.y : ptx.x);
+                        const float dy = p0.z + ((u & 1) ? pty.y : pty.x);
+                        const float dz = p1.x + ((u & 1) ? ptz.y : ptz.x);
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (r2 > 0.f && r2 < tau2) {
+                            const int t = min(t0 + l + tpg * u, nb - 1);
+                            const double ex = a.sx[ps] - a.tx[tb + t], ey = a.sy[ps] - a.ty[tb + t];
+                            const double ez = a.sz[ps] - a.tz[tb + t];
+                            const double r2d = ex * ex + ey * ey + ez * ez;
+                            double rid = rsqrt(r2d);
+                            if (KER == BLTC_KERNEL_YUKAWA) rid *= exp(-a.kappa * (r2d * rid));
+                            float ri = rsqrt_approx(r2);
+                            if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
+                            lo[u] += static_cast<float>(a.sq[ps] * rid - static_cast<double>(p1.z * ri));
+                            const float qu = (u & 1) ? qt[u / 2].y : qt[u / 2].x;
+                            if (qu != 0.f)
+                                cj += static_cast<float>(a.sq[tb + t] * rid - static_cast<double>(qu * ri));
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cj += __shfl_xor_sync(0xffffffffu, cj, o);
+                    if (lane == 0) sbuf[warp * kTile + j] += cj;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kT; ++u) acc[u * kThreads] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
+        // C's row: each staged source's sum over the group's warps, in warp order
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kThreads) {
+            const int w0 = ((j / kBlock) % G) * wpg;
+            double sum = 0.0;
+            for (int w = w0; w < w0 + wpg; ++w) sum += static_cast<double>(sbuf[w * kTile + j]);
+            if (t0 == 0) mrow[j0 + j] = sum; else mrow[j0 + j] += sum;
+        }
     }
 }
 
@@ -356,9 +521,21 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
                 const int de = d0 + e - na;
                 const int C = a.dir_ids[de];
                 const float tau2 = a.dir_tau2[de];
-                switch (a.dir_sel[de]) {
+                const uint8_t sel = a.dir_sel[de];
+                if (sel & kSelSkip) continue;            // evaluated by the partner's mutual entry
+                if (sel & kSelMutual) {
+                    float* sbuf = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + kSmemBytes + kAccBytes);
+                    double* mrow = a.mpart + a.dir_moff[de];
+                    switch (sel & (kSelZero | kSelClose)) {
+                        case 0: near_mutual<KER, false, false>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
+                        case kSelClose: near_mutual<KER, false, true>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
+                        default: near_mutual<KER, true, true>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
+                    }
+                    continue;
+                }
+                switch (sel & (kSelZero | kSelClose)) {
                     case 0: near_mixed<KER, false, false>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
-                    case 2: near_mixed<KER, false, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                    case kSelClose: near_mixed<KER, false, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
                     default: near_mixed<KER, true, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
                 }
             }
@@ -583,7 +760,33 @@ struct PlanArgs {
     const double* s_hi;
     uint8_t* dir_sel;
     float* dir_tau2;
+    // mutual pairs
+    const int32_t* s_nch;
+    const int32_t* lidx;         // source node -> batch index (leaves; batches = sources), or -1
+    int32_t* partner;            // per direct entry: the partner's entry for B, or -1
+    int64_t* mlen;               // per direct entry: mutual row length (owners only)
+    const int64_t* moff_e;       // per direct entry: exclusive scan of mlen
+    int64_t* dir_moff;
 };
+
+// The batch owning direct entry e: the last b with dir_off[b] <= e.
+__device__ __forceinline__ int64_t batch_of_entry(const PlanArgs& a, int64_t e) {
+    int64_t lo = 0, hi = a.n_batches;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a.dir_off[mid] <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Cost of direct entry e of a batch of nb targets in the mixed sweep: skipped entries cost
+// nothing, mutual owners carry the partner's side too.
+__device__ __forceinline__ int64_t dir_cost(const PlanArgs& a, int64_t e, int64_t nb) {
+    const int64_t c = nb * static_cast<int64_t>(a.s_count[a.dir_ids[e]]);
+    if (!a.dir_sel) return c;
+    const uint8_t sel = a.dir_sel[e];
+    return (sel & kSelSkip) ? 0 : ((sel & kSelMutual) ? c + c / 4 : c);
+}
 
 // Marks the direct entries where the mixed sweep must test r^2 == 0.  A target t of batch B
 // and a source s of cluster C enter the sweep as fp32(t - c_B) and fp32(s - c_B); each
@@ -596,13 +799,7 @@ struct PlanArgs {
 __global__ void k_dir_flags(PlanArgs a, int64_t n_dir) {
     const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= n_dir) return;
-    // the batch owning entry e: the last b with dir_off[b] <= e
-    int64_t lo = 0, hi = a.n_batches;
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (a.dir_off[mid] <= e) lo = mid; else hi = mid;
-    }
-    const int B = a.b_leaves[lo];
+    const int B = a.b_leaves[batch_of_entry(a, e)];
     const int C = a.dir_ids[e];
     bool separated = false;
     double Mmax = 0.0;
@@ -629,14 +826,58 @@ __global__ void k_dir_flags(PlanArgs a, int64_t n_dir) {
     a.dir_tau2[e] = static_cast<float>(tau * tau);
 }
 
+// Mutual pairs (batches = sources, same tree): leaf C in batch b's direct list whose own
+// batch b2 has b's leaf in its direct list.  The entry of the smaller batch index owns the
+// pair (bit kSelMutual) and computes both sides; the other is skipped (kSelSkip).  Lists are
+// in DFS order, i.e. sorted by node id, so the partner entry is found by binary search.
+__global__ void k_leaf_index(PlanArgs a, int32_t* lidx) {
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b < a.n_batches) lidx[a.b_leaves[b]] = static_cast<int32_t>(b);
+}
+
+__global__ void k_mutual_mark(PlanArgs a, int64_t n_dir) {
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n_dir) return;
+    const int64_t b = batch_of_entry(a, e);
+    const int A = a.b_leaves[b], C = a.dir_ids[e];
+    int32_t partner = -1;
+    int64_t len = 0;
+    const int b2 = C != A && a.s_nch[C] == 0 ? a.lidx[C] : -1;
+    if (b2 >= 0) {
+        int lo = a.dir_off[b2], hi = a.dir_off[b2 + 1];       // search A in [lo, hi)
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a.dir_ids[mid] < A) lo = mid + 1; else hi = mid;
+        }
+        if (lo < a.dir_off[b2 + 1] && a.dir_ids[lo] == A) {
+            partner = lo;
+            if (b < b2) {
+                a.dir_sel[e] |= kSelMutual;
+                len = a.s_count[C];
+            } else {
+                a.dir_sel[e] |= kSelSkip;
+            }
+        }
+    }
+    a.partner[e] = partner;
+    a.mlen[e] = len;
+}
+
+__global__ void k_mutual_moff(PlanArgs a, int64_t n_dir) {
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n_dir) return;
+    const uint8_t sel = a.dir_sel[e];
+    a.dir_moff[e] = (sel & kSelMutual) ? a.moff_e[e] : ((sel & kSelSkip) ? a.moff_e[a.partner[e]] : -1);
+}
+
 __global__ void k_batch_cost(PlanArgs a) {
     const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (b >= a.n_batches) return;
     const int64_t nb = a.b_count[a.b_leaves[b]];
-    int64_t c = static_cast<int64_t>(a.app_off[b + 1] - a.app_off[b]) * a.P;
-    for (int e = a.dir_off[b]; e < a.dir_off[b + 1]; ++e) c += a.s_count[a.dir_ids[e]];
-    a.cost[b] = c * nb;
-    atomicAdd(a.total, static_cast<unsigned long long>(c * nb));
+    int64_t c = static_cast<int64_t>(a.app_off[b + 1] - a.app_off[b]) * a.P * nb;
+    for (int e = a.dir_off[b]; e < a.dir_off[b + 1]; ++e) c += dir_cost(a, e, nb);
+    a.cost[b] = c;
+    atomicAdd(a.total, static_cast<unsigned long long>(c));
 }
 
 // Greedy cut of a batch's list (approximated clusters first, then direct ones) into items
@@ -653,7 +894,7 @@ __global__ void k_chunks(PlanArgs a) {
     int64_t acc = 0;
     int4* out = kFill ? a.items + a.item_off[b] : nullptr;
     for (int e = 0; e < ne; ++e) {
-        const int64_t c = nb * (e < na ? a.P : static_cast<int64_t>(a.s_count[a.dir_ids[d0 + e - na]]));
+        const int64_t c = e < na ? nb * a.P : dir_cost(a, d0 + e - na, nb);
         if (acc > 0 && acc + c > a.cut) {
             if (kFill) out[chunk] = make_int4(static_cast<int>(b), start, e, chunk);
             ++chunk;
@@ -680,14 +921,18 @@ __global__ void k_item_costs(PlanArgs a, const int4* __restrict__ items, int64_t
     const int64_t nb = a.b_count[a.b_leaves[b]];
     const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
     int64_t c = 0;
-    for (int e = it.y; e < it.z; ++e) c += e < na ? a.P : static_cast<int64_t>(a.s_count[a.dir_ids[d0 + e - na]]);
-    cost[i] = c * nb;
+    for (int e = it.y; e < it.z; ++e) c += e < na ? nb * a.P : dir_cost(a, d0 + e - na, nb);
+    cost[i] = c;
 }
 
+// Per target: its items' partials in item order, then (mutual pairs) the rows that partner
+// batches wrote for it, in list order; scattered to the caller's order.
 __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* __restrict__ b_begin,
                            const int32_t* __restrict__ b_count, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ n_chunks, const int64_t* __restrict__ part_off,
-                           const double* __restrict__ partials, double* __restrict__ phi) {
+                           const double* __restrict__ partials, const int32_t* __restrict__ dir_off,
+                           const uint8_t* __restrict__ dir_sel, const int64_t* __restrict__ dir_moff,
+                           const double* __restrict__ mpart, double* __restrict__ phi) {
     const int b = blockIdx.x;
     const int B = b_leaves[b];
     const int tb = b_begin[B], nb = b_count[B], K = n_chunks[b];
@@ -695,29 +940,37 @@ __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* 
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
         double s = 0.0;
         for (int c = 0; c < K; ++c) s += p[static_cast<int64_t>(c) * nb + t];
+        if (mpart)
+            for (int e = dir_off[b]; e < dir_off[b + 1]; ++e)
+                if (dir_sel[e] & kSelSkip) s += mpart[dir_moff[e] + t];
         phi[perm[tb + t]] = s;
     }
 }
 
 __global__ void k_counts(const int32_t* b_leaves, const int32_t* b_count, const int32_t* s_count,
                          const int32_t* app_off, const int32_t* dir_off, const int32_t* dir_ids,
-                         int64_t n_batches, int64_t P, unsigned long long* out) {
+                         const uint8_t* dir_sel, int64_t n_batches, int64_t P, unsigned long long* out) {
     const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (b >= n_batches) return;
     const int64_t nb = b_count[b_leaves[b]];
-    int64_t d = 0;
-    for (int e = dir_off[b]; e < dir_off[b + 1]; ++e) d += s_count[dir_ids[e]];
+    int64_t d = 0, de = 0;
+    for (int e = dir_off[b]; e < dir_off[b + 1]; ++e) {
+        d += s_count[dir_ids[e]];
+        if (!dir_sel || !(dir_sel[e] & kSelSkip)) de += s_count[dir_ids[e]];
+    }
     atomicAdd(&out[0], static_cast<unsigned long long>(d * nb));
     atomicAdd(&out[1], static_cast<unsigned long long>(static_cast<int64_t>(app_off[b + 1] - app_off[b]) * P * nb));
+    atomicAdd(&out[2], static_cast<unsigned long long>(de * nb));
 }
 
 }  // namespace
 
-void build_plan(Context* ctx, Lists* L, int degree) {
+void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
     cudaStream_t s = ctx->stream;
     const int64_t nb = L->n_batches;
     const int64_t np1 = degree + 1;
     Plan& pl = L->plan;
+    pl.valid = false;
     PlanArgs a{};
     a.b_leaves = L->bt->leaves.p;
     a.b_count = L->bt->count.p;
@@ -727,6 +980,44 @@ void build_plan(Context* ctx, Lists* L, int degree) {
     a.dir_ids = L->dir_ids.p;
     a.n_batches = nb;
     a.P = np1 * np1 * np1;
+    // per direct entry: the self-pair and close-pair flags, then the mutual pairs
+    pl.dir_sel = DBuf<uint8_t>(ctx, L->n_dir);
+    pl.dir_tau2 = DBuf<float>(ctx, L->n_dir);
+    a.dir_tau2 = pl.dir_tau2.p;
+    a.b_lo = L->bt->lo.p;
+    a.b_hi = L->bt->hi.p;
+    a.b_center = L->bt->center.p;
+    a.s_lo = L->st->lo.p;
+    a.s_hi = L->st->hi.p;
+    a.dir_sel = pl.dir_sel.p;
+    if (L->n_dir > 0) {
+        k_dir_flags<<<grid_for(L->n_dir, 256), 256, 0, s>>>(a, L->n_dir); ++ctx->launches;
+    }
+    BLTC_LAUNCH_CHECK("plan flags");
+    pl.mutual = mutual && L->bt == L->st && L->n_dir > 0;
+    pl.mpart_len = 0;
+    pl.dir_moff = DBuf<int64_t>();
+    if (pl.mutual) {
+        const int64_t m = L->st->n_nodes;
+        DBuf<int32_t> lidx(ctx, m), partner(ctx, L->n_dir);
+        DBuf<int64_t> mlen(ctx, L->n_dir), moff_e(ctx, L->n_dir), tot(ctx, 1);
+        pl.dir_moff = DBuf<int64_t>(ctx, L->n_dir);
+        BLTC_CUDA(cudaMemsetAsync(lidx.p, 0xff, sizeof(int32_t) * m, s));
+        a.s_nch = L->st->nch.p;
+        a.lidx = lidx.p;
+        a.partner = partner.p;
+        a.mlen = mlen.p;
+        a.moff_e = moff_e.p;
+        a.dir_moff = pl.dir_moff.p;
+        k_leaf_index<<<grid_for(nb, 256), 256, 0, s>>>(a, lidx.p); ++ctx->launches;
+        k_mutual_mark<<<grid_for(L->n_dir, 256), 256, 0, s>>>(a, L->n_dir); ++ctx->launches;
+        BLTC_LAUNCH_CHECK("plan mutual");
+        exclusive_scan_i64(ctx, mlen.p, moff_e.p, L->n_dir, tot.p);
+        k_mutual_moff<<<grid_for(L->n_dir, 256), 256, 0, s>>>(a, L->n_dir); ++ctx->launches;
+        BLTC_LAUNCH_CHECK("plan mutual rows");
+        pl.mpart_len = ctx->read_words(tot.p, 1)[0];
+    }
+    // costs and items (skipped mutual entries cost nothing)
     DBuf<int64_t> cost(ctx, nb), part_len(ctx, nb), words(ctx, 4);
     BLTC_CUDA(cudaMemsetAsync(words.p, 0, 4 * sizeof(int64_t), s));
     a.cost = cost.p;
@@ -757,13 +1048,13 @@ void build_plan(Context* ctx, Lists* L, int degree) {
     // short ones fill the gaps at the end.  The order does not change any result (each item
     // writes its own partials); ties keep batch order (stable sort).
     if (pl.n_items > 1) {
-        DBuf<int64_t> cost(ctx, pl.n_items);
-        k_item_costs<<<grid_for(pl.n_items, 256), 256, 0, s>>>(a, pl.items.p, pl.n_items, cost.p); ++ctx->launches;
+        DBuf<int64_t> icost(ctx, pl.n_items);
+        k_item_costs<<<grid_for(pl.n_items, 256), 256, 0, s>>>(a, pl.items.p, pl.n_items, icost.p); ++ctx->launches;
         BLTC_LAUNCH_CHECK("plan costs");
         std::vector<int4> h_items(static_cast<size_t>(pl.n_items));
         std::vector<int64_t> h_cost(static_cast<size_t>(pl.n_items));
         BLTC_CUDA(cudaMemcpyAsync(h_items.data(), pl.items.p, sizeof(int4) * pl.n_items, cudaMemcpyDeviceToHost, s));
-        BLTC_CUDA(cudaMemcpyAsync(h_cost.data(), cost.p, sizeof(int64_t) * pl.n_items, cudaMemcpyDeviceToHost, s));
+        BLTC_CUDA(cudaMemcpyAsync(h_cost.data(), icost.p, sizeof(int64_t) * pl.n_items, cudaMemcpyDeviceToHost, s));
         BLTC_CUDA(cudaStreamSynchronize(s));
         std::vector<int64_t> order(static_cast<size_t>(pl.n_items));
         for (int64_t i = 0; i < pl.n_items; ++i) order[static_cast<size_t>(i)] = i;
@@ -778,23 +1069,9 @@ void build_plan(Context* ctx, Lists* L, int degree) {
     } else {
         pl.h_cost.assign(static_cast<size_t>(pl.n_items), 1);
     }
-    pl.dir_sel = DBuf<uint8_t>(ctx, L->n_dir);
-    pl.dir_tau2 = DBuf<float>(ctx, L->n_dir);
-    a.dir_tau2 = pl.dir_tau2.p;
-    a.b_lo = L->bt->lo.p;
-    a.b_hi = L->bt->hi.p;
-    a.b_center = L->bt->center.p;
-    a.s_lo = L->st->lo.p;
-    a.s_hi = L->st->hi.p;
-    a.dir_sel = pl.dir_sel.p;
-    if (L->n_dir > 0) {
-        k_dir_flags<<<grid_for(L->n_dir, 256), 256, 0, s>>>(a, L->n_dir); ++ctx->launches;
-    }
-    BLTC_LAUNCH_CHECK("plan flags");
     pl.degree = degree;
     pl.valid = true;
 }
-
 
 static void check_eval(const Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
                        const double* phi) {
@@ -840,6 +1117,8 @@ static SweepArgs make_args(Context* ctx, const Lists* L, const Tree* bt, const T
     a.dir_ids = L->dir_ids.p;
     a.dir_sel = pl.dir_sel.p;
     a.dir_tau2 = pl.dir_tau2.p;
+    a.dir_moff = pl.mutual ? pl.dir_moff.p : nullptr;
+    a.mpart = nullptr;
     a.items = pl.items.p;
     a.part_off = pl.part_off.p;
     a.partials = partials;
@@ -852,20 +1131,25 @@ static SweepArgs make_args(Context* ctx, const Lists* L, const Tree* bt, const T
     return a;
 }
 
-void prepare_plan(Context* ctx, Lists* L, int degree) {
-    if (!L->plan.valid || L->plan.degree != degree) build_plan(ctx, L, degree);
+
+void prepare_plan(Context* ctx, Lists* L, int degree, int precision) {
+    const bool mutual = precision == BLTC_PRECISION_MIXED && L->bt == L->st;
+    if (!L->plan.valid || L->plan.degree != degree || L->plan.mutual != (mutual && L->n_dir > 0))
+        build_plan(ctx, L, degree, mutual);
 }
 
 void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
               double* phi) {
     check_eval(L, bt, st, p, phi);
     cudaStream_t s = ctx->stream;
-    prepare_plan(ctx, L, p.degree);
+    prepare_plan(ctx, L, p.degree, p.precision);
     Plan& pl = L->plan;
     DBuf<double> partials(ctx, pl.partial_len);
+    DBuf<double> mpart(ctx, pl.mutual ? pl.mpart_len : 0);
     DBuf<unsigned int> counter(ctx, 1);
     BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
-    const SweepArgs a = make_args(ctx, L, bt, st, p, partials.p, counter.p);
+    SweepArgs a = make_args(ctx, L, bt, st, p, partials.p, counter.p);
+    a.mpart = pl.mutual ? mpart.p : nullptr;
     const int per_sm = p.precision == BLTC_PRECISION_MIXED ? kMinBlocks : 2;
     const unsigned grid = static_cast<unsigned>(
         std::min<int64_t>(pl.n_items, per_sm * static_cast<int64_t>(std::max(1, ctx->sm_count))));
@@ -893,7 +1177,7 @@ void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc
     ctx->mark(Context::kSweepEnd);
     k_finalize<<<static_cast<unsigned>(L->n_batches), 256, 0, s>>>(
         bt->leaves.p, bt->begin.p, bt->count.p, bt->perm.p, pl.n_chunks.p, pl.part_off.p,
-        partials.p, phi); ++ctx->launches;
+        partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi); ++ctx->launches;
     BLTC_LAUNCH_CHECK("finalize");
     ctx->mark(Context::kEnd);
 }
@@ -902,9 +1186,10 @@ void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
     if (jobs.empty()) return;
     cudaStream_t s = ctx->stream;
     const int R = static_cast<int>(jobs.size());
-    std::vector<DBuf<double>> partials;
+    std::vector<DBuf<double>> partials, mparts;
     std::vector<SweepArgs> args;
     partials.reserve(jobs.size());
+    mparts.reserve(jobs.size());
     args.reserve(jobs.size());
     DBuf<unsigned int> counter(ctx, 1);
     BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
@@ -914,11 +1199,14 @@ void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
         const SweepJob& j = jobs[static_cast<size_t>(r)];
         require(j.p.precision == BLTC_PRECISION_MIXED, "serving runs the mixed-precision sweep");
         check_eval(j.L, j.bt, j.st, j.p, j.phi);
-        if (!j.L->plan.valid || j.L->plan.degree != j.p.degree)
+        if (!j.L->plan.valid || j.L->plan.degree != j.p.degree ||
+            j.L->plan.mutual != (j.L->bt == j.L->st && j.L->n_dir > 0))
             throw Error(BLTC_ERR_STATE, "evaluate_multi: request has no work plan");
         const Plan& pl = j.L->plan;
         partials.emplace_back(ctx, pl.partial_len);
+        mparts.emplace_back(ctx, pl.mutual ? pl.mpart_len : 0);
         args.push_back(make_args(ctx, j.L, j.bt, j.st, j.p, partials.back().p, counter.p));
+        args.back().mpart = pl.mutual ? mparts.back().p : nullptr;
         for (int64_t i = 0; i < pl.n_items; ++i)
             all.push_back({pl.h_cost[static_cast<size_t>(i)], make_int2(r, static_cast<int>(i))});
     }
@@ -961,22 +1249,38 @@ void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
         const Plan& pl = j.L->plan;
         k_finalize<<<static_cast<unsigned>(j.L->n_batches), 256, 0, s>>>(
             j.bt->leaves.p, j.bt->begin.p, j.bt->count.p, j.bt->perm.p, pl.n_chunks.p, pl.part_off.p,
-            partials[static_cast<size_t>(r)].p, j.phi); ++ctx->launches;
+            partials[static_cast<size_t>(r)].p, j.L->dir_off.p, pl.dir_sel.p,
+            pl.mutual ? pl.dir_moff.p : nullptr, pl.mutual ? mparts[static_cast<size_t>(r)].p : nullptr,
+            j.phi); ++ctx->launches;
         BLTC_LAUNCH_CHECK("finalize multi");
     }
 }
 
-void interaction_counts(Context* ctx, const Lists* L, int64_t* n_dir, int64_t* n_app) {
-    DBuf<int64_t> w(ctx, 2);
-    BLTC_CUDA(cudaMemsetAsync(w.p, 0, 2 * sizeof(int64_t), ctx->stream));
+static void counts(Context* ctx, const Lists* L, const uint8_t* dir_sel, int64_t* out3) {
+    DBuf<int64_t> w(ctx, 3);
+    BLTC_CUDA(cudaMemsetAsync(w.p, 0, 3 * sizeof(int64_t), ctx->stream));
     const int64_t np1 = L->degree + 1;
     k_counts<<<grid_for(L->n_batches, 128), 128, 0, ctx->stream>>>(
         L->bt->leaves.p, L->bt->count.p, L->st->count.p, L->app_off.p, L->dir_off.p,
-        L->dir_ids.p, L->n_batches, np1 * np1 * np1, reinterpret_cast<unsigned long long*>(w.p)); ++ctx->launches;
+        L->dir_ids.p, dir_sel, L->n_batches, np1 * np1 * np1, reinterpret_cast<unsigned long long*>(w.p)); ++ctx->launches;
     BLTC_LAUNCH_CHECK("counts");
-    const int64_t* r = ctx->read_words(w.p, 2);
+    const int64_t* r = ctx->read_words(w.p, 3);
+    for (int i = 0; i < 3; ++i) out3[i] = r[i];
+}
+
+void interaction_counts(Context* ctx, const Lists* L, int64_t* n_dir, int64_t* n_app) {
+    int64_t r[3];
+    counts(ctx, L, nullptr, r);
     if (n_dir) *n_dir = r[0];
     if (n_app) *n_app = r[1];
+}
+
+int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision) {
+    require(degree == L->degree, "evaluations: the lists were built for another degree");
+    prepare_plan(ctx, L, degree, precision);
+    int64_t r[3];
+    counts(ctx, L, L->plan.dir_sel.p, r);
+    return r[1] + r[2];
 }
 
 }  // namespace bltc

@@ -48,34 +48,60 @@ __device__ __forceinline__ double cheb_point(const double* t, int k, int n, doub
     return __dadd_rn(lo, __dmul_rn(__dmul_rn(0.5, __dadd_rn(t[k], 1.0)), __dsub_rn(hi, lo)));
 }
 
-template <typename F>
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// P2M (Eq. 12 with Eq. 14-15 factored): the modified charges of one leaf's particle range.
+// Phase A turns each particle of a 128-particle tile into its three 1-D factor vectors
+// a_l[k] = L_k(y_l) (barycentric form, exact hits of Sec. II-C), with q folded into a_1;
+// phase B adds a_1[k1] a_2[k2] a_3[k3] over the tile with one thread per (k1, k2) and
+// particle group, n+1 accumulators per thread.
+//   Mixed: y - s_k comes from FP32 (hi, lo) pairs of y - c and s_k - c (c the box midpoint),
+//   so each particle costs two FP64 operations per dimension instead of n+1; the result has
+//   the relative error of rounding the FP64 difference to FP32.  1/(y - s_k) is the SFU
+//   reciprocal (w_k is +-1 or +-1/2, so w_k / (y - s_k) is that reciprocal scaled exactly).
+//   The barycentric denominator is summed by TwoSum (its terms alternate in sign).
+//   FP64: differences, divisions and sums in double.
+// Shared memory: fac2 [kTile][np4] (dimension 3, one row per particle padded to a multiple
+// of 4 for vector loads), then fac0, fac1 [np1][kTile + 1]; at the end the group-reduction
+// buffer [G][P].  NMAX bounds n + 1 (register arrays).
+template <typename F, int NMAX>
 __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    F* fac = reinterpret_cast<F*>(smem_raw);       // [3][np1][kTile + 1]
     const int np1 = a.np1, n = np1 - 1;
+    const int np4 = (np1 + 3) & ~3;
     const int pairs = np1 * np1;
     const int P = pairs * np1;
     const int G = max(1, kThreads / pairs);
     const int stride = kTile + 1;
+    F* fac2 = reinterpret_cast<F*>(smem_raw);
+    F* fac0 = fac2 + kTile * np4;
+    F* fac1 = fac0 + np1 * stride;
     const int4 it = a.items[blockIdx.x];
     const int node = a.slot_node[it.x];
-    const double lo[3] = {a.lo[3 * node], a.lo[3 * node + 1], a.lo[3 * node + 2]};
-    const double hi[3] = {a.hi[3 * node], a.hi[3 * node + 1], a.hi[3 * node + 2]};
     const int tid = threadIdx.x;
     const bool active = tid < pairs * G;
     const int p = tid % pairs, g = tid / pairs;
     const int k1 = p / np1, k2 = p % np1;
-    // Per-thread sums over its particles: blocks of the tile summed in F, folded into a
-    // TwoSum (hi, lo) accumulator so FP32 rounding does not grow with the particle count.
-    F acc[kMaxNp1], lo_acc[kMaxNp1];
+    F acc[NMAX], lo_acc[NMAX];
 #pragma unroll
-    for (int k = 0; k < kMaxNp1; ++k) acc[k] = lo_acc[k] = F(0);
-    // the 3(n+1) Chebyshev points of this cluster, once per block
-    __shared__ double s_pts[3 * kMaxNp1];
+    for (int k = 0; k < NMAX; ++k) acc[k] = lo_acc[k] = F(0);
+    __shared__ double s_c[3];
+    __shared__ double s_pts[3 * NMAX];          // the cluster's Chebyshev points (FP64 path)
+    __shared__ float s_hi[3 * NMAX], s_lo[3 * NMAX];   // s_k - c as FP32 pairs (mixed path)
+    if (tid < 3) s_c[tid] = __dmul_rn(0.5, __dadd_rn(a.lo[3 * node + tid], a.hi[3 * node + tid]));
+    __syncthreads();
     if (tid < 3 * np1) {
         const int d = tid / np1, k = tid - d * np1;
-        s_pts[tid] = cheb_point(a.cheb_t, k, n, d == 0 ? lo[0] : (d == 1 ? lo[1] : lo[2]),
-                                d == 0 ? hi[0] : (d == 1 ? hi[1] : hi[2]));
+        const double sk = cheb_point(a.cheb_t, k, n, a.lo[3 * node + d], a.hi[3 * node + d]);
+        s_pts[tid] = sk;
+        const double r = __dsub_rn(sk, s_c[d]);
+        const float h = __double2float_rn(r);
+        s_hi[tid] = h;
+        s_lo[tid] = __double2float_rn(__dsub_rn(r, static_cast<double>(h)));
     }
 
     for (int j0 = it.y; j0 < it.z; j0 += kTile) {
@@ -86,102 +112,144 @@ __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
             if (j < m) {
                 const int pos = j0 + j;
                 const double yv = d == 0 ? a.px[pos] : (d == 1 ? a.py[pos] : a.pz[pos]);
-                const double* pts = s_pts + d * np1;
                 const double qv = d == 0 ? a.pq[pos] : 1.0;
-                double dk[kMaxNp1];
+                F vals[NMAX];
+#pragma unroll
+                for (int k = 0; k < NMAX; ++k) vals[k] = F(0);
                 int hit = -1;
+                if constexpr (sizeof(F) == 4) {
+                    const double r = __dsub_rn(yv, s_c[d]);
+                    const float yh = __double2float_rn(r);
+                    const float yl = __double2float_rn(__dsub_rn(r, static_cast<double>(yh)));
+                    float dk[NMAX];
 #pragma unroll
-                for (int k = 0; k < kMaxNp1; ++k) {
-                    if (k < np1) {
-                        dk[k] = yv - pts[k];
-                        // FP64: |y - s_k| < DBL_MIN.  Mixed: the FP32 difference underflows
-                        // (|fp32(y - s_k)| < FLT_MIN), a superset changing L by < 1e-29.
-                        const bool h = sizeof(F) == 4
-                                           ? fabsf(__double2float_rn(dk[k])) < 1.17549435e-38f
-                                           : fabs(dk[k]) < 2.2250738585072014e-308;
-                        if (h && hit < 0) hit = k;
-                    }
-                }
-                F* row = fac + d * np1 * stride + j;
-                if (hit >= 0) {
-#pragma unroll
-                    for (int k = 0; k < kMaxNp1; ++k)
-                        if (k < np1) row[k * stride] = k == hit ? F(qv) : F(0);
-                } else {
-                    F raw[kMaxNp1];
-                    F den = F(0), den_lo = F(0);
-#pragma unroll
-                    for (int k = 0; k < kMaxNp1; ++k) {
+                    for (int k = 0; k < NMAX; ++k) {
                         if (k < np1) {
-                            const F w = ((k == 0 || k == n) ? F(0.5) : F(1)) * ((k & 1) ? F(-1) : F(1));
-                            raw[k] = w / F(dk[k]);
-                            if (sizeof(F) == 4) {
-                                // the barycentric denominator by TwoSum: its terms alternate
-                                // in sign, and a plain FP32 sum loses digits to cancellation
-                                const F s = den + raw[k];
-                                const F bb = s - den;
-                                den_lo += (den - (s - bb)) + (raw[k] - bb);
-                                den = s;
-                            } else {
-                                den += raw[k];
-                            }
+                            dk[k] = __fadd_rn(__fsub_rn(yh, s_hi[d * np1 + k]), __fsub_rn(yl, s_lo[d * np1 + k]));
+                            // |y - s_k| below FLT_MIN is an exact hit (a superset of the FP64
+                            // rule |y - s_k| < DBL_MIN, changing L by < 1e-29)
+                            if (fabsf(dk[k]) < 1.17549435e-38f && hit < 0) hit = k;
                         }
                     }
-                    const F scale = F(qv) / (den + den_lo);
+                    if (hit < 0) {
+                        float den = 0.f, den_lo = 0.f;
 #pragma unroll
-                    for (int k = 0; k < kMaxNp1; ++k)
-                        if (k < np1) row[k * stride] = raw[k] * scale;
+                        for (int k = 0; k < NMAX; ++k) {
+                            if (k < np1) {
+                                const float w = ((k == 0 || k == n) ? 0.5f : 1.f) * ((k & 1) ? -1.f : 1.f);
+                                vals[k] = w * rcp_approx(dk[k]);
+                                const float sum = den + vals[k];
+                                const float bb = sum - den;
+                                den_lo += (den - (sum - bb)) + (vals[k] - bb);
+                                den = sum;
+                            }
+                        }
+                        const float scale = static_cast<float>(qv) / (den + den_lo);
+#pragma unroll
+                        for (int k = 0; k < NMAX; ++k) vals[k] *= scale;
+                    }
+                } else {
+                    const double* pts = s_pts + d * np1;
+                    double dk[NMAX];
+#pragma unroll
+                    for (int k = 0; k < NMAX; ++k) {
+                        if (k < np1) {
+                            dk[k] = yv - pts[k];
+                            if (fabs(dk[k]) < 2.2250738585072014e-308 && hit < 0) hit = k;
+                        }
+                    }
+                    if (hit < 0) {
+                        double den = 0.0;
+#pragma unroll
+                        for (int k = 0; k < NMAX; ++k) {
+                            if (k < np1) {
+                                const double w = ((k == 0 || k == n) ? 0.5 : 1.0) * ((k & 1) ? -1.0 : 1.0);
+                                vals[k] = w / dk[k];
+                                den += vals[k];
+                            }
+                        }
+                        const double scale = qv / den;
+#pragma unroll
+                        for (int k = 0; k < NMAX; ++k) vals[k] *= scale;
+                    }
+                }
+                if (hit >= 0) {
+#pragma unroll
+                    for (int k = 0; k < NMAX; ++k) vals[k] = k == hit ? F(qv) : F(0);
+                }
+                if (d == 2) {
+                    F* row = fac2 + j * np4;
+#pragma unroll
+                    for (int k = 0; k < NMAX; ++k)
+                        if (k < np1) row[k] = vals[k];
+                    for (int k = np1; k < np4; ++k) row[k] = F(0);
+                } else {
+                    F* col = (d == 0 ? fac0 : fac1) + j;
+#pragma unroll
+                    for (int k = 0; k < NMAX; ++k)
+                        if (k < np1) col[k * stride] = vals[k];
                 }
             }
         }
         __syncthreads();
         if (active) {
-            const F* f0 = fac + k1 * stride;
-            const F* f1 = fac + (np1 + k2) * stride;
-            const F* f2 = fac + 2 * np1 * stride;
-            if constexpr (sizeof(F) == 4) {
-                F blk[kMaxNp1];
+            const F* f0 = fac0 + k1 * stride;
+            const F* f1 = fac1 + k2 * stride;
+            F blk[NMAX + 3];
 #pragma unroll
-                for (int k = 0; k < kMaxNp1; ++k) blk[k] = F(0);
-                for (int j = g; j < m; j += G) {
-                    const F a12 = f0[j] * f1[j];
+            for (int k = 0; k < NMAX + 3; ++k) blk[k] = F(0);
+            for (int j = g; j < m; j += G) {
+                const F a12 = f0[j] * f1[j];
+                const F* row = fac2 + j * np4;
+                if constexpr (sizeof(F) == 4) {
 #pragma unroll
-                    for (int k = 0; k < kMaxNp1; ++k)
-                        if (k < np1) blk[k] += a12 * f2[k * stride + j];
+                    for (int k4 = 0; k4 < NMAX; k4 += 4) {
+                        if (k4 < np1) {
+                            const float4 v = *reinterpret_cast<const float4*>(row + k4);
+                            blk[k4] += a12 * v.x;
+                            blk[k4 + 1] += a12 * v.y;
+                            blk[k4 + 2] += a12 * v.z;
+                            blk[k4 + 3] += a12 * v.w;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NMAX; ++k)
+                        if (k < np1) blk[k] += a12 * row[k];
                 }
+            }
+            if constexpr (sizeof(F) == 4) {
+                // fold the tile's FP32 sums into a TwoSum accumulator
 #pragma unroll
-                for (int k = 0; k < kMaxNp1; ++k) {
+                for (int k = 0; k < NMAX; ++k) {
                     if (k < np1) {
-                        const F s = acc[k] + blk[k];
-                        const F bb = s - acc[k];
-                        lo_acc[k] += (acc[k] - (s - bb)) + (blk[k] - bb);
-                        acc[k] = s;
+                        const F sum = acc[k] + blk[k];
+                        const F bb = sum - acc[k];
+                        lo_acc[k] += (acc[k] - (sum - bb)) + (blk[k] - bb);
+                        acc[k] = sum;
                     }
                 }
             } else {
-                for (int j = g; j < m; j += G) {
-                    const F a12 = f0[j] * f1[j];
 #pragma unroll
-                    for (int k = 0; k < kMaxNp1; ++k)
-                        if (k < np1) acc[k] += a12 * f2[k * stride + j];
-                }
+                for (int k = 0; k < NMAX; ++k)
+                    if (k < np1) acc[k] += blk[k];
             }
         }
     }
     // Sum the particle groups in a fixed order.
     __syncthreads();
-    F* red = fac;                                   // [G][P]
+    F* red = fac2;                                  // [G][P]
     if (active) {
 #pragma unroll
-        for (int k = 0; k < kMaxNp1; ++k)
+        for (int k = 0; k < NMAX; ++k)
             if (k < np1) red[g * P + p * np1 + k] = acc[k] + lo_acc[k];
     }
     __syncthreads();
     double* out = a.partial + static_cast<int64_t>(blockIdx.x) * P;
     for (int o = tid; o < P; o += kThreads) {
-        double s = 0.0;
-        for (int gg = 0; gg < G; ++gg) s += static_cast<double>(red[gg * P + o]);
-        out[o] = s;
+        double sum = 0.0;
+        for (int gg = 0; gg < G; ++gg) sum += static_cast<double>(red[gg * P + o]);
+        out[o] = sum;
     }
 }
 
@@ -277,100 +345,109 @@ struct M2MArgs {
     int np1;
 };
 
-// Exact transfer of the children's modified charges to their parent (NEXT to Eq. 12: the
-// parent's Lagrange polynomials L^P_k have degree n in each variable, so a child's tensor
-// interpolant reproduces them exactly and
+// Exact transfer of the children's modified charges to their parent (the parent's Lagrange
+// polynomials L^P_k have degree n in each variable, so a child's tensor interpolant (Eq. 4-8)
+// reproduces them exactly and, from Eq. 12,
 //   qhat^P_k = sum_children sum_k' L^P_k1(s^c_k'1) L^P_k2(s^c_k'2) L^P_k3(s^c_k'3) qhat^c_k').
-// One block per parent: for each child, the three (n+1)x(n+1) matrices T_l[k][k'] =
-// L^P_k(s^c_k'l) (barycentric form, exact hits as in Sec. II-C), then three mode products.
-// FP64 throughout.
-__global__ void __launch_bounds__(256) k_m2m(M2MArgs a, const int32_t* __restrict__ nodes) {
+// GB300's FP64 rate is low per SM, so the work is spread over one block per (parent, child)
+// pair: the three (n+1)x(n+1) matrices T_l[k][k'] = L^P_k(s^c_k'l) (barycentric form, exact
+// hits as in Sec. II-C), then three mode products into the pair's scratch row.  A second
+// kernel adds a parent's rows in child order.  FP64 throughout.
+__global__ void __launch_bounds__(256) k_m2m_child(M2MArgs a, const int32_t* __restrict__ nodes,
+                                                   double* __restrict__ scratch) {
     extern __shared__ __align__(16) double m2m_smem[];
-    const int v = nodes[blockIdx.x];
+    const int v = nodes[blockIdx.x >> 3], ci = static_cast<int>(blockIdx.x & 7);
+    if (ci >= a.nch[v]) return;
+    const int c = a.child[8 * v + ci];
     const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1, n2 = np1 * np1;
     double* A = m2m_smem;            // child charges, then the second mode product
     double* Bm = A + P;              // first mode product
-    double* out = Bm + P;            // the parent's charges
-    double* T = out + P;             // [3][np1][np1]
+    double* T = Bm + P;              // [3][np1][np1]
     double* sp = T + 3 * n2;         // parent points [3][np1]
     const int tid = threadIdx.x;
     if (tid < 3 * np1) {
         const int d = tid / np1, k = tid - d * np1;
         sp[tid] = cheb_point(a.cheb_t, k, n, a.lo[3 * v + d], a.hi[3 * v + d]);
     }
-    for (int i = tid; i < P; i += blockDim.x) out[i] = 0.0;
-    const int nc = a.nch[v];
-    for (int ci = 0; ci < nc; ++ci) {
-        const int c = a.child[8 * v + ci];
-        __syncthreads();
-        const double* qc = a.qhat64 + static_cast<int64_t>(a.qslot[c]) * P;
-        for (int i = tid; i < P; i += blockDim.x) A[i] = qc[i];
-        if (tid < 3 * np1) {
-            // column k' of T_d: the parent's 1-D Lagrange values at the child's point s^c_k'
-            const int d = tid / np1, kp = tid - d * np1;
-            const double y = cheb_point(a.cheb_t, kp, n, a.lo[3 * c + d], a.hi[3 * c + d]);
-            const double* s = sp + d * np1;
-            double* col = T + d * n2 + kp;            // T_d[k][kp] at col[k * np1]
-            int hit = -1;
-            for (int k = 0; k < np1; ++k)
-                if (hit < 0 && fabs(y - s[k]) < 2.2250738585072014e-308) hit = k;
-            if (hit >= 0) {
-                for (int k = 0; k < np1; ++k) col[k * np1] = k == hit ? 1.0 : 0.0;
-            } else {
-                double den = 0.0;
-                for (int k = 0; k < np1; ++k) {
-                    const double w = ((k == 0 || k == n) ? 0.5 : 1.0) * ((k & 1) ? -1.0 : 1.0);
-                    den += w / (y - s[k]);
-                }
-                for (int k = 0; k < np1; ++k) {
-                    const double w = ((k == 0 || k == n) ? 0.5 : 1.0) * ((k & 1) ? -1.0 : 1.0);
-                    col[k * np1] = (w / (y - s[k])) / den;
-                }
+    const double* qc = a.qhat64 + static_cast<int64_t>(a.qslot[c]) * P;
+    for (int i = tid; i < P; i += blockDim.x) A[i] = qc[i];
+    __syncthreads();
+    if (tid < 3 * np1) {
+        // column k' of T_d: the parent's 1-D Lagrange values at the child's point s^c_k'
+        const int d = tid / np1, kp = tid - d * np1;
+        const double y = cheb_point(a.cheb_t, kp, n, a.lo[3 * c + d], a.hi[3 * c + d]);
+        const double* sv = sp + d * np1;
+        double* col = T + d * n2 + kp;            // T_d[k][kp] at col[k * np1]
+        int hit = -1;
+        for (int k = 0; k < np1; ++k)
+            if (hit < 0 && fabs(y - sv[k]) < 2.2250738585072014e-308) hit = k;
+        if (hit >= 0) {
+            for (int k = 0; k < np1; ++k) col[k * np1] = k == hit ? 1.0 : 0.0;
+        } else {
+            double den = 0.0;
+            for (int k = 0; k < np1; ++k) {
+                const double w = ((k == 0 || k == n) ? 0.5 : 1.0) * ((k & 1) ? -1.0 : 1.0);
+                den += w / (y - sv[k]);
             }
-        }
-        __syncthreads();
-        // B[k1,k2',k3'] = sum_k1' T1[k1][k1'] A[k1',k2',k3']
-        for (int i = tid; i < P; i += blockDim.x) {
-            const int k1 = i / n2, r = i - k1 * n2;
-            double acc = 0.0;
-            for (int j = 0; j < np1; ++j) acc += T[k1 * np1 + j] * A[j * n2 + r];
-            Bm[i] = acc;
-        }
-        __syncthreads();
-        // C[k1,k2,k3'] = sum_k2' T2[k2][k2'] B[k1,k2',k3']   (into A)
-        for (int i = tid; i < P; i += blockDim.x) {
-            const int k1 = i / n2, r = i - k1 * n2, k2 = r / np1, k3 = r - k2 * np1;
-            double acc = 0.0;
-            for (int j = 0; j < np1; ++j) acc += T[n2 + k2 * np1 + j] * Bm[k1 * n2 + j * np1 + k3];
-            A[i] = acc;
-        }
-        __syncthreads();
-        // out[k1,k2,k3] += sum_k3' T3[k3][k3'] C[k1,k2,k3']
-        for (int i = tid; i < P; i += blockDim.x) {
-            const int k3 = i % np1, base = i - k3;
-            double acc = 0.0;
-            for (int j = 0; j < np1; ++j) acc += T[2 * n2 + k3 * np1 + j] * A[base + j];
-            out[i] += acc;
+            for (int k = 0; k < np1; ++k) {
+                const double w = ((k == 0 || k == n) ? 0.5 : 1.0) * ((k & 1) ? -1.0 : 1.0);
+                col[k * np1] = (w / (y - sv[k])) / den;
+            }
         }
     }
     __syncthreads();
-    double* q = a.qhat64 + static_cast<int64_t>(a.qslot[v]) * P;
+    // B[k1,k2',k3'] = sum_k1' T1[k1][k1'] A[k1',k2',k3']
     for (int i = tid; i < P; i += blockDim.x) {
-        q[i] = out[i];
-        if (a.qhat32) a.qhat32[static_cast<int64_t>(a.qslot[v]) * P + i] = static_cast<float>(out[i]);
+        const int k1 = i / n2, r = i - k1 * n2;
+        double acc = 0.0;
+        for (int j = 0; j < np1; ++j) acc += T[k1 * np1 + j] * A[j * n2 + r];
+        Bm[i] = acc;
+    }
+    __syncthreads();
+    // C[k1,k2,k3'] = sum_k2' T2[k2][k2'] B[k1,k2',k3']   (into A)
+    for (int i = tid; i < P; i += blockDim.x) {
+        const int k1 = i / n2, r = i - k1 * n2, k2 = r / np1, k3 = r - k2 * np1;
+        double acc = 0.0;
+        for (int j = 0; j < np1; ++j) acc += T[n2 + k2 * np1 + j] * Bm[k1 * n2 + j * np1 + k3];
+        A[i] = acc;
+    }
+    __syncthreads();
+    // row[k1,k2,k3] = sum_k3' T3[k3][k3'] C[k1,k2,k3']
+    double* row = scratch + static_cast<int64_t>(blockIdx.x) * P;
+    for (int i = tid; i < P; i += blockDim.x) {
+        const int k3 = i % np1, base = i - k3;
+        double acc = 0.0;
+        for (int j = 0; j < np1; ++j) acc += T[2 * n2 + k3 * np1 + j] * A[base + j];
+        row[i] = acc;
+    }
+}
+
+// qhat of each parent: its children's rows added in child order.
+__global__ void k_m2m_sum(M2MArgs a, const int32_t* __restrict__ nodes,
+                          const double* __restrict__ scratch) {
+    const int v = nodes[blockIdx.x], nc = a.nch[v];
+    const int P = a.np1 * a.np1 * a.np1;
+    const double* rows = scratch + static_cast<int64_t>(blockIdx.x) * 8 * P;
+    double* q = a.qhat64 + static_cast<int64_t>(a.qslot[v]) * P;
+    float* q32 = a.qhat32 ? a.qhat32 + static_cast<int64_t>(a.qslot[v]) * P : nullptr;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        double s = 0.0;
+        for (int ci = 0; ci < nc; ++ci) s += rows[static_cast<int64_t>(ci) * P + i];
+        q[i] = s;
+        if (q32) q32[i] = static_cast<float>(s);
     }
 }
 
 size_t m2m_smem_bytes(int np1) {
     const size_t P = static_cast<size_t>(np1) * np1 * np1;
-    return sizeof(double) * (3 * P + 3 * static_cast<size_t>(np1) * np1 + 3 * np1);
+    return sizeof(double) * (2 * P + 3 * static_cast<size_t>(np1) * np1 + 3 * np1);
 }
 
 template <typename F>
 size_t upward_smem(int np1) {
-    const int pairs = np1 * np1, P = pairs * np1;
+    const int pairs = np1 * np1, P = pairs * np1, np4 = (np1 + 3) & ~3;
     const int G = std::max(1, kThreads / pairs);
-    size_t a = sizeof(F) * 3 * np1 * (kTile + 1);
+    size_t a = sizeof(F) * (static_cast<size_t>(kTile) * np4 + 2 * static_cast<size_t>(np1) * (kTile + 1));
     size_t b = sizeof(F) * static_cast<size_t>(G) * P;
     return std::max(a, b);
 }
@@ -383,6 +460,13 @@ int upward_smem_max() {
     size_t m = 0;
     for (int np1 = 2; np1 <= BLTC_MAX_DEGREE + 1; ++np1) m = std::max(m, upward_smem<F>(np1));
     return static_cast<int>(m);
+}
+
+template <typename F, int NMAX>
+void launch_partial(const UpArgs& a, int32_t n_items, size_t smem, cudaStream_t s) {
+    BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<F, NMAX>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, upward_smem_max<F>()));
+    k_upward_partial<F, NMAX><<<n_items, kThreads, smem, s>>>(a);
 }
 
 }  // namespace
@@ -457,17 +541,14 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
     if (n_items > 0) {
         if (precision == BLTC_PRECISION_MIXED) {
             const size_t sm = upward_smem<float>(np1);
-            BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<float>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           upward_smem_max<float>()));
-            k_upward_partial<float><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
+            if (np1 <= 9) launch_partial<float, 9>(a, n_items, sm, s);
+            else launch_partial<float, BLTC_MAX_DEGREE + 1>(a, n_items, sm, s);
         } else {
             const size_t sm = upward_smem<double>(np1);
-            BLTC_CUDA(cudaFuncSetAttribute(k_upward_partial<double>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           upward_smem_max<double>()));
-            k_upward_partial<double><<<n_items, kThreads, sm, s>>>(a); ++ctx->launches;
+            if (np1 <= 9) launch_partial<double, 9>(a, n_items, sm, s);
+            else launch_partial<double, BLTC_MAX_DEGREE + 1>(a, n_items, sm, s);
         }
+        ++ctx->launches;
         BLTC_LAUNCH_CHECK("upward partial");
     }
     k_upward_reduce<<<n_slots, 256, 0, s>>>(partial.p, item0.p, P, st->qhat64.p,
@@ -494,11 +575,21 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
             M2MArgs ma{st->nch.p, st->child.p, st->qslot.p, st->lo.p, st->hi.p, a.cheb_t, st->qhat64.p,
                        precision == BLTC_PRECISION_MIXED ? st->qhat32.p : nullptr, np1};
             const size_t sm = m2m_smem_bytes(np1);
-            BLTC_CUDA(cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            BLTC_CUDA(cudaFuncSetAttribute(k_m2m_child, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(m2m_smem_bytes(BLTC_MAX_DEGREE + 1))));
+            // scratch rows for 8 children per parent, at most ~32 MB at a time
+            int32_t hmax = 0;
+            for (int L = 0; L < nl; ++L) hmax = std::max(hmax, h[L]);
+            const int32_t chunk = static_cast<int32_t>(std::max<int64_t>(
+                1, std::min<int64_t>(hmax, (int64_t(32) << 20) / (8 * static_cast<int64_t>(P) * 8))));
+            DBuf<double> scratch(ctx, static_cast<int64_t>(chunk) * 8 * P);
             for (int L = nl - 1; L >= 0; --L) {
-                if (h[L] == 0) continue;
-                k_m2m<<<h[L], 256, sm, s>>>(ma, list.p + off[L]); ++ctx->launches;
+                for (int32_t p0 = 0; p0 < h[L]; p0 += chunk) {
+                    const int32_t np = std::min(chunk, h[L] - p0);
+                    const int32_t* nodes = list.p + off[L] + p0;
+                    k_m2m_child<<<8 * np, 256, sm, s>>>(ma, nodes, scratch.p); ++ctx->launches;
+                    k_m2m_sum<<<np, 256, 0, s>>>(ma, nodes, scratch.p); ++ctx->launches;
+                }
             }
             BLTC_LAUNCH_CHECK("upward m2m");
         }

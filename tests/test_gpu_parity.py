@@ -378,3 +378,37 @@ def test_full_size_1e6_sampled(gpu):
     assert_close_abs(want[idx], got64[idx], want_abs[idx], FP64_REL2, FP64_ELEM, "1e6 fp64 sampled")
     e = oracle.rel_err(got64, gotmx)
     assert e <= MIXED_REL2, e
+
+
+def test_mutual_pairs_counted_once(gpu):
+    # In mixed precision with batches = sources, a leaf pair in each other's direct list is
+    # evaluated once for both batches; the count of kernel evaluations must equal the
+    # paper's count minus the partner side of every such pair (found here from the oracle's
+    # lists), and the FP64 path evaluates everything.
+    x, y, z, q = system("cube", 60000, 20031881)
+    st, X = gpu_tree(gpu, x, y, z, q, 700)
+    try:
+        p = b.params(6, 0.7, 700)
+        L = b.bltc_lists_build(gpu.h, st, st, p)
+        try:
+            c = b.bltc_stats(gpu.h, L)
+            ev_mx = b.bltc_evaluations(gpu.h, L, p)
+            ev_64 = b.bltc_evaluations(gpu.h, L, b.params(6, 0.7, 700, precision=b.BLTC_PRECISION_FP64))
+        finally:
+            b.bltc_lists_destroy(L)
+        ot = oracle.Tree(x, y, z, 700)
+        ol = oracle.lists(ot, ot, 0.7, 6)
+        leaf_of = {int(v): i for i, v in enumerate(ot.leaves)}
+        dirs = [set(ol["direct_ids"][ol["direct_off"][i]:ol["direct_off"][i + 1]].tolist())
+                for i in range(len(ot.leaves))]
+        saved = 0
+        for i, A in enumerate(ot.leaves):
+            for C in dirs[i]:
+                j = leaf_of.get(int(C))
+                if j is not None and j < i and int(A) in dirs[j]:
+                    saved += int(ot.count[A]) * int(ot.count[C])   # i's side of a pair owned by j
+        assert saved > 0
+        assert ev_64 == c["direct"] + c["approx"]
+        assert ev_mx == c["direct"] + c["approx"] - saved
+    finally:
+        b.bltc_tree_destroy(st)
