@@ -926,24 +926,47 @@ __global__ void k_item_costs(PlanArgs a, const int4* __restrict__ items, int64_t
 }
 
 // Per target: its items' partials in item order, then (mutual pairs) the rows that partner
-// batches wrote for it, in list order; scattered to the caller's order.
+// batches wrote for it, in list order; scattered to the caller's order.  Each thread keeps 8
+// targets so that every row is read with 8 independent, coalesced loads in flight.
 __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* __restrict__ b_begin,
                            const int32_t* __restrict__ b_count, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ n_chunks, const int64_t* __restrict__ part_off,
                            const double* __restrict__ partials, const int32_t* __restrict__ dir_off,
                            const uint8_t* __restrict__ dir_sel, const int64_t* __restrict__ dir_moff,
                            const double* __restrict__ mpart, double* __restrict__ phi) {
+    constexpr int U = 8;
     const int b = blockIdx.x;
     const int B = b_leaves[b];
     const int tb = b_begin[B], nb = b_count[B], K = n_chunks[b];
     const double* p = partials + part_off[b];
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < K; ++c) s += p[static_cast<int64_t>(c) * nb + t];
-        if (mpart)
-            for (int e = dir_off[b]; e < dir_off[b + 1]; ++e)
-                if (dir_sel[e] & kSelSkip) s += mpart[dir_moff[e] + t];
-        phi[perm[tb + t]] = s;
+    for (int t0 = 0; t0 < nb; t0 += U * static_cast<int>(blockDim.x)) {
+        double s[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) s[u] = 0.0;
+        for (int c = 0; c < K; ++c) {
+            const double* row = p + static_cast<int64_t>(c) * nb;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
+                if (t < nb) s[u] += row[t];
+            }
+        }
+        if (mpart) {
+            for (int e = dir_off[b]; e < dir_off[b + 1]; ++e) {
+                if (!(dir_sel[e] & kSelSkip)) continue;
+                const double* row = mpart + dir_moff[e];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
+                    if (t < nb) s[u] += row[t];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
+            if (t < nb) phi[perm[tb + t]] = s[u];
+        }
     }
 }
 
@@ -997,10 +1020,13 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
     pl.mutual = mutual && L->bt == L->st && L->n_dir > 0;
     pl.mpart_len = 0;
     pl.dir_moff = DBuf<int64_t>();
+    // words: [0] total cost, [1] items (int32), [2] partial length, [3] mutual row length
+    DBuf<int64_t> cost(ctx, nb), part_len(ctx, nb), words(ctx, 4);
+    BLTC_CUDA(cudaMemsetAsync(words.p, 0, 4 * sizeof(int64_t), s));
     if (pl.mutual) {
         const int64_t m = L->st->n_nodes;
         DBuf<int32_t> lidx(ctx, m), partner(ctx, L->n_dir);
-        DBuf<int64_t> mlen(ctx, L->n_dir), moff_e(ctx, L->n_dir), tot(ctx, 1);
+        DBuf<int64_t> mlen(ctx, L->n_dir), moff_e(ctx, L->n_dir);
         pl.dir_moff = DBuf<int64_t>(ctx, L->n_dir);
         BLTC_CUDA(cudaMemsetAsync(lidx.p, 0xff, sizeof(int32_t) * m, s));
         a.s_nch = L->st->nch.p;
@@ -1012,19 +1038,18 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
         k_leaf_index<<<grid_for(nb, 256), 256, 0, s>>>(a, lidx.p); ++ctx->launches;
         k_mutual_mark<<<grid_for(L->n_dir, 256), 256, 0, s>>>(a, L->n_dir); ++ctx->launches;
         BLTC_LAUNCH_CHECK("plan mutual");
-        exclusive_scan_i64(ctx, mlen.p, moff_e.p, L->n_dir, tot.p);
+        exclusive_scan_i64(ctx, mlen.p, moff_e.p, L->n_dir, words.p + 3);
         k_mutual_moff<<<grid_for(L->n_dir, 256), 256, 0, s>>>(a, L->n_dir); ++ctx->launches;
         BLTC_LAUNCH_CHECK("plan mutual rows");
-        pl.mpart_len = ctx->read_words(tot.p, 1)[0];
     }
     // costs and items (skipped mutual entries cost nothing)
-    DBuf<int64_t> cost(ctx, nb), part_len(ctx, nb), words(ctx, 4);
-    BLTC_CUDA(cudaMemsetAsync(words.p, 0, 4 * sizeof(int64_t), s));
     a.cost = cost.p;
     a.total = reinterpret_cast<unsigned long long*>(words.p);
     k_batch_cost<<<grid_for(nb, 128), 128, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("plan cost");
-    const int64_t total = ctx->read_words(words.p, 1)[0];
+    const int64_t* w0 = ctx->read_words(words.p, 4);
+    const int64_t total = w0[0];
+    if (pl.mutual) pl.mpart_len = w0[3];
     const int64_t blocks = kMinBlocks * static_cast<int64_t>(std::max(1, ctx->sm_count));
     a.cut = std::max<int64_t>(total / (blocks * kItemsPerBlock), int64_t(1) << 20);
     pl.n_chunks = DBuf<int32_t>(ctx, nb);
