@@ -29,6 +29,7 @@ _lib = None
 KERNEL_COULOMB = 0
 KERNEL_YUKAWA = 1
 KERNEL_POLY = 2
+KERNEL_SOFT = 3          # 1/sqrt(r^2 + eps^2), eps passed as kappa
 MAX_DEGREE = 32
 
 _f64 = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")

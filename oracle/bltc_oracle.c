@@ -73,6 +73,12 @@ static int kernel_G(int kernel, double kappa, int degree,
         *g = poly_kernel(degree, tx, ty, tz, sx, sy, sz);
         return 1;
     }
+    if (kernel == ORACLE_KERNEL_SOFT) {
+        /* softened Coulomb 1/sqrt(r^2 + eps^2), eps = kappa: a smooth, non-oscillatory
+         * radial kernel outside Eq. 2, as the method allows (Sec. I, Sec. V) */
+        *g = 1.0 / sqrt(r2 + kappa * kappa);
+        return 1;
+    }
     double r = sqrt(r2);
     if (kernel == ORACLE_KERNEL_YUKAWA)
         *g = exp(-kappa * r) / r;       /* Yukawa, Eq. 2 right */

@@ -15,7 +15,8 @@ extern "C" {
 
 #define ORACLE_MAX_DEGREE 32
 
-enum { ORACLE_KERNEL_COULOMB = 0, ORACLE_KERNEL_YUKAWA = 1, ORACLE_KERNEL_POLY = 2 };
+enum { ORACLE_KERNEL_COULOMB = 0, ORACLE_KERNEL_YUKAWA = 1, ORACLE_KERNEL_POLY = 2,
+       ORACLE_KERNEL_SOFT = 3 };
 
 typedef struct oracle_tree oracle_tree;
 

@@ -470,3 +470,36 @@ def test_ts_error_band_and_decay():
     errs = [oracle.rel_err(ref, oracle.bltc_ts(T, S, q, 0.7, n, 300, 300)[0]) for n in (1, 3, 5, 7)]
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
     assert 1e-9 < errs[2] < 1e-4 and errs[0] > 1e-4, errs
+
+
+# ---------------------------------------------------------------------------------------
+# A kernel outside Eq. 2: softened Coulomb 1/sqrt(r^2 + eps^2) (smooth, non-oscillatory)
+# ---------------------------------------------------------------------------------------
+
+def test_soft_kernel_closed_form():
+    eps = 0.3
+    # charges 0.75 at the origin and -0.25 at distance 0.5 (a 3-4-5 triangle scaled)
+    phi = _direct([[0.0, 0.0, 0.0], [0.3, 0.4, 0.0]], [0.75, -0.25], oracle.KERNEL_SOFT, eps)
+    d = math.sqrt(0.25 + eps * eps)
+    assert phi[0] == pytest.approx(-0.25 / d, rel=1e-15)
+    assert phi[1] == pytest.approx(0.75 / d, rel=1e-15)
+
+
+def test_soft_kernel_eps0_is_coulomb_bitwise():
+    x, y, z, q = _system(3000)
+    pts = np.stack([x, y, z])
+    a = oracle.direct_sum(pts, pts, q, oracle.KERNEL_COULOMB)
+    b = oracle.direct_sum(pts, pts, q, oracle.KERNEL_SOFT, 0.0)
+    assert np.array_equal(a, b)
+
+
+def test_soft_kernel_treecode():
+    # theta = 0 is the direct sum; the approximation error falls with n for a smooth kernel
+    x, y, z, q = _system(6000, 20031861)
+    pts = np.stack([x, y, z])
+    ref = oracle.direct_sum(pts, pts, q, oracle.KERNEL_SOFT, 0.05)
+    phi, _, _ = oracle.bltc(x, y, z, q, 0.0, 4, 300, 300, oracle.KERNEL_SOFT, 0.05)
+    assert oracle.rel_err(ref, phi) < 1e-14
+    errs = [oracle.rel_err(ref, oracle.bltc(x, y, z, q, 0.7, n, 300, 300, oracle.KERNEL_SOFT, 0.05)[0])
+            for n in (1, 3, 5)]
+    assert errs[0] > errs[1] > errs[2] and 1e-9 < errs[2] < 1e-4, errs
