@@ -42,7 +42,17 @@ WORKLOAD_NAME = ("uniform cube N=1e6 (q in [-1,1]), Coulomb, theta=0.7, n=8, N_L
 XU_PER_CLK_PER_SM = 16
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
-SWEEP_SOURCE = os.path.join(ROOT, "paper_2003_01836_gb300", "csrc", "sweep.cu")
+# the sweep kernel's source: its device code and the file that instantiates and launches it
+SWEEP_SOURCES = [os.path.join(ROOT, "paper_2003_01836_gb300", "csrc", f)
+                 for f in ("sweep_device.cuh", "sweep.cu")]
+
+
+def sweep_source_sha256():
+    h = hashlib.sha256()
+    for path in SWEEP_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_sweep_mixed_traffic.txt")
 
 
@@ -190,8 +200,7 @@ def traffic_for_current_kernel():
     try:
         with open(TRAFFIC_FILE) as f:
             kv = dict(line.strip().split(": ", 1) for line in f if ": " in line)
-        with open(SWEEP_SOURCE, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        sha = sweep_source_sha256()
         if kv.get("sweep_source_sha256") != sha:
             return None
         return float(kv["dram_bytes_per_launch_full_size"])

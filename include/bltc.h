@@ -63,6 +63,8 @@ typedef enum bltc_status {
 } bltc_status;
 
 enum { BLTC_KERNEL_COULOMB = 0, BLTC_KERNEL_YUKAWA = 1 };
+/* Ids of user kernels registered in a context (bltc_kernel_register) start here. */
+#define BLTC_KERNEL_USER_BASE 16
 
 /* FP64: every step in FP64 (the reference path; Sec. IV computes in double precision).
  * MIXED: kernel evaluations in FP32 on coordinates relative to the batch centre with FP32
@@ -75,11 +77,12 @@ typedef struct bltc_params {
     int32_t degree;      /* n, interpolation degree, 1..BLTC_MAX_DEGREE; (n+1)^3 points */
     int32_t leaf_size;   /* N_L >= 1, source clusters hold at most N_L particles */
     int32_t batch_size;  /* N_B >= 1, target batches hold at most N_B particles */
-    int32_t kernel;      /* BLTC_KERNEL_COULOMB or BLTC_KERNEL_YUKAWA */
+    int32_t kernel;      /* BLTC_KERNEL_COULOMB, BLTC_KERNEL_YUKAWA or a registered user id */
     int32_t precision;   /* BLTC_PRECISION_FP64 or BLTC_PRECISION_MIXED */
     int32_t reserved;    /* must be 0 */
     double theta;        /* MAC parameter, 0 <= theta < 1 (theta = 0: all direct) */
-    double kappa;        /* Yukawa inverse Debye length, >= 0 (ignored for Coulomb) */
+    double kappa;        /* Yukawa inverse Debye length, >= 0 (ignored for Coulomb); the
+                          * parameter of a user kernel */
 } bltc_params;
 
 typedef struct bltc_context bltc_context;
@@ -240,6 +243,27 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
                           const double* q, int64_t n, const bltc_params* params,
                           const int32_t* leaf, const int32_t* batch, int32_t n_candidates,
                           int32_t repeats, int32_t use_cache, bltc_params* best, float* ms);
+
+/* ---- user kernels: a hook for any smooth, non-oscillatory radial G ---------------- */
+/* The treecode needs only evaluations of G (Sec. I; Sec. V names other kernels as the
+ * method's generality).  `source` is CUDA C++ source that defines
+ *     __device__ float  bltc_user_g32(float r2, float r, float param);
+ *     __device__ double bltc_user_g64(double r2, double r, double param);
+ * returning G at distance r = sqrt(r2) > 0 in FP32 (MIXED) and FP64; param is
+ * params->kappa.  G must depend on r only (the mixed sweep evaluates a mutual leaf pair once
+ * for both of its batches).  Pairs with r^2 == 0 are skipped as for the built-in kernels.
+ * The library compiles its sweep kernels with these functions at run time with NVRTC
+ * (libnvrtc.so of the CUDA toolkit, loaded on first use; BLTC_NVRTC_PATH may name it) for
+ * the context's device, and writes the id to use as params->kernel in this context:
+ * bltc_solve, bltc_solve_targets, bltc_evaluate and bltc_autotune accept it; the direct sum
+ * and the serving runtime take the built-in kernels only.
+ * Errors: ARG (NULL arguments, or the source does not compile: the compiler log is in
+ * bltc_last_error), STATE (NVRTC not found), CUDA. */
+bltc_status bltc_kernel_register(bltc_context* ctx, const char* source, int32_t* kernel_id);
+/* Compiles a user kernel source for sm_<arch> (e.g. 103) without a device, as a check.
+ * Copies the compiler log to log[len] (may be NULL) and returns BLTC_OK if it compiled, ARG
+ * if not, STATE if NVRTC is not found. */
+bltc_status bltc_kernel_check(const char* source, int32_t arch, char* log, int64_t len);
 
 /* ---- direct summation, Eq. 1 (the GPU baseline) ----------------------------------- */
 

@@ -33,6 +33,7 @@ BLTC_KERNEL_YUKAWA = 1
 BLTC_PRECISION_FP64 = 0
 BLTC_PRECISION_MIXED = 1
 BLTC_MAX_DEGREE = 16
+BLTC_KERNEL_USER_BASE = 16
 
 _STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
            -5: "ERR_STATE", -6: "ERR_CANCELLED"}
@@ -125,6 +126,8 @@ _SIGNATURES = {
                                 ctypes.c_int),
     "bltc_autotune": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                        ctypes.c_int32, _P, _vp], ctypes.c_int),
+    "bltc_kernel_register": ([_vp, ctypes.c_char_p, ctypes.POINTER(_i32)], ctypes.c_int),
+    "bltc_kernel_check": ([ctypes.c_char_p, _i32, ctypes.c_char_p, _i64], ctypes.c_int),
     "bltc_server_create": ([ctypes.POINTER(bltc_server_config), _pp], ctypes.c_int),
     "bltc_server_submit": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, ctypes.POINTER(ctypes.c_uint64)],
                            ctypes.c_int),
@@ -384,6 +387,21 @@ def bltc_solve_host(ctx, x, y, z, q, p: bltc_params, phi):
     n = x.shape[0]
     _check(ctx, lib().bltc_solve_host(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), n,
                                       ctypes.byref(p), _ptr(phi)))
+
+
+def bltc_kernel_register(ctx, source: str) -> int:
+    """Compiles the sweeps for a user kernel (CUDA source defining bltc_user_g32 and
+    bltc_user_g64) and returns its id for ``params.kernel`` in this context."""
+    kid = _i32()
+    _check(ctx, lib().bltc_kernel_register(ctx, source.encode(), ctypes.byref(kid)))
+    return kid.value
+
+
+def bltc_kernel_check(source: str, arch: int = 103):
+    """Compiles a user kernel for sm_<arch> without a device: (status, compiler log)."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    st = lib().bltc_kernel_check(source.encode(), int(arch), buf, len(buf))
+    return st, buf.value.decode(errors="replace")
 
 
 def bltc_direct_sum(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):

@@ -19,7 +19,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbltc.so")
 
 SOURCES = ["api.cu", "scan.cu", "tree.cu", "lists.cu", "upward.cu", "sweep.cu", "direct.cu",
-           "server.cu"]
+           "server.cu", "user_kernel.cu"]
+# the sweep device code, embedded as text for run-time compilation of user kernels
+EMBED = ("sweep_device.cuh", "kSweepDeviceSource")
 NO_FMAD = {"tree.cu", "lists.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -66,8 +68,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
+    def embed():
+        text = open(os.path.join(CSRC, EMBED[0])).read()
+        assert ")BLTCSRC" not in text
+        gen = os.path.join(BUILD, "embedded_sources.cpp")
+        with open(gen, "w") as f:
+            f.write("// generated by build.py from csrc/%s\n" % EMBED[0])
+            f.write("namespace bltc {\nextern const char* const %s;\n" % EMBED[1])
+            f.write('const char* const %s = R"BLTCSRC(%s)BLTCSRC";\n}\n' % (EMBED[1], text))
+        obj = os.path.join(BUILD, "embedded_sources.o")
+        r = subprocess.run([cc, "-c", gen, "-o", obj, "-Xcompiler", "-fPIC"], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"embedding failed:\n{r.stdout}\n{r.stderr}")
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES) + 1, os.cpu_count() or 4)) as ex:
+        fut = ex.submit(embed)
         objs = list(ex.map(compile_one, SOURCES))
+        objs.append(fut.result())
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

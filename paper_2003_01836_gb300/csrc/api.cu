@@ -77,9 +77,13 @@ static void check_params(const bltc_params* p) {
     require(std::isfinite(p->theta) && p->theta >= 0.0 && p->theta < 1.0,
             "theta must satisfy 0 <= theta < 1");
     require(p->leaf_size >= 1 && p->batch_size >= 1, "leaf_size and batch_size must be >= 1");
-    require(p->kernel == BLTC_KERNEL_COULOMB || p->kernel == BLTC_KERNEL_YUKAWA, "unknown kernel");
+    require(p->kernel == BLTC_KERNEL_COULOMB || p->kernel == BLTC_KERNEL_YUKAWA ||
+                p->kernel >= BLTC_KERNEL_USER_BASE,
+            "unknown kernel");
     require(p->kernel != BLTC_KERNEL_YUKAWA || (std::isfinite(p->kappa) && p->kappa >= 0.0),
             "kappa must be finite and >= 0");
+    require(p->kernel < BLTC_KERNEL_USER_BASE || std::isfinite(p->kappa),
+            "a user kernel's parameter (kappa) must be finite");
     require(p->precision == BLTC_PRECISION_FP64 || p->precision == BLTC_PRECISION_MIXED,
             "unknown precision");
     require(p->reserved == 0, "params.reserved must be 0");
@@ -208,6 +212,8 @@ void bltc_context_destroy(bltc_context* ctx) {
         if (t) cudaFree(t);
     for (cudaEvent_t& e : c.events)
         if (e) cudaEventDestroy(e);
+    for (Context::UserKernel& k : c.user_kernels)
+        if (k.lib) cudaLibraryUnload(k.lib);
     if (c.pinned) cudaFreeHost(c.pinned);
     if (c.pool) cudaMemPoolDestroy(c.pool);
     delete ctx;
@@ -515,6 +521,32 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
         cudaEventDestroy(e1);
         ctx->tuned[key] = {best->leaf_size, best->batch_size};
     });
+}
+
+bltc_status bltc_kernel_register(bltc_context* ctx, const char* source, int32_t* kernel_id) {
+    if (!ctx || !source || !kernel_id) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] { *kernel_id = register_user_kernel(&ctx->c, source); });
+}
+
+bltc_status bltc_kernel_check(const char* source, int32_t arch, char* log, int64_t len) {
+    if (!source) return BLTC_ERR_ARG;
+    std::string text;
+    bltc_status st = BLTC_OK;
+    try {
+        if (!compile_user_kernel(source, arch, &text, nullptr)) st = BLTC_ERR_ARG;
+    } catch (const Error& e) {
+        text = e.what();
+        st = e.status;
+    } catch (const std::exception& e) {
+        text = e.what();
+        st = BLTC_ERR_CUDA;
+    }
+    if (log && len > 0) {
+        const int64_t m = std::min<int64_t>(static_cast<int64_t>(text.size()), len - 1);
+        std::memcpy(log, text.data(), static_cast<size_t>(m));
+        log[m] = '\0';
+    }
+    return st;
 }
 
 bltc_status bltc_direct_sum_noalloc(bltc_context* ctx, const double* tx, const double* ty,

@@ -79,6 +79,18 @@ struct Context {
     // Copies `words` int64 values from device to the pinned buffer and waits.
     const int64_t* read_words(const void* dev, int words);
     const double* cheb_table(int degree);
+    // User kernels (bltc_kernel_register): run-time compiled sweeps, id USER_BASE + index.
+    struct UserKernel {
+        cudaLibrary_t lib = nullptr;
+        cudaKernel_t mixed = nullptr, fp64 = nullptr;
+    };
+    std::vector<UserKernel> user_kernels;
+    const UserKernel& user_kernel(int id) const {
+        const int i = id - BLTC_KERNEL_USER_BASE;
+        if (i < 0 || i >= static_cast<int>(user_kernels.size()))
+            throw Error(BLTC_ERR_ARG, "kernel id is not a kernel registered in this context");
+        return user_kernels[static_cast<size_t>(i)];
+    }
 };
 
 // RAII device buffer from the context allocator.
@@ -182,6 +194,11 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual);
 void prepare_plan(Context* ctx, Lists* L, int degree, int precision);
 // Kernel evaluations the sweep performs for that plan (mutual pairs counted once).
 int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision);
+// Compiles the sweeps for a user kernel given as CUDA source (user_kernel.cu); returns its id.
+int register_user_kernel(Context* ctx, const char* source);
+// Compiles a user kernel's sweeps for sm_<arch> without a device and returns the compiler
+// log; true when it compiled.
+bool compile_user_kernel(const char* source, int arch, std::string* log, std::vector<char>* cubin);
 // One request of a multi-request sweep: its lists, trees, parameters and device phi.
 struct SweepJob {
     Lists* L;
