@@ -93,6 +93,10 @@ def _load():
                                        c.c_int32, c.c_double, c.c_int32, c.c_void_p, c.c_int64,
                                        _f64, c.c_void_p, _f64]
         lib.oracle_bltc_ts.restype = c.c_int
+        lib.oracle_bltc_cp.argtypes = [_f64, _f64, _f64, c.c_int64, _f64, _f64, _f64, _f64,
+                                       c.c_int64, c.c_double, c.c_int32, c.c_int32, c.c_int32,
+                                       c.c_int32, c.c_double, c.c_int32, _f64, c.c_void_p]
+        lib.oracle_bltc_cp.restype = c.c_int
         lib.oracle_max_threads.restype = c.c_int
         _lib = lib
         return lib
@@ -264,6 +268,25 @@ def bltc_ts(targets, sources, q, theta, degree, leaf_size, batch_size,
     if rc:
         raise ValueError(f"oracle_bltc_ts failed ({rc})")
     return phi, phi_abs, {"setup": tm[0], "precompute": tm[1], "compute": tm[2]}
+
+
+def bltc_cp(targets, sources, q, theta, degree, leaf_size, batch_size,
+            kernel=KERNEL_COULOMB, kappa=0.0, threads=0, with_abs=False):
+    """Cluster-particle variant: targets in clusters of ``leaf_size`` (interpolated),
+    sources in batches of ``batch_size`` (summed exactly).  Returns (phi, phi_abs or None)."""
+    lib = _load()
+    tx, ty, tz = (_c(a) for a in targets)
+    sx, sy, sz = (_c(a) for a in sources)
+    q = _c(q)
+    phi = np.empty(tx.shape[0])
+    phi_abs = np.empty(tx.shape[0]) if with_abs else None
+    rc = lib.oracle_bltc_cp(tx, ty, tz, tx.shape[0], sx, sy, sz, q, sx.shape[0], float(theta),
+                            int(degree), int(leaf_size), int(batch_size), int(kernel),
+                            float(kappa), int(threads), phi,
+                            None if phi_abs is None else phi_abs.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle_bltc_cp failed ({rc})")
+    return phi, phi_abs
 
 
 def rel_err(reference, approx):

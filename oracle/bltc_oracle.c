@@ -702,6 +702,179 @@ int oracle_bltc(const double* x, const double* y, const double* z, const double*
                           kernel, kappa, threads, batch_subset, n_subset, phi, phi_abs, timings);
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Cluster-particle variant (the paper's future work, Sec. V): the roles of Algorithm 1    */
+/* swapped.  Targets form the clusters, which are interpolated; sources form the batches,  */
+/* which are summed exactly.                                                              */
+/* ------------------------------------------------------------------------------------ */
+
+/* Per source batch S (a leaf of the source tree, DFS order), ComputePotential walks the
+ * target tree with the same MAC (Eq. 13, here (r_S + r_T)/R < theta and (n+1)^3 < N_T):
+ *   - approximated target cluster T: the potential at T's Chebyshev points,
+ *       phihat_T[k] += sum_{y_j in S} G(t_k, y_j) q_j,        t_k = (s1[k1], s2[k2], s3[k3]);
+ *   - direct (leaf T, or T failing the size test): phi(x_i) += sum_{y_j in S} G(x_i, y_j) q_j
+ *     for every target x_i in T.
+ * Afterwards every target takes the interpolant of each of its clusters' point potentials,
+ *   phi(x_i) += sum_k L_k1(x_i1) L_k2(x_i2) L_k3(x_i3) phihat_T[k]   (Eq. 4-8, exact hits),
+ * clusters from the root down.  The direct part of a target is summed over batches S in
+ * ascending order, particles in tree order; phihat_T the same way. */
+int oracle_bltc_cp(const double* tx, const double* ty, const double* tz, int64_t nt,
+                   const double* sx, const double* sy, const double* sz, const double* sq,
+                   int64_t ns, double theta, int32_t degree, int32_t leaf_size,
+                   int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
+                   double* phi, double* phi_abs)
+{
+    if (nt < 1 || ns < 1 || degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    oracle_tree *tt = NULL, *st = NULL;
+    if (oracle_tree_build(tx, ty, tz, nt, leaf_size, &tt)) return -2;
+    if (oracle_tree_build(sx, sy, sz, ns, batch_size, &st)) {
+        oracle_tree_free(tt);
+        return -2;
+    }
+    const int n1 = degree + 1;
+    const int64_t P = (int64_t)n1 * n1 * n1;
+    const int64_t m = tt->n_nodes;
+    int rc = -2;
+    /* the lists, per source batch: target clusters approximated / summed directly */
+    int64_t nb = collect_leaves(st, NULL), na = 0, nd = 0;
+    int64_t* sleaves = (int64_t*)malloc((size_t)nb * sizeof(int64_t));
+    int64_t* a_off = (int64_t*)malloc((size_t)(nb + 1) * sizeof(int64_t));
+    int64_t* d_off = (int64_t*)malloc((size_t)(nb + 1) * sizeof(int64_t));
+    int64_t *a_ids = NULL, *d_ids = NULL;
+    /* per target node: the batches approximated into it; per target leaf: the batches
+     * summed directly (a direct non-leaf cluster passes its batch to all of its leaves) */
+    int64_t *ta_off = NULL, *ta_ids = NULL, *td_off = NULL, *td_ids = NULL, *fill = NULL;
+    int64_t* leaf_of = NULL;     /* target position -> its leaf */
+    double *phat = NULL, *phat_abs = NULL, *near = NULL, *near_abs = NULL;
+    if (!sleaves || !a_off || !d_off) goto done;
+    collect_leaves(st, sleaves);
+    if (oracle_lists(st, tt, theta, degree, NULL, NULL, NULL, NULL, &na, &nd)) goto done;
+    a_ids = (int64_t*)malloc((size_t)(na > 0 ? na : 1) * sizeof(int64_t));
+    d_ids = (int64_t*)malloc((size_t)(nd > 0 ? nd : 1) * sizeof(int64_t));
+    if (!a_ids || !d_ids) goto done;
+    if (oracle_lists(st, tt, theta, degree, a_off, a_ids, d_off, d_ids, &na, &nd)) goto done;
+
+    ta_off = (int64_t*)calloc((size_t)(m + 1), sizeof(int64_t));
+    td_off = (int64_t*)calloc((size_t)(m + 1), sizeof(int64_t));
+    fill = (int64_t*)calloc((size_t)(m + 1), sizeof(int64_t));
+    leaf_of = (int64_t*)malloc((size_t)nt * sizeof(int64_t));
+    if (!ta_off || !td_off || !fill || !leaf_of) goto done;
+    for (int64_t v = 0; v < m; ++v)
+        if (tt->n_children[v] == 0)
+            for (int64_t i = tt->begin[v]; i < tt->begin[v] + tt->count[v]; ++i) leaf_of[i] = v;
+    /* counts */
+    int64_t n_td = 0;
+    for (int64_t e = 0; e < na; ++e) ta_off[a_ids[e] + 1]++;
+    for (int64_t b = 0; b < nb; ++b)
+        for (int64_t e = d_off[b]; e < d_off[b + 1]; ++e) {
+            const int64_t T = d_ids[e];
+            for (int64_t v = T; v < m && (v == T || tt->begin[v] < tt->begin[T] + tt->count[T]); ++v)
+                if (tt->n_children[v] == 0) { td_off[v + 1]++; n_td++; }
+        }
+    for (int64_t v = 0; v < m; ++v) {
+        ta_off[v + 1] += ta_off[v];
+        td_off[v + 1] += td_off[v];
+    }
+    ta_ids = (int64_t*)malloc((size_t)(na > 0 ? na : 1) * sizeof(int64_t));
+    td_ids = (int64_t*)malloc((size_t)(n_td > 0 ? n_td : 1) * sizeof(int64_t));
+    if (!ta_ids || !td_ids) goto done;
+    for (int64_t b = 0; b < nb; ++b)          /* ascending b, so every list is ascending */
+        for (int64_t e = a_off[b]; e < a_off[b + 1]; ++e) {
+            const int64_t T = a_ids[e];
+            ta_ids[ta_off[T] + fill[T]++] = b;
+        }
+    memset(fill, 0, (size_t)(m + 1) * sizeof(int64_t));
+    for (int64_t b = 0; b < nb; ++b)
+        for (int64_t e = d_off[b]; e < d_off[b + 1]; ++e) {
+            const int64_t T = d_ids[e];
+            for (int64_t v = T; v < m && (v == T || tt->begin[v] < tt->begin[T] + tt->count[T]); ++v)
+                if (tt->n_children[v] == 0) td_ids[td_off[v] + fill[v]++] = b;
+        }
+
+    /* potentials at the Chebyshev points of every approximated target cluster */
+    phat = (double*)calloc((size_t)(m * P), sizeof(double));
+    phat_abs = (double*)calloc((size_t)(m * P), sizeof(double));
+    if (!phat || !phat_abs) goto done;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t T = 0; T < m; ++T) {
+        if (ta_off[T + 1] == ta_off[T]) continue;
+        double s1[ORACLE_MAX_DEGREE + 1], s2[ORACLE_MAX_DEGREE + 1], s3[ORACLE_MAX_DEGREE + 1];
+        double w[ORACLE_MAX_DEGREE + 1];
+        oracle_cheb(degree, tt->lo[3 * T], tt->hi[3 * T], s1, w);
+        oracle_cheb(degree, tt->lo[3 * T + 1], tt->hi[3 * T + 1], s2, w);
+        oracle_cheb(degree, tt->lo[3 * T + 2], tt->hi[3 * T + 2], s3, w);
+        for (int k1 = 0; k1 < n1; ++k1)
+            for (int k2 = 0; k2 < n1; ++k2)
+                for (int k3 = 0; k3 < n1; ++k3) {
+                    double acc = 0.0, acc_abs = 0.0;
+                    for (int64_t e = ta_off[T]; e < ta_off[T + 1]; ++e) {
+                        const int64_t S = sleaves[ta_ids[e]];
+                        for (int64_t mm = st->begin[S]; mm < st->begin[S] + st->count[S]; ++mm) {
+                            const int64_t j = st->perm[mm];
+                            double g;
+                            if (!kernel_G(kernel, kappa, degree, s1[k1], s2[k2], s3[k3], sx[j], sy[j],
+                                          sz[j], &g))
+                                continue;
+                            acc = acc + g * sq[j];
+                            acc_abs = acc_abs + fabs(g * sq[j]);
+                        }
+                    }
+                    phat[T * P + (k1 * n1 + k2) * n1 + k3] = acc;
+                    phat_abs[T * P + (k1 * n1 + k2) * n1 + k3] = acc_abs;
+                }
+    }
+    /* direct part, then the interpolants of the target's clusters from the root down */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < nt; ++i) {
+        const int64_t L = leaf_of[i];
+        const int64_t t = tt->perm[i];
+        double acc = 0.0, acc_abs = 0.0;
+        for (int64_t e = td_off[L]; e < td_off[L + 1]; ++e) {
+            const int64_t S = sleaves[td_ids[e]];
+            for (int64_t mm = st->begin[S]; mm < st->begin[S] + st->count[S]; ++mm) {
+                const int64_t j = st->perm[mm];
+                double g;
+                if (!kernel_G(kernel, kappa, degree, tx[t], ty[t], tz[t], sx[j], sy[j], sz[j], &g))
+                    continue;
+                acc = acc + g * sq[j];
+                acc_abs = acc_abs + fabs(g * sq[j]);
+            }
+        }
+        int64_t chain[128];
+        int depth = 0;
+        for (int64_t v = L; v >= 0 && depth < 128; v = tt->parent[v]) chain[depth++] = v;
+        for (int d = depth - 1; d >= 0; --d) {
+            const int64_t T = chain[d];
+            if (ta_off[T + 1] == ta_off[T]) continue;
+            double a1[ORACLE_MAX_DEGREE + 1], a2[ORACLE_MAX_DEGREE + 1], a3[ORACLE_MAX_DEGREE + 1];
+            oracle_lagrange(degree, tt->lo[3 * T], tt->hi[3 * T], tx[t], a1);
+            oracle_lagrange(degree, tt->lo[3 * T + 1], tt->hi[3 * T + 1], ty[t], a2);
+            oracle_lagrange(degree, tt->lo[3 * T + 2], tt->hi[3 * T + 2], tz[t], a3);
+            for (int k1 = 0; k1 < n1; ++k1)
+                for (int k2 = 0; k2 < n1; ++k2)
+                    for (int k3 = 0; k3 < n1; ++k3) {
+                        const int64_t k = (k1 * n1 + k2) * n1 + k3;
+                        const double l = a1[k1] * a2[k2] * a3[k3];
+                        acc = acc + l * phat[T * P + k];
+                        acc_abs = acc_abs + fabs(l) * phat_abs[T * P + k];
+                    }
+        }
+        phi[t] = acc;
+        if (phi_abs) phi_abs[t] = acc_abs;
+    }
+    rc = 0;
+done:
+    free(sleaves); free(a_off); free(d_off); free(a_ids); free(d_ids);
+    free(ta_off); free(ta_ids); free(td_off); free(td_ids); free(fill); free(leaf_of);
+    free(phat); free(phat_abs); free(near); free(near_abs);
+    oracle_tree_free(tt);
+    oracle_tree_free(st);
+    return rc;
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

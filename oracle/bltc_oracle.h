@@ -66,6 +66,14 @@ int oracle_bltc_ts(const double* tx, const double* ty, const double* tz, int64_t
                    const int64_t* batch_subset, int64_t n_subset, double* phi, double* phi_abs,
                    double* timings);
 
+/* Cluster-particle variant: targets clustered (leaf_size) and interpolated, sources in
+ * batches (batch_size) summed exactly; the same MAC and exact-hit rules. */
+int oracle_bltc_cp(const double* tx, const double* ty, const double* tz, int64_t nt,
+                   const double* sx, const double* sy, const double* sz, const double* sq,
+                   int64_t ns, double theta, int32_t degree, int32_t leaf_size,
+                   int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
+                   double* phi, double* phi_abs);
+
 int oracle_max_threads(void);
 
 #ifdef __cplusplus

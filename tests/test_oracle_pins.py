@@ -503,3 +503,52 @@ def test_soft_kernel_treecode():
     errs = [oracle.rel_err(ref, oracle.bltc(x, y, z, q, 0.7, n, 300, 300, oracle.KERNEL_SOFT, 0.05)[0])
             for n in (1, 3, 5)]
     assert errs[0] > errs[1] > errs[2] and 1e-9 < errs[2] < 1e-4, errs
+
+
+# ---------------------------------------------------------------------------------------
+# Cluster-particle variant (future work of Sec. V): targets interpolated, sources exact
+# ---------------------------------------------------------------------------------------
+
+def test_cp_theta_zero_equals_direct_sum():
+    T, S, q = _targets_and_sources(2500, 4000, 20031863)
+    phi, _ = oracle.bltc_cp(T, S, q, 0.0, 4, 300, 170)
+    ref = oracle.direct_sum(np.stack(T), np.stack(S), q)
+    assert oracle.rel_err(ref, phi) < 1e-14
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_cp_polynomial_kernel_is_exact(n):
+    # G(x, y) of degree n in every TARGET coordinate is reproduced by the interpolant of the
+    # target cluster's point potentials, whatever theta
+    T, S, q = _targets_and_sources(4000, 3000, 20031865)
+    phi, phi_abs = oracle.bltc_cp(T, S, q, 0.7, n, 220, 150, oracle.KERNEL_POLY, with_abs=True)
+    ref, ref_abs = oracle.direct_sum(np.stack(T), np.stack(S), q, oracle.KERNEL_POLY, 0.0, n,
+                                     with_abs=True)
+    assert np.max(np.abs(phi - ref) / ref_abs) < 1e-12
+    # the approximation is used: some target cluster is approximated for some batch
+    tt, st = oracle.Tree(*T, 220), oracle.Tree(*S, 150)
+    assert len(oracle.lists(st, tt, 0.7, n)["approx_ids"]) > 0
+
+
+def test_cp_same_particles_and_error_decay():
+    x, y, z, q = _system(20000, 20031867)
+    pts = np.stack([x, y, z])
+    ref = oracle.direct_sum(pts, pts, q)
+    errs = [oracle.rel_err(ref, oracle.bltc_cp((x, y, z), (x, y, z), q, 0.7, n, 400, 400)[0])
+            for n in (1, 3, 5, 7)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert 1e-9 < errs[2] < 1e-4 and errs[0] > 1e-4, errs
+
+
+def test_cp_lists_cover_every_pair_once():
+    # every (target, source batch) pair is in exactly one list entry: an approximated target
+    # cluster holding the target, or a direct one
+    T, S, _ = _targets_and_sources(3000, 2500, 20031869)
+    tt, st = oracle.Tree(*T, 200), oracle.Tree(*S, 130)
+    L = oracle.lists(st, tt, 0.7, 4)
+    for b in range(len(st.leaves)):
+        cover = np.zeros(len(T[0]), np.int64)
+        for key in ("approx", "direct"):
+            for C in L[key + "_ids"][L[key + "_off"][b]:L[key + "_off"][b + 1]]:
+                cover[tt.begin[C]:tt.begin[C] + tt.count[C]] += 1
+        assert (cover == 1).all(), b
