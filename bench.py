@@ -312,11 +312,17 @@ def run_ours(args, dist: Dist):
     return out
 
 
+def rel_err(reference, approx):
+    """Eq. 16: relative 2-norm error of approx against reference."""
+    reference = np.asarray(reference, dtype=np.float64)
+    approx = np.asarray(approx, dtype=np.float64)
+    return float(np.sqrt(np.sum((reference - approx) ** 2) / np.sum(reference ** 2)))
+
+
 def check_errors(ctx, b, X, p, w, phi_mixed):
     """Relative 2-norm errors (Eq. 16): mixed vs FP64 GPU treecode (the metric's condition),
     and both vs the FP64 GPU direct sum on a seeded sample of targets."""
     import torch
-    import oracle
     phi_mx = phi_mixed.clone()
     p64 = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
                    b.BLTC_PRECISION_FP64)
@@ -332,10 +338,10 @@ def check_errors(ctx, b, X, p, w, phi_mixed):
     b.bltc_direct_sum(ctx.h, *T, *X[:3], X[3], p64, ref)
     torch.cuda.synchronize()
     h = lambda t: t.cpu().numpy()
-    e_mx_64 = oracle.rel_err(h(phi64), h(phi_mx))
+    e_mx_64 = rel_err(h(phi64), h(phi_mx))
     return {"mixed_vs_fp64_gpu_bltc": e_mx_64, "meets_1e-6": bool(e_mx_64 <= 1e-6),
-            "fp64_bltc_vs_direct_sampled": oracle.rel_err(h(ref), h(phi64.index_select(0, idx))),
-            "mixed_bltc_vs_direct_sampled": oracle.rel_err(h(ref), h(phi_mx.index_select(0, idx))),
+            "fp64_bltc_vs_direct_sampled": rel_err(h(ref), h(phi64.index_select(0, idx))),
+            "mixed_bltc_vs_direct_sampled": rel_err(h(ref), h(phi_mx.index_select(0, idx))),
             "fp64_gpu_bltc_seconds": t64, "direct_sample_targets": int(idx.numel())}
 
 
@@ -466,6 +472,85 @@ def run_serving(args, dist: Dist):
                                              "peak_live_bytes", "budget_bytes")}}
 
 
+# ---- cluster-particle variant -----------------------------------------------------------------
+
+def run_cp(args, dist: Dist):
+    """The cluster-particle variant (targets interpolated, sources exact) on the same workload:
+    time-to-solution with inputs resident, and its errors next to the treecode's."""
+    import torch
+
+    import paper_2003_01836_gb300 as b
+    from paper_2003_01836_gb300 import build, inputs
+    build.build()
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+    x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"] + dist.rank)
+    X = [torch.from_numpy(a).to(f"cuda:{dev}") for a in (x, y, z, q)]
+    phi = torch.empty_like(X[0])
+    ctx = b.Context(dev)
+    p = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
+                 b.BLTC_PRECISION_MIXED)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
+    solve = lambda pp, out: b.bltc_solve_cp(ctx.h, *X[:3], *X, pp, out)
+    for _ in range(args.warmup):
+        solve(p, phi)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    step_ms = []
+    launches0 = b.bltc_context_launch_count(ctx.h)
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        solve(p, phi)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    launches = b.bltc_context_launch_count(ctx.h) - launches0
+    agg = aggregate(sum(step_ms) / len(step_ms), w["n"], dist)
+    out = {"metric": "cluster-particle variant: targets/s (time-to-solution, inputs resident)",
+           "value": agg["targets_per_s"], "unit": "targets/s", "n_gpus": dist.world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 (f64 accumulation and interpolation)", "data": "synthetic",
+           "config": {"workload": "cluster-particle variant on " + WORKLOAD_NAME, "n_particles": w["n"],
+                      "theta": w["theta"], "degree": w["degree"], "target_leaf_size": w["leaf"],
+                      "source_batch_size": w["batch"], "kernel": "coulomb", "precision": "mixed",
+                      "l2": "flushed before every timed step (256 MiB device write)"},
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+           "clocks": clocks, "gpu_launches": int(launches)}
+    if not args.no_check:
+        p64 = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
+                       b.BLTC_PRECISION_FP64)
+        phi64 = torch.empty_like(phi)
+        solve(p64, phi64)
+        tree = torch.empty_like(phi)
+        ctx.solve(*X, p, tree)
+        rng = np.random.default_rng(20031836)
+        idx = torch.from_numpy(np.sort(rng.choice(w["n"], size=min(w["n"], 4096), replace=False))).cuda()
+        T = [a.index_select(0, idx).contiguous() for a in X[:3]]
+        ref = torch.empty_like(T[0])
+        b.bltc_direct_sum(ctx.h, *T, *X[:3], X[3], p64, ref)
+        torch.cuda.synchronize()
+        h = lambda t: t.cpu().numpy()
+        out["error"] = {"mixed_vs_fp64_gpu_cp": rel_err(h(phi64), h(phi)),
+                        "fp64_cp_vs_direct_sampled": rel_err(h(ref), h(phi64.index_select(0, idx))),
+                        "mixed_cp_vs_direct_sampled": rel_err(h(ref), h(phi.index_select(0, idx))),
+                        "mixed_treecode_vs_direct_sampled": rel_err(h(ref), h(tree.index_select(0, idx))),
+                        "direct_sample_targets": int(idx.numel())}
+    ctx.close()
+    return out
+
+
 # ---- reference arm: the oracle --------------------------------------------------------------
 
 def run_reference(args, dist: Dist):
@@ -511,6 +596,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
                     help="time the serving runtime on the request stream instead")
+    ap.add_argument("--variant", choices=("treecode", "cp"), default="treecode",
+                    help="cp: time the cluster-particle variant on the same workload instead")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-workers", type=int, default=3)
     args = ap.parse_args(argv)
@@ -522,6 +609,8 @@ def main(argv=None):
             out = run_reference(args, dist)
         elif args.serving:
             out = run_serving(args, dist)
+        elif args.variant == "cp":
+            out = run_cp(args, dist)
         else:
             out = run_ours(args, dist)
         if out is not None and dist.rank == 0:

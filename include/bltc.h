@@ -224,6 +224,21 @@ bltc_status bltc_solve_targets(bltc_context* ctx, const double* tx, const double
                                const double* sz, const double* sq, int64_t ns,
                                const bltc_params* params, double* phi);
 
+/* The cluster-particle variant (the paper's future work, Sec. V): the roles of Algorithm 1
+ * swapped.  Targets (tx, ty, tz; nt) form the clusters, in a tree with params->leaf_size,
+ * and are interpolated; sources (sx, sy, sz, sq; ns) form the batches, leaves of a tree with
+ * params->batch_size, and are summed exactly.  For every source batch S, ComputePotential
+ * walks the target tree with the MAC of Eq. 13 ((r_S + r_T)/R < theta and (n+1)^3 < N_T):
+ * an approximated target cluster T accumulates phihat_T[k] = sum_{y_j in S} G(t_k, y_j) q_j
+ * at its Chebyshev points t_k; a direct one adds sum_{y_j in S} G(x_i, y_j) q_j to each of
+ * its targets.  Finally phi(x_i) += sum_k L_k1 L_k2 L_k3 (x_i) phihat_T[k] (Eq. 4-8, exact
+ * hits) for every cluster T holding x_i.  Device pointers; phi[nt] in the caller's target
+ * order.  Built-in and registered kernels, both precisions (the interpolation runs in FP64).
+ * Errors: as bltc_solve. */
+bltc_status bltc_solve_cp(bltc_context* ctx, const double* tx, const double* ty, const double* tz,
+                          int64_t nt, const double* sx, const double* sy, const double* sz,
+                          const double* sq, int64_t ns, const bltc_params* params, double* phi);
+
 /* bltc_solve for HOST buffers x, y, z, q, phi (pinned memory recommended): copies the
  * inputs to the device, solves, copies phi back.  Synchronizes.  Errors: as bltc_solve. */
 bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,

@@ -118,6 +118,7 @@ _SIGNATURES = {
     "bltc_evaluate": ([_vp, _vp, _vp, _vp, _P, _vp], ctypes.c_int),
     "bltc_solve": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_host": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
+    "bltc_solve_cp": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_targets": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                            ctypes.c_int),
     "bltc_direct_sum": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
@@ -379,6 +380,13 @@ def bltc_solve_targets(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):
     _check(ctx, lib().bltc_solve_targets(ctx, _ptr(tx), _ptr(ty), _ptr(tz), tx.numel(), _ptr(sx),
                                          _ptr(sy), _ptr(sz), _ptr(sq), sx.numel(), ctypes.byref(p),
                                          _ptr(phi)))
+
+
+def bltc_solve_cp(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):
+    """Cluster-particle variant: targets interpolated (leaf_size), sources exact (batch_size)."""
+    _stream(ctx)
+    _check(ctx, lib().bltc_solve_cp(ctx, _ptr(tx), _ptr(ty), _ptr(tz), tx.numel(), _ptr(sx), _ptr(sy),
+                                    _ptr(sz), _ptr(sq), sx.numel(), ctypes.byref(p), _ptr(phi)))
 
 
 def bltc_solve_host(ctx, x, y, z, q, p: bltc_params, phi):

@@ -438,6 +438,17 @@ bltc_status bltc_solve_targets(bltc_context* ctx, const double* tx, const double
     });
 }
 
+bltc_status bltc_solve_cp(bltc_context* ctx, const double* tx, const double* ty, const double* tz,
+                          int64_t nt, const double* sx, const double* sy, const double* sz,
+                          const double* sq, int64_t ns, const bltc_params* params, double* phi) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(tx && ty && tz && sx && sy && sz && sq && phi, "solve_cp: NULL pointer");
+        solve_device_cp(&ctx->c, tx, ty, tz, nt, sx, sy, sz, sq, ns, *params, phi);
+    });
+}
+
 bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y, const double* z,
                             const double* q, int64_t n, const bltc_params* params, double* phi) {
     if (!ctx) return BLTC_ERR_ARG;

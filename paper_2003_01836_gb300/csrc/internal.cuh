@@ -194,6 +194,10 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual);
 void prepare_plan(Context* ctx, Lists* L, int degree, int precision);
 // Kernel evaluations the sweep performs for that plan (mutual pairs counted once).
 int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision);
+// The cluster-particle variant (cp.cu): targets interpolated, sources summed exactly.
+void solve_device_cp(Context* c, const double* tx, const double* ty, const double* tz, int64_t nt,
+                     const double* sx, const double* sy, const double* sz, const double* sq, int64_t ns,
+                     const bltc_params& p, double* phi);
 // Compiles the sweeps for a user kernel given as CUDA source (user_kernel.cu); returns its id.
 int register_user_kernel(Context* ctx, const char* source);
 // Compiles a user kernel's sweeps for sm_<arch> without a device and returns the compiler
