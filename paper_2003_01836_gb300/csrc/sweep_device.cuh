@@ -455,12 +455,12 @@ __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const T
     for (int u = 0; u < kT; ++u) hi[u] = lo[u] = 0.f;
     // rows are summed in FP32 in runs of about kBlock terms, then folded by TwoSum
     const int R = np1 * np1, run = max(1, kBlock / np1) * G;
+    int k1 = g / np1, k2 = g - k1 * np1;          // (k1, k2) of the current row, stepped by G
     for (int row0 = g; row0 < R; row0 += run) {
         float2 f[kH];
 #pragma unroll
         for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
         for (int row = row0; row < min(R, row0 + run); row += G) {
-            const int k1 = row / np1, k2 = row - k1 * np1;
             const float2 sx = sxp[k1], sy = syp[k2];
             float2 t[kH];
 #pragma unroll
@@ -480,6 +480,7 @@ __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const T
                     f[v] = fma2(q, ri2_mixed<KER>(r2, a.neg_kappa_log2e, a.param32, false), f[v]);
                 }
             }
+            for (k2 += G; k2 >= np1; k2 -= np1) ++k1;
         }
 #pragma unroll
         for (int v = 0; v < kH; ++v) {
