@@ -1,14 +1,17 @@
 """FP64 CPU oracle of the barycentric Lagrange treecode (test infrastructure only).
 
 This package is the plain, slow reference that the CUDA library is checked against.  Only
-``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import it.
+``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline and reference legs
+may import it.
 It shares no code with ``paper_2003_01836_gb300``; the two meet only through the seeded input
 arrays of ``paper_2003_01836_gb300.inputs``, which hold none of the method's arithmetic.
 
 The C source (``bltc_oracle.c``) cites the paper passage each function follows:
 Eq. 1-2 (direct sum, kernels), Eq. 4-7 (barycentric Lagrange interpolation at Chebyshev
 points of the second kind), Sec. II-C (exact hits), Eq. 12 (modified charges), Eq. 13 (MAC)
-and Algorithm 1 (the treecode), plus Eq. 16 (relative 2-norm error) here in Python.
+and Algorithm 1 (the treecode, for targets = sources and for separate sets), the
+cluster-particle variant named as future work in Sec. V, plus Eq. 16 (relative 2-norm error)
+here in Python.
 """
 from __future__ import annotations
 

@@ -4,7 +4,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct reference that the
  * CUDA library is checked against.  Only tests/, __graft_entry__.smoke() and bench.py's
- * CPU-baseline leg may load it.  It shares no code, header, table or helper with the
+ * CPU-baseline and reference legs may load it.  It shares no code, header, table or helper with the
  * library; both receive the same input arrays from the seeded generators and nothing else.
  *
  * Everything is IEEE FP64, compiled with -ffp-contract=off so that a*b+c is never fused.

@@ -264,9 +264,13 @@ void solve_device_cp(Context* c, const double* tx, const double* ty, const doubl
     cudaStream_t s = c->stream;
     const int np1 = p.degree + 1, P = np1 * np1 * np1;
     c->mark(Context::kStart);
-    Tree tt, ss;
-    build_tree(c, tx, ty, tz, nullptr, nt, p.leaf_size, &tt);      // target clusters
+    Tree ts, ss;
     build_tree(c, sx, sy, sz, sq, ns, p.batch_size, &ss);           // source batches
+    // the same particles with the same leaf size share one tree, so that the near half's
+    // mutual leaf pairs are evaluated once (mixed sweep)
+    const bool same = tx == sx && ty == sy && tz == sz && nt == ns && p.leaf_size == p.batch_size;
+    if (!same) build_tree(c, tx, ty, tz, nullptr, nt, p.leaf_size, &ts);   // target clusters
+    Tree& tt = same ? ss : ts;
     require(tt.n_levels <= kMaxDepth, "solve_cp: target tree deeper than 128 levels");
     c->mark(Context::kTrees);
     Lists L;                                                        // per source batch

@@ -55,3 +55,21 @@ def test_cp_theta0_and_determinism(gpu):
     assert oracle.rel_err(ref, got) < 1e-13
     p = b.params(6, 0.7, 400, 400)
     assert np.array_equal(_solve(gpu, T, S, q, p), _solve(gpu, T, S, q, p))
+
+
+def test_cp_shared_tree_for_same_particles(gpu):
+    # targets and sources passed as the same device arrays with leaf = batch share one tree,
+    # so the near half's mutual leaf pairs are evaluated once; results as for separate trees
+    import torch
+    x, y, z, q = system("plummer", 25000, 20031909)
+    X = dev(x, y, z, q)
+    want, want_abs = oracle.bltc_cp((x, y, z), (x, y, z), q, 0.7, 6, 700, 700, with_abs=True)
+    out = {}
+    for prec in (b.BLTC_PRECISION_FP64, b.BLTC_PRECISION_MIXED):
+        phi = torch.empty_like(X[0])
+        b.bltc_solve_cp(gpu.h, *X[:3], *X, b.params(6, 0.7, 700, 700, precision=prec), phi)
+        torch.cuda.synchronize()
+        out[prec] = host(phi)
+    assert_close_abs(want, out[b.BLTC_PRECISION_FP64], want_abs, FP64_REL2, FP64_ELEM, "cp shared fp64")
+    assert_close_abs(out[b.BLTC_PRECISION_FP64], out[b.BLTC_PRECISION_MIXED], want_abs, MIXED_REL2,
+                     MIXED_ELEM, "cp shared mixed")

@@ -412,3 +412,28 @@ def test_mutual_pairs_counted_once(gpu):
         assert ev_mx == c["direct"] + c["approx"] - saved
     finally:
         b.bltc_tree_destroy(st)
+
+
+def test_bltc_degenerate_systems(gpu):
+    # duplicates (pairs with r^2 == 0 inside a leaf), a lattice (exact hits on Chebyshev end
+    # points and many equal distances), two far-apart clumps, and a single repeated point
+    rng = np.random.default_rng(20031907)
+    dup = np.repeat(rng.uniform(-1, 1, (3, 1500)), 4, axis=1)
+    lat = np.array(np.meshgrid(np.arange(24.0), np.arange(24.0), np.arange(12.0))).reshape(3, -1)
+    clumps = np.concatenate([rng.normal(0, 0.01, (3, 3000)), rng.normal(0, 0.01, (3, 3000)) + 50.0], axis=1)
+    for pts, leaf, deg in ((dup, 300, 4), (lat, 200, 3), (clumps, 400, 5)):
+        q = rng.uniform(-1, 1, pts.shape[1])
+        x, y, z = pts
+        p64 = b.params(deg, 0.7, leaf, leaf, 0, 0.0, b.BLTC_PRECISION_FP64)
+        pmx = b.params(deg, 0.7, leaf, leaf, 0, 0.0, b.BLTC_PRECISION_MIXED)
+        want, want_abs = _oracle(x, y, z, q, p64)
+        got64 = gpu_solve(gpu, x, y, z, q, p64)
+        gotmx = gpu_solve(gpu, x, y, z, q, pmx)
+        assert_close_abs(want, got64, want_abs, FP64_REL2, FP64_ELEM, "degenerate fp64 vs oracle")
+        assert_close_abs(got64, gotmx, want_abs, MIXED_REL2, MIXED_ELEM, "degenerate mixed vs fp64")
+    # one point repeated: every pair has r^2 == 0, every potential is exactly 0
+    x = np.full(5000, 0.25)
+    q = rng.uniform(-1, 1, 5000)
+    for prec in (b.BLTC_PRECISION_FP64, b.BLTC_PRECISION_MIXED):
+        got = gpu_solve(gpu, x, x.copy(), x.copy(), q, b.params(4, 0.7, 100, precision=prec))
+        assert np.all(got == 0.0)
