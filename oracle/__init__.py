@@ -100,6 +100,11 @@ def _load():
                                        c.c_int64, c.c_double, c.c_int32, c.c_int32, c.c_int32,
                                        c.c_int32, c.c_double, c.c_int32, _f64, c.c_void_p]
         lib.oracle_bltc_cp.restype = c.c_int
+        lib.oracle_bltc_cc.argtypes = lib.oracle_bltc_cp.argtypes
+        lib.oracle_bltc_cc.restype = c.c_int
+        lib.oracle_dual_lists_export.argtypes = [c.c_void_p, c.c_void_p, c.c_double, c.c_int32,
+                                                 c.c_void_p, c.c_void_p, c.c_void_p]
+        lib.oracle_dual_lists_export.restype = c.c_int
         lib.oracle_max_threads.restype = c.c_int
         _lib = lib
         return lib
@@ -290,6 +295,46 @@ def bltc_cp(targets, sources, q, theta, degree, leaf_size, batch_size,
     if rc:
         raise ValueError(f"oracle_bltc_cp failed ({rc})")
     return phi, phi_abs
+
+
+def bltc_cc(targets, sources, q, theta, degree, leaf_size, batch_size,
+            kernel=KERNEL_COULOMB, kappa=0.0, threads=0, with_abs=False):
+    """Cluster-cluster variant (dual tree traversal): sources in a tree with ``leaf_size``,
+    targets in a tree with ``batch_size``.  Returns (phi, phi_abs or None)."""
+    lib = _load()
+    tx, ty, tz = (_c(a) for a in targets)
+    sx, sy, sz = (_c(a) for a in sources)
+    q = _c(q)
+    phi = np.empty(tx.shape[0])
+    phi_abs = np.empty(tx.shape[0]) if with_abs else None
+    rc = lib.oracle_bltc_cc(tx, ty, tz, tx.shape[0], sx, sy, sz, q, sx.shape[0], float(theta),
+                            int(degree), int(leaf_size), int(batch_size), int(kernel),
+                            float(kappa), int(threads), phi,
+                            None if phi_abs is None else phi_abs.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle_bltc_cc failed ({rc})")
+    return phi, phi_abs
+
+
+def dual_lists(targets: Tree, sources: Tree, theta, degree):
+    """The dual traversal's interaction lists: {"cc", "cp", "pc", "pp"} -> (target ids,
+    source ids), each in traversal order."""
+    lib = _load()
+    counts = np.zeros(4, np.int64)
+    lib.oracle_dual_lists_export(targets._h, sources._h, float(theta), int(degree),
+                                 counts.ctypes.data, None, None)
+    tot = int(counts.sum())
+    t = np.empty(max(tot, 1), np.int64)
+    s = np.empty(max(tot, 1), np.int64)
+    rc = lib.oracle_dual_lists_export(targets._h, sources._h, float(theta), int(degree),
+                                      counts.ctypes.data, t.ctypes.data, s.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle_dual_lists_export failed ({rc})")
+    out, o = {}, 0
+    for name, n in zip(("cc", "cp", "pc", "pp"), counts):
+        out[name] = (t[o:o + n].copy(), s[o:o + n].copy())
+        o += int(n)
+    return out
 
 
 def rel_err(reference, approx):

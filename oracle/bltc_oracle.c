@@ -875,6 +875,287 @@ done:
     return rc;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Cluster-cluster variant (dual tree traversal, the paper's future work, Sec. V).         */
+/* ------------------------------------------------------------------------------------ */
+
+/* Reading (the paper names the variant but does not define it).  Both sides are trees:
+ * sources with leaf_size (N_L), targets with batch_size (N_B).  DualTraversal(T, S) starts
+ * at the two roots:
+ *   if (r_T + r_S)/R < theta (Eq. 13's geometric test):
+ *       P < N_T and P < N_S  -> CC: phihat_T[k] += sum_k' G(t_k, s_k') qhat_S[k']
+ *       P < N_T only         -> CP: phihat_T[k] += sum_{y_j in S} G(t_k, y_j) q_j
+ *       P < N_S only         -> PC: phi(x_i) += sum_k' G(x_i, s_k') qhat_S[k'],  x_i in T
+ *       neither              -> PP: phi(x_i) += sum_{y_j in S} G(x_i, y_j) q_j, x_i in T
+ *   else if T and S are leaves -> PP
+ *   else split one side, children in stored order: T if S is a leaf, or if T is not a leaf and
+ *       r_T >= r_S; S otherwise.
+ * Finally phi(x_i) += sum_k L_k1 L_k2 L_k3 (x_i) phihat_T[k] for every target cluster T holding
+ * x_i (Eq. 4-8, exact hits), root first.  Per target the PC and PP terms are summed for its
+ * clusters root first, each cluster's interactions in traversal order. */
+typedef struct {
+    int64_t *t, *s;
+    int64_t n, cap;
+} pair_list;
+
+static int pair_push(pair_list* l, int64_t t, int64_t s)
+{
+    if (l->n == l->cap) {
+        int64_t nc = l->cap ? 2 * l->cap : 1024;
+        int64_t* a = (int64_t*)realloc(l->t, (size_t)nc * sizeof(int64_t));
+        if (!a) return -1;
+        l->t = a;
+        a = (int64_t*)realloc(l->s, (size_t)nc * sizeof(int64_t));
+        if (!a) return -1;
+        l->s = a;
+        l->cap = nc;
+    }
+    l->t[l->n] = t;
+    l->s[l->n] = s;
+    l->n++;
+    return 0;
+}
+
+typedef struct {
+    const oracle_tree *tt, *st;
+    double theta;
+    int64_t P;
+    pair_list cc, cp, pc, pp;
+    int fail;
+} dual_ctx;
+
+static void dual_traverse(dual_ctx* c, int64_t T, int64_t S)
+{
+    const double* ct = c->tt->center + 3 * T;
+    const double* cs = c->st->center + 3 * S;
+    double dx = ct[0] - cs[0];
+    double dy = ct[1] - cs[1];
+    double dz = ct[2] - cs[2];
+    double R = sqrt(dx * dx + dy * dy + dz * dz);
+    double ratio = (c->tt->radius[T] + c->st->radius[S]) / R;
+    const int t_leaf = c->tt->n_children[T] == 0, s_leaf = c->st->n_children[S] == 0;
+    if (ratio < c->theta) {
+        const int tc = c->P < c->tt->count[T], sc = c->P < c->st->count[S];
+        pair_list* l = tc ? (sc ? &c->cc : &c->cp) : (sc ? &c->pc : &c->pp);
+        if (pair_push(l, T, S)) c->fail = 1;
+    } else if (t_leaf && s_leaf) {
+        if (pair_push(&c->pp, T, S)) c->fail = 1;
+    } else if (s_leaf || (!t_leaf && c->tt->radius[T] >= c->st->radius[S])) {
+        for (int k = 0; k < c->tt->n_children[T]; ++k) dual_traverse(c, c->tt->children[8 * T + k], S);
+    } else {
+        for (int k = 0; k < c->st->n_children[S]; ++k) dual_traverse(c, T, c->st->children[8 * S + k]);
+    }
+}
+
+/* The four interaction lists of the dual traversal, in traversal order (pairs of target and
+ * source node ids).  Arrays are malloc'ed; the caller frees them with free(). */
+int oracle_dual_lists(const oracle_tree* tt, const oracle_tree* st, double theta, int32_t degree,
+                      int64_t* n_out, int64_t** t_out, int64_t** s_out)
+{
+    dual_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.tt = tt;
+    c.st = st;
+    c.theta = theta;
+    c.P = (int64_t)(degree + 1) * (degree + 1) * (degree + 1);
+    dual_traverse(&c, 0, 0);
+    pair_list* ls[4] = {&c.cc, &c.cp, &c.pc, &c.pp};
+    for (int i = 0; i < 4; ++i) {
+        n_out[i] = ls[i]->n;
+        t_out[i] = ls[i]->t;
+        s_out[i] = ls[i]->s;
+    }
+    return c.fail ? -2 : 0;
+}
+
+/* Copies the four lists (CC, CP, PC, PP) into caller arrays sized by a first call with NULL
+ * arrays, which only returns the counts. */
+int oracle_dual_lists_export(const oracle_tree* tt, const oracle_tree* st, double theta,
+                             int32_t degree, int64_t* counts, int64_t* t_ids, int64_t* s_ids)
+{
+    int64_t n[4];
+    int64_t *t[4], *s[4];
+    int rc = oracle_dual_lists(tt, st, theta, degree, n, t, s);
+    int64_t o = 0;
+    for (int i = 0; i < 4; ++i) {
+        counts[i] = n[i];
+        if (t_ids && s_ids) {
+            memcpy(t_ids + o, t[i], (size_t)n[i] * sizeof(int64_t));
+            memcpy(s_ids + o, s[i], (size_t)n[i] * sizeof(int64_t));
+        }
+        o += n[i];
+        free(t[i]);
+        free(s[i]);
+    }
+    return rc;
+}
+
+int oracle_bltc_cc(const double* tx, const double* ty, const double* tz, int64_t nt,
+                   const double* sx, const double* sy, const double* sz, const double* sq,
+                   int64_t ns, double theta, int32_t degree, int32_t leaf_size,
+                   int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
+                   double* phi, double* phi_abs)
+{
+    if (nt < 1 || ns < 1 || degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    oracle_tree *tt = NULL, *st = NULL;
+    if (oracle_tree_build(sx, sy, sz, ns, leaf_size, &st)) return -2;
+    if (oracle_tree_build(tx, ty, tz, nt, batch_size, &tt)) {
+        oracle_tree_free(st);
+        return -2;
+    }
+    const int n1 = degree + 1;
+    const int64_t P = (int64_t)n1 * n1 * n1;
+    const int64_t mt = tt->n_nodes, ms = st->n_nodes;
+    int rc = -2;
+    int64_t n[4] = {0, 0, 0, 0};
+    int64_t *lt[4] = {NULL, NULL, NULL, NULL}, *ls[4] = {NULL, NULL, NULL, NULL};
+    /* per target node, its interactions of each kind (CSR over target nodes, traversal order) */
+    int64_t *off[4] = {NULL, NULL, NULL, NULL}, *ids[4] = {NULL, NULL, NULL, NULL};
+    double *qhat = NULL, *phat = NULL, *phat_abs = NULL;
+    int64_t* leaf_of = NULL;
+    if (oracle_dual_lists(tt, st, theta, degree, n, lt, ls)) goto done;
+    for (int i = 0; i < 4; ++i) {
+        off[i] = (int64_t*)calloc((size_t)(mt + 1), sizeof(int64_t));
+        ids[i] = (int64_t*)malloc((size_t)(n[i] > 0 ? n[i] : 1) * sizeof(int64_t));
+        if (!off[i] || !ids[i]) goto done;
+        for (int64_t e = 0; e < n[i]; ++e) off[i][lt[i][e] + 1]++;
+        for (int64_t v = 0; v < mt; ++v) off[i][v + 1] += off[i][v];
+        int64_t* fill = (int64_t*)calloc((size_t)(mt + 1), sizeof(int64_t));
+        if (!fill) goto done;
+        for (int64_t e = 0; e < n[i]; ++e) ids[i][off[i][lt[i][e]] + fill[lt[i][e]]++] = ls[i][e];
+        free(fill);
+    }
+    qhat = (double*)malloc((size_t)(ms * P) * sizeof(double));
+    phat = (double*)calloc((size_t)(mt * P), sizeof(double));
+    phat_abs = (double*)calloc((size_t)(mt * P), sizeof(double));
+    leaf_of = (int64_t*)malloc((size_t)nt * sizeof(int64_t));
+    if (!qhat || !phat || !phat_abs || !leaf_of) goto done;
+    oracle_modified_charges(st, sx, sy, sz, sq, degree, threads, qhat);
+    for (int64_t v = 0; v < mt; ++v)
+        if (tt->n_children[v] == 0)
+            for (int64_t i = tt->begin[v]; i < tt->begin[v] + tt->count[v]; ++i) leaf_of[i] = v;
+
+    /* point potentials of the target clusters: CC terms, then CP terms */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t T = 0; T < mt; ++T) {
+        if (off[0][T + 1] == off[0][T] && off[1][T + 1] == off[1][T]) continue;
+        double t1[ORACLE_MAX_DEGREE + 1], t2[ORACLE_MAX_DEGREE + 1], t3[ORACLE_MAX_DEGREE + 1];
+        double w[ORACLE_MAX_DEGREE + 1];
+        oracle_cheb(degree, tt->lo[3 * T], tt->hi[3 * T], t1, w);
+        oracle_cheb(degree, tt->lo[3 * T + 1], tt->hi[3 * T + 1], t2, w);
+        oracle_cheb(degree, tt->lo[3 * T + 2], tt->hi[3 * T + 2], t3, w);
+        for (int k1 = 0; k1 < n1; ++k1)
+            for (int k2 = 0; k2 < n1; ++k2)
+                for (int k3 = 0; k3 < n1; ++k3) {
+                    double acc = 0.0, acc_abs = 0.0;
+                    for (int64_t e = off[0][T]; e < off[0][T + 1]; ++e) {
+                        const int64_t S = ids[0][e];
+                        double s1[ORACLE_MAX_DEGREE + 1], s2[ORACLE_MAX_DEGREE + 1], s3[ORACLE_MAX_DEGREE + 1];
+                        oracle_cheb(degree, st->lo[3 * S], st->hi[3 * S], s1, w);
+                        oracle_cheb(degree, st->lo[3 * S + 1], st->hi[3 * S + 1], s2, w);
+                        oracle_cheb(degree, st->lo[3 * S + 2], st->hi[3 * S + 2], s3, w);
+                        for (int m1 = 0; m1 < n1; ++m1)
+                            for (int m2 = 0; m2 < n1; ++m2)
+                                for (int m3 = 0; m3 < n1; ++m3) {
+                                    double g;
+                                    if (!kernel_G(kernel, kappa, degree, t1[k1], t2[k2], t3[k3], s1[m1],
+                                                  s2[m2], s3[m3], &g))
+                                        continue;
+                                    const double term = g * qhat[S * P + (m1 * n1 + m2) * n1 + m3];
+                                    acc = acc + term;
+                                    acc_abs = acc_abs + fabs(term);
+                                }
+                    }
+                    for (int64_t e = off[1][T]; e < off[1][T + 1]; ++e) {
+                        const int64_t S = ids[1][e];
+                        for (int64_t mm = st->begin[S]; mm < st->begin[S] + st->count[S]; ++mm) {
+                            const int64_t j = st->perm[mm];
+                            double g;
+                            if (!kernel_G(kernel, kappa, degree, t1[k1], t2[k2], t3[k3], sx[j], sy[j],
+                                          sz[j], &g))
+                                continue;
+                            acc = acc + g * sq[j];
+                            acc_abs = acc_abs + fabs(g * sq[j]);
+                        }
+                    }
+                    phat[T * P + (k1 * n1 + k2) * n1 + k3] = acc;
+                    phat_abs[T * P + (k1 * n1 + k2) * n1 + k3] = acc_abs;
+                }
+    }
+    /* per target: PC and PP terms of its clusters root first, then the interpolants */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < nt; ++i) {
+        const int64_t t = tt->perm[i];
+        int64_t chain[128];
+        int depth = 0;
+        for (int64_t v = leaf_of[i]; v >= 0 && depth < 128; v = tt->parent[v]) chain[depth++] = v;
+        double acc = 0.0, acc_abs = 0.0;
+        for (int d = depth - 1; d >= 0; --d) {
+            const int64_t T = chain[d];
+            for (int64_t e = off[2][T]; e < off[2][T + 1]; ++e) {        /* PC */
+                const int64_t S = ids[2][e];
+                double s1[ORACLE_MAX_DEGREE + 1], s2[ORACLE_MAX_DEGREE + 1], s3[ORACLE_MAX_DEGREE + 1];
+                double w[ORACLE_MAX_DEGREE + 1];
+                oracle_cheb(degree, st->lo[3 * S], st->hi[3 * S], s1, w);
+                oracle_cheb(degree, st->lo[3 * S + 1], st->hi[3 * S + 1], s2, w);
+                oracle_cheb(degree, st->lo[3 * S + 2], st->hi[3 * S + 2], s3, w);
+                for (int m1 = 0; m1 < n1; ++m1)
+                    for (int m2 = 0; m2 < n1; ++m2)
+                        for (int m3 = 0; m3 < n1; ++m3) {
+                            double g;
+                            if (!kernel_G(kernel, kappa, degree, tx[t], ty[t], tz[t], s1[m1], s2[m2],
+                                          s3[m3], &g))
+                                continue;
+                            const double term = g * qhat[S * P + (m1 * n1 + m2) * n1 + m3];
+                            acc = acc + term;
+                            acc_abs = acc_abs + fabs(term);
+                        }
+            }
+            for (int64_t e = off[3][T]; e < off[3][T + 1]; ++e) {        /* PP */
+                const int64_t S = ids[3][e];
+                for (int64_t mm = st->begin[S]; mm < st->begin[S] + st->count[S]; ++mm) {
+                    const int64_t j = st->perm[mm];
+                    double g;
+                    if (!kernel_G(kernel, kappa, degree, tx[t], ty[t], tz[t], sx[j], sy[j], sz[j], &g))
+                        continue;
+                    acc = acc + g * sq[j];
+                    acc_abs = acc_abs + fabs(g * sq[j]);
+                }
+            }
+        }
+        for (int d = depth - 1; d >= 0; --d) {
+            const int64_t T = chain[d];
+            if (off[0][T + 1] == off[0][T] && off[1][T + 1] == off[1][T]) continue;
+            double a1[ORACLE_MAX_DEGREE + 1], a2[ORACLE_MAX_DEGREE + 1], a3[ORACLE_MAX_DEGREE + 1];
+            oracle_lagrange(degree, tt->lo[3 * T], tt->hi[3 * T], tx[t], a1);
+            oracle_lagrange(degree, tt->lo[3 * T + 1], tt->hi[3 * T + 1], ty[t], a2);
+            oracle_lagrange(degree, tt->lo[3 * T + 2], tt->hi[3 * T + 2], tz[t], a3);
+            for (int k1 = 0; k1 < n1; ++k1)
+                for (int k2 = 0; k2 < n1; ++k2)
+                    for (int k3 = 0; k3 < n1; ++k3) {
+                        const int64_t k = (k1 * n1 + k2) * n1 + k3;
+                        const double l = a1[k1] * a2[k2] * a3[k3];
+                        acc = acc + l * phat[T * P + k];
+                        acc_abs = acc_abs + fabs(l) * phat_abs[T * P + k];
+                    }
+        }
+        phi[t] = acc;
+        if (phi_abs) phi_abs[t] = acc_abs;
+    }
+    rc = 0;
+done:
+    for (int i = 0; i < 4; ++i) {
+        free(lt[i]); free(ls[i]); free(off[i]); free(ids[i]);
+    }
+    free(qhat); free(phat); free(phat_abs); free(leaf_of);
+    oracle_tree_free(tt);
+    oracle_tree_free(st);
+    return rc;
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

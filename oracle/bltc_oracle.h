@@ -74,6 +74,18 @@ int oracle_bltc_cp(const double* tx, const double* ty, const double* tz, int64_t
                    int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
                    double* phi, double* phi_abs);
 
+/* Cluster-cluster variant (dual tree traversal): sources in a tree with leaf_size,
+ * targets in a tree with batch_size; CC, CP, PC and PP interactions, then interpolation. */
+int oracle_bltc_cc(const double* tx, const double* ty, const double* tz, int64_t nt,
+                   const double* sx, const double* sy, const double* sz, const double* sq,
+                   int64_t ns, double theta, int32_t degree, int32_t leaf_size,
+                   int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
+                   double* phi, double* phi_abs);
+/* The dual traversal's four lists (CC, CP, PC, PP) as (target node, source node) pairs;
+ * counts[4]; t_ids/s_ids sized sum(counts) (NULL on a first call for the counts). */
+int oracle_dual_lists_export(const oracle_tree* tt, const oracle_tree* st, double theta,
+                             int32_t degree, int64_t* counts, int64_t* t_ids, int64_t* s_ids);
+
 int oracle_max_threads(void);
 
 #ifdef __cplusplus

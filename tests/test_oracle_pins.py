@@ -552,3 +552,60 @@ def test_cp_lists_cover_every_pair_once():
             for C in L[key + "_ids"][L[key + "_off"][b]:L[key + "_off"][b + 1]]:
                 cover[tt.begin[C]:tt.begin[C] + tt.count[C]] += 1
         assert (cover == 1).all(), b
+
+
+# ---------------------------------------------------------------------------------------
+# Cluster-cluster variant (dual tree traversal, future work of Sec. V)
+# ---------------------------------------------------------------------------------------
+
+def test_cc_theta_zero_equals_direct_sum():
+    T, S, q = _targets_and_sources(2500, 4000, 20031871)
+    phi, _ = oracle.bltc_cc(T, S, q, 0.0, 4, 300, 170)
+    ref = oracle.direct_sum(np.stack(T), np.stack(S), q)
+    assert oracle.rel_err(ref, phi) < 1e-14
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_cc_polynomial_kernel_is_exact(n):
+    # a kernel of degree n in every target AND source coordinate is reproduced by both
+    # interpolations (CC, CP and PC terms), whatever theta
+    x, y, z, q = _system(12000, 20031873)
+    T = S = (x, y, z)
+    phi, _ = oracle.bltc_cc(T, S, q, 0.7, n, 300, 300, oracle.KERNEL_POLY)
+    ref, ref_abs = oracle.direct_sum(np.stack(T), np.stack(S), q, oracle.KERNEL_POLY, 0.0, n,
+                                     with_abs=True)
+    assert np.max(np.abs(phi - ref) / ref_abs) < 1e-12
+    L = oracle.dual_lists(oracle.Tree(x, y, z, 300), oracle.Tree(x, y, z, 300), 0.7, n)
+    assert len(L["cc"][0]) > 0 and len(L["pp"][0]) > 0
+    # and with separate sets of very different density, the mixed kinds CP and PC appear
+    T2, S2, q2 = _targets_and_sources(6000, 1500, 20031874)
+    phi2, _ = oracle.bltc_cc(T2, S2, q2, 0.7, n, 40, 400, oracle.KERNEL_POLY)
+    ref2, ref2_abs = oracle.direct_sum(np.stack(T2), np.stack(S2), q2, oracle.KERNEL_POLY, 0.0, n,
+                                       with_abs=True)
+    assert np.max(np.abs(phi2 - ref2) / ref2_abs) < 1e-12
+    L2 = oracle.dual_lists(oracle.Tree(*T2, 400), oracle.Tree(*S2, 40), 0.7, n)
+    assert len(L2["cp"][0]) + len(L2["pc"][0]) > 0
+
+
+def test_cc_lists_cover_every_pair_once():
+    # every (target, source) pair lies in exactly one interaction (brute force)
+    T, S, _ = _targets_and_sources(1200, 1500, 20031875)
+    tt, st = oracle.Tree(*T, 60), oracle.Tree(*S, 80)
+    L = oracle.dual_lists(tt, st, 0.7, 2)
+    cover = np.zeros((len(T[0]), len(S[0])), np.int64)
+    for name in ("cc", "cp", "pc", "pp"):
+        for a, c in zip(*L[name]):
+            cover[np.ix_(tt.perm[tt.begin[a]:tt.begin[a] + tt.count[a]],
+                         st.perm[st.begin[c]:st.begin[c] + st.count[c]])] += 1
+    assert (cover == 1).all()
+    assert all(len(L[k][0]) > 0 for k in ("cc", "pp"))
+
+
+def test_cc_error_decay_and_band():
+    x, y, z, q = _system(20000, 20031877)
+    pts = np.stack([x, y, z])
+    ref = oracle.direct_sum(pts, pts, q)
+    errs = [oracle.rel_err(ref, oracle.bltc_cc((x, y, z), (x, y, z), q, 0.7, n, 400, 400)[0])
+            for n in (1, 3, 5, 7)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert 1e-9 < errs[2] < 1e-4 and errs[0] > 1e-4, errs
