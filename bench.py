@@ -472,11 +472,15 @@ def run_serving(args, dist: Dist):
                                              "peak_live_bytes", "budget_bytes")}}
 
 
-# ---- cluster-particle variant -----------------------------------------------------------------
+# ---- cluster-particle and cluster-cluster variants -----------------------------------------------------------------
 
-def run_cp(args, dist: Dist):
-    """The cluster-particle variant (targets interpolated, sources exact) on the same workload:
-    time-to-solution with inputs resident, and its errors next to the treecode's."""
+VARIANT_NAMES = {"cp": "cluster-particle", "cc": "cluster-cluster (dual tree traversal)"}
+
+
+def run_variant(args, dist: Dist):
+    """A variant on the same workload: cp (targets interpolated, sources exact) or cc (dual
+    tree traversal, both sides interpolated); time-to-solution with inputs resident, and its
+    errors next to the treecode's."""
     import torch
 
     import paper_2003_01836_gb300 as b
@@ -494,7 +498,9 @@ def run_cp(args, dist: Dist):
     p = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
                  b.BLTC_PRECISION_MIXED)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
-    solve = lambda pp, out: b.bltc_solve_cp(ctx.h, *X[:3], *X, pp, out)
+    fn = b.bltc_solve_cp if args.variant == "cp" else b.bltc_solve_cc
+    solve = lambda pp, out: fn(ctx.h, *X[:3], *X, pp, out)
+    name = VARIANT_NAMES[args.variant]
     for _ in range(args.warmup):
         solve(p, phi)
     torch.cuda.synchronize()
@@ -517,14 +523,14 @@ def run_cp(args, dist: Dist):
     clocks = sampler.stop()
     launches = b.bltc_context_launch_count(ctx.h) - launches0
     agg = aggregate(sum(step_ms) / len(step_ms), w["n"], dist)
-    out = {"metric": "cluster-particle variant: targets/s (time-to-solution, inputs resident)",
+    out = {"metric": f"{name} variant: targets/s (time-to-solution, inputs resident)",
            "value": agg["targets_per_s"], "unit": "targets/s", "n_gpus": dist.world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 (f64 accumulation and interpolation)", "data": "synthetic",
-           "config": {"workload": "cluster-particle variant on " + WORKLOAD_NAME, "n_particles": w["n"],
-                      "theta": w["theta"], "degree": w["degree"], "target_leaf_size": w["leaf"],
-                      "source_batch_size": w["batch"], "kernel": "coulomb", "precision": "mixed",
+           "config": {"workload": f"{name} variant on " + WORKLOAD_NAME, "n_particles": w["n"],
+                      "theta": w["theta"], "degree": w["degree"], "leaf_size": w["leaf"],
+                      "batch_size": w["batch"], "kernel": "coulomb", "precision": "mixed",
                       "l2": "flushed before every timed step (256 MiB device write)"},
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
            "clocks": clocks, "gpu_launches": int(launches)}
@@ -542,9 +548,10 @@ def run_cp(args, dist: Dist):
         b.bltc_direct_sum(ctx.h, *T, *X[:3], X[3], p64, ref)
         torch.cuda.synchronize()
         h = lambda t: t.cpu().numpy()
-        out["error"] = {"mixed_vs_fp64_gpu_cp": rel_err(h(phi64), h(phi)),
-                        "fp64_cp_vs_direct_sampled": rel_err(h(ref), h(phi64.index_select(0, idx))),
-                        "mixed_cp_vs_direct_sampled": rel_err(h(ref), h(phi.index_select(0, idx))),
+        v = args.variant
+        out["error"] = {f"mixed_vs_fp64_gpu_{v}": rel_err(h(phi64), h(phi)),
+                        f"fp64_{v}_vs_direct_sampled": rel_err(h(ref), h(phi64.index_select(0, idx))),
+                        f"mixed_{v}_vs_direct_sampled": rel_err(h(ref), h(phi.index_select(0, idx))),
                         "mixed_treecode_vs_direct_sampled": rel_err(h(ref), h(tree.index_select(0, idx))),
                         "direct_sample_targets": int(idx.numel())}
     ctx.close()
@@ -596,8 +603,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
                     help="time the serving runtime on the request stream instead")
-    ap.add_argument("--variant", choices=("treecode", "cp"), default="treecode",
-                    help="cp: time the cluster-particle variant on the same workload instead")
+    ap.add_argument("--variant", choices=("treecode", "cp", "cc"), default="treecode",
+                    help="cp / cc: time the cluster-particle or cluster-cluster variant on the "
+                         "same workload instead")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-workers", type=int, default=3)
     args = ap.parse_args(argv)
@@ -609,8 +617,8 @@ def main(argv=None):
             out = run_reference(args, dist)
         elif args.serving:
             out = run_serving(args, dist)
-        elif args.variant == "cp":
-            out = run_cp(args, dist)
+        elif args.variant in ("cp", "cc"):
+            out = run_variant(args, dist)
         else:
             out = run_ours(args, dist)
         if out is not None and dist.rank == 0:

@@ -239,6 +239,29 @@ bltc_status bltc_solve_cp(bltc_context* ctx, const double* tx, const double* ty,
                           int64_t nt, const double* sx, const double* sy, const double* sz,
                           const double* sq, int64_t ns, const bltc_params* params, double* phi);
 
+/* The cluster-cluster variant (dual tree traversal; the paper's future work, Sec. V).
+ * Sources (sx, sy, sz, sq; ns) in a tree with params->leaf_size, targets (tx, ty, tz; nt) in
+ * a tree with params->batch_size.  DualTraversal(T, S) from the two roots: if
+ * (r_T + r_S)/R < theta (Eq. 13) the pair interacts as CC when (n+1)^3 < N_T and
+ * (n+1)^3 < N_S (point potentials of T's Chebyshev grid from S's modified charges), CP when
+ * only (n+1)^3 < N_T (from S's particles), PC when only (n+1)^3 < N_S (T's targets from S's
+ * modified charges), PP otherwise (exact); else leaf-leaf pairs are PP and otherwise T is
+ * split when S is a leaf or (T is not a leaf and r_T >= r_S), S otherwise, children in stored
+ * order.  Each target then adds the interpolants (Eq. 4-8, exact hits) of its clusters'
+ * point potentials.  Device pointers; phi[nt] in the caller's target order.  Errors: as
+ * bltc_solve. */
+bltc_status bltc_solve_cc(bltc_context* ctx, const double* tx, const double* ty, const double* tz,
+                          int64_t nt, const double* sx, const double* sy, const double* sz,
+                          const double* sq, int64_t ns, const bltc_params* params, double* phi);
+/* The dual traversal's interaction lists for two trees (params->theta, params->degree):
+ * counts[4] = the numbers of CC, CP, PC and PP pairs; target_ids / source_ids (HOST arrays of
+ * sum(counts), or NULL for the counts only) receive the pairs' node ids (DFS pre-order),
+ * the four lists one after the other, each level by level in traversal order.  Synchronizes.
+ * Errors: ARG, OOM, CUDA. */
+bltc_status bltc_dual_lists(bltc_context* ctx, const bltc_tree* targets, const bltc_tree* sources,
+                            const bltc_params* params, int64_t* counts, int64_t* target_ids,
+                            int64_t* source_ids);
+
 /* bltc_solve for HOST buffers x, y, z, q, phi (pinned memory recommended): copies the
  * inputs to the device, solves, copies phi back.  Synchronizes.  Errors: as bltc_solve. */
 bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,

@@ -119,6 +119,8 @@ _SIGNATURES = {
     "bltc_solve": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_host": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_cp": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
+    "bltc_solve_cc": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
+    "bltc_dual_lists": ([_vp, _vp, _vp, _P, _vp, _vp, _vp], ctypes.c_int),
     "bltc_solve_targets": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                            ctypes.c_int),
     "bltc_direct_sum": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
@@ -387,6 +389,30 @@ def bltc_solve_cp(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):
     _stream(ctx)
     _check(ctx, lib().bltc_solve_cp(ctx, _ptr(tx), _ptr(ty), _ptr(tz), tx.numel(), _ptr(sx), _ptr(sy),
                                     _ptr(sz), _ptr(sq), sx.numel(), ctypes.byref(p), _ptr(phi)))
+
+
+def bltc_solve_cc(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi):
+    """Cluster-cluster variant: sources in clusters of leaf_size, targets of batch_size."""
+    _stream(ctx)
+    _check(ctx, lib().bltc_solve_cc(ctx, _ptr(tx), _ptr(ty), _ptr(tz), tx.numel(), _ptr(sx), _ptr(sy),
+                                    _ptr(sz), _ptr(sq), sx.numel(), ctypes.byref(p), _ptr(phi)))
+
+
+def bltc_dual_lists(ctx, targets, sources, p: bltc_params):
+    """The dual traversal's lists: {"cc", "cp", "pc", "pp"} -> (target ids, source ids)."""
+    counts = np.zeros(4, np.int64)
+    _check(ctx, lib().bltc_dual_lists(ctx, targets, sources, ctypes.byref(p), counts.ctypes.data,
+                                      None, None))
+    tot = int(counts.sum())
+    t = np.empty(max(tot, 1), np.int64)
+    s = np.empty(max(tot, 1), np.int64)
+    _check(ctx, lib().bltc_dual_lists(ctx, targets, sources, ctypes.byref(p), counts.ctypes.data,
+                                      t.ctypes.data, s.ctypes.data))
+    out, o = {}, 0
+    for name, n in zip(("cc", "cp", "pc", "pp"), counts):
+        out[name] = (t[o:o + n].copy(), s[o:o + n].copy())
+        o += int(n)
+    return out
 
 
 def bltc_solve_host(ctx, x, y, z, q, p: bltc_params, phi):

@@ -449,6 +449,45 @@ bltc_status bltc_solve_cp(bltc_context* ctx, const double* tx, const double* ty,
     });
 }
 
+bltc_status bltc_solve_cc(bltc_context* ctx, const double* tx, const double* ty, const double* tz,
+                          int64_t nt, const double* sx, const double* sy, const double* sz,
+                          const double* sq, int64_t ns, const bltc_params* params, double* phi) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(tx && ty && tz && sx && sy && sz && sq && phi, "solve_cc: NULL pointer");
+        solve_device_cc(&ctx->c, tx, ty, tz, nt, sx, sy, sz, sq, ns, *params, phi);
+    });
+}
+
+bltc_status bltc_dual_lists(bltc_context* ctx, const bltc_tree* targets, const bltc_tree* sources,
+                            const bltc_params* params, int64_t* counts, int64_t* target_ids,
+                            int64_t* source_ids) {
+    if (!ctx || !targets || !sources || !counts) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        DBuf<int2> lists[4];
+        int64_t n[4];
+        dual_lists(&ctx->c, targets->t, sources->t, params->theta, params->degree, lists, n);
+        int64_t o = 0;
+        for (int k = 0; k < 4; ++k) {
+            counts[k] = n[k];
+            if (target_ids && source_ids && n[k] > 0) {
+                std::vector<int2> h(static_cast<size_t>(n[k]));
+                BLTC_CUDA(cudaMemcpyAsync(h.data(), lists[k].p, sizeof(int2) * n[k], cudaMemcpyDeviceToHost,
+                                          ctx->c.stream));
+                BLTC_CUDA(cudaStreamSynchronize(ctx->c.stream));
+                for (int64_t i = 0; i < n[k]; ++i) {
+                    target_ids[o + i] = h[static_cast<size_t>(i)].x;
+                    source_ids[o + i] = h[static_cast<size_t>(i)].y;
+                }
+            }
+            o += n[k];
+        }
+        BLTC_CUDA(cudaStreamSynchronize(ctx->c.stream));
+    });
+}
+
 bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y, const double* z,
                             const double* q, int64_t n, const bltc_params* params, double* phi) {
     if (!ctx) return BLTC_ERR_ARG;

@@ -198,6 +198,13 @@ int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision);
 void solve_device_cp(Context* c, const double* tx, const double* ty, const double* tz, int64_t nt,
                      const double* sx, const double* sy, const double* sz, const double* sq, int64_t ns,
                      const bltc_params& p, double* phi);
+// The cluster-cluster variant (cp.cu): dual tree traversal, then the same sweeps.
+void solve_device_cc(Context* c, const double* tx, const double* ty, const double* tz, int64_t nt,
+                     const double* sx, const double* sy, const double* sz, const double* sq, int64_t ns,
+                     const bltc_params& p, double* phi);
+// The dual traversal's CC, CP, PC and PP lists as (target node, source node) pairs.
+void dual_lists(Context* c, const Tree& tt, const Tree& st, double theta, int degree,
+                DBuf<int2> (&lists)[4], int64_t (&counts)[4]);
 // Compiles the sweeps for a user kernel given as CUDA source (user_kernel.cu); returns its id.
 int register_user_kernel(Context* ctx, const char* source);
 // Compiles a user kernel's sweeps for sm_<arch> without a device and returns the compiler
