@@ -100,6 +100,14 @@ def _load():
                                        c.c_int64, c.c_double, c.c_int32, c.c_int32, c.c_int32,
                                        c.c_int32, c.c_double, c.c_int32, _f64, c.c_void_p]
         lib.oracle_bltc_cp.restype = c.c_int
+        lib.oracle_hermite_factors.argtypes = [c.c_int32, c.c_double, c.c_double, c.c_double, _f64, _f64]
+        lib.oracle_hermite_factors.restype = None
+        lib.oracle_kernel_dG.argtypes = [c.c_int32, c.c_double, c.c_int32, _f64, _f64, _f64]
+        lib.oracle_kernel_dG.restype = c.c_int
+        lib.oracle_bltc_hermite.argtypes = [_f64, _f64, _f64, _f64, c.c_int64, c.c_double, c.c_int32,
+                                            c.c_int32, c.c_int32, c.c_int32, c.c_double, c.c_int32,
+                                            _f64, c.c_void_p]
+        lib.oracle_bltc_hermite.restype = c.c_int
         lib.oracle_bltc_cc.argtypes = lib.oracle_bltc_cp.argtypes
         lib.oracle_bltc_cc.restype = c.c_int
         lib.oracle_dual_lists_export.argtypes = [c.c_void_p, c.c_void_p, c.c_double, c.c_int32,
@@ -335,6 +343,37 @@ def dual_lists(targets: Tree, sources: Tree, theta, degree):
         out[name] = (t[o:o + n].copy(), s[o:o + n].copy())
         o += int(n)
     return out
+
+
+def hermite_factors(degree, lo, hi, y):
+    """The 1-D Hermite basis on the Chebyshev points of [lo, hi]: (H_k(y), K_k(y)), k = 0..n."""
+    h = np.empty(degree + 1)
+    k = np.empty(degree + 1)
+    _load().oracle_hermite_factors(int(degree), float(lo), float(hi), float(y), h, k)
+    return h, k
+
+
+def kernel_derivatives(kernel, kappa, kdeg, x, y):
+    """D^a G(x, y) for a in {0,1}^3 (index a1*4 + a2*2 + a3); None when r^2 == 0."""
+    out = np.empty(8)
+    ok = _load().oracle_kernel_dG(int(kernel), float(kappa), int(kdeg), _c(np.asarray(x, float)),
+                                  _c(np.asarray(y, float)), out)
+    return out if ok else None
+
+
+def bltc_hermite(x, y, z, q, theta, degree, leaf_size, batch_size, kernel=KERNEL_COULOMB,
+                 kappa=0.0, threads=0, with_abs=False):
+    """The barycentric Hermite treecode (targets = sources).  Returns (phi, phi_abs or None)."""
+    lib = _load()
+    x, y, z, q = _c(x), _c(y), _c(z), _c(q)
+    phi = np.empty(x.shape[0])
+    phi_abs = np.empty(x.shape[0]) if with_abs else None
+    rc = lib.oracle_bltc_hermite(x, y, z, q, x.shape[0], float(theta), int(degree), int(leaf_size),
+                                 int(batch_size), int(kernel), float(kappa), int(threads), phi,
+                                 None if phi_abs is None else phi_abs.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle_bltc_hermite failed ({rc})")
+    return phi, phi_abs
 
 
 def rel_err(reference, approx):

@@ -1156,6 +1156,274 @@ done:
     return rc;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Barycentric Hermite treecode (the paper's future work, Sec. V).                         */
+/* ------------------------------------------------------------------------------------ */
+
+/* Reading (the paper names the method without defining it).  On the n+1 Chebyshev points of
+ * Eq. 6 the Hermite interpolant of a function f of one variable is
+ *     p(y) = sum_k f(s_k) H_k(y) + f'(s_k) K_k(y),
+ *     H_k(y) = (1 - 2 L_k'(s_k) (y - s_k)) L_k(y)^2,   K_k(y) = (y - s_k) L_k(y)^2,
+ * with L_k of Eq. 4 and L_k'(s_k) = sum_{j != k} 1/(s_k - s_j); it reproduces polynomials of
+ * degree 2n+1.  The tensor product in three variables needs the 8 mixed derivatives
+ * D^a = d^{a1}/dy1 d^{a2}/dy2 d^{a3}/dy3, a in {0,1}^3 (index a1*4 + a2*2 + a3), so that
+ *     phi(x_i) ~ sum_k sum_a D^a G(x_i, s_k) qhat^a_k,
+ *     qhat^a_k = sum_{y_j in C} q_j B^{a1}_{k1}(y_j1) B^{a2}_{k2}(y_j2) B^{a3}_{k3}(y_j3),
+ * B^0 = H, B^1 = K.  An exact hit y = s_m (Sec. II-C) gives H = e_m, K = 0.  The MAC is
+ * Eq. 13 with the size test 8(n+1)^3 < N_C (the approximation evaluates 8 terms per point).
+ * For a radial kernel G(r), r = |x - y|, d = x - y: D^a G = prod_{l: a_l = 1} d_l * G_|a|(r)
+ * with G_0 = G and G_{m+1}(r) = -G_m'(r)/r. */
+static void hermite_factors(int32_t degree, double lo, double hi, double y, double* h, double* k)
+{
+    double s[ORACLE_MAX_DEGREE + 1], w[ORACLE_MAX_DEGREE + 1], l[ORACLE_MAX_DEGREE + 1];
+    oracle_cheb(degree, lo, hi, s, w);
+    for (int m = 0; m <= degree; ++m) {
+        if (fabs(y - s[m]) < DBL_MIN) {
+            for (int j = 0; j <= degree; ++j) {
+                h[j] = (j == m) ? 1.0 : 0.0;
+                k[j] = 0.0;
+            }
+            return;
+        }
+    }
+    oracle_lagrange(degree, lo, hi, y, l);
+    for (int j = 0; j <= degree; ++j) {
+        double dl = 0.0;
+        for (int m = 0; m <= degree; ++m)
+            if (m != j) dl = dl + 1.0 / (s[j] - s[m]);
+        const double l2 = l[j] * l[j];
+        h[j] = (1.0 - 2.0 * dl * (y - s[j])) * l2;
+        k[j] = (y - s[j]) * l2;
+    }
+}
+
+void oracle_hermite_factors(int32_t degree, double lo, double hi, double y, double* h, double* k)
+{
+    hermite_factors(degree, lo, hi, y, h, k);
+}
+
+/* D^a G(x, y) for the 8 a in {0,1}^3; returns 0 when r^2 == 0 (pair skipped, reading R1).
+ * The polynomial test kernel is prod_l (1 + x_l y_l / 2)^kdeg. */
+static int kernel_dG(int kernel, double kappa, int kdeg, double tx, double ty, double tz,
+                     double sx, double sy, double sz, double* out)
+{
+    const double d[3] = {tx - sx, ty - sy, tz - sz};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2 == 0.0) return 0;
+    if (kernel == ORACLE_KERNEL_POLY) {
+        const double xs[3] = {tx, ty, tz}, ys[3] = {sx, sy, sz};
+        double f[3], df[3];
+        for (int l = 0; l < 3; ++l) {
+            const double b = 1.0 + 0.5 * xs[l] * ys[l];
+            double pm1 = 1.0;
+            for (int m = 0; m < kdeg - 1; ++m) pm1 = pm1 * b;
+            f[l] = pm1 * b;
+            df[l] = (double)kdeg * pm1 * 0.5 * xs[l];
+        }
+        for (int a = 0; a < 8; ++a)
+            out[a] = ((a & 4) ? df[0] : f[0]) * ((a & 2) ? df[1] : f[1]) * ((a & 1) ? df[2] : f[2]);
+        return 1;
+    }
+    double g[4];
+    if (kernel == ORACLE_KERNEL_SOFT) {
+        const double u = r2 + kappa * kappa;         /* (r^2 + eps^2) */
+        const double v = 1.0 / sqrt(u);
+        g[0] = v;
+        g[1] = v / u;
+        g[2] = 3.0 * v / (u * u);
+        g[3] = 15.0 * v / (u * u * u);
+    } else {
+        const double r = sqrt(r2);
+        const double e = (kernel == ORACLE_KERNEL_YUKAWA) ? exp(-kappa * r) : 1.0;
+        const double kr = (kernel == ORACLE_KERNEL_YUKAWA) ? kappa * r : 0.0;
+        g[0] = e / r;
+        g[1] = e * (1.0 + kr) / (r * r2);
+        g[2] = e * (3.0 + 3.0 * kr + kr * kr) / (r * r2 * r2);
+        g[3] = e * (15.0 + 15.0 * kr + 6.0 * kr * kr + kr * kr * kr) / (r * r2 * r2 * r2);
+    }
+    for (int a = 0; a < 8; ++a) {
+        const int m = ((a >> 2) & 1) + ((a >> 1) & 1) + (a & 1);
+        double p = g[m];
+        if (a & 4) p = p * d[0];
+        if (a & 2) p = p * d[1];
+        if (a & 1) p = p * d[2];
+        out[a] = p;
+    }
+    return 1;
+}
+
+int oracle_kernel_dG(int32_t kernel, double kappa, int32_t kdeg, const double* x, const double* y,
+                     double* out)
+{
+    return kernel_dG(kernel, kappa, kdeg, x[0], x[1], x[2], y[0], y[1], y[2], out);
+}
+
+/* Hermite modified charges of every cluster: [n_nodes][8][(n+1)^3], a-major, k in C order. */
+int oracle_hermite_charges(const oracle_tree* t, const double* x, const double* y, const double* z,
+                           const double* q, int32_t degree, int32_t threads, double* qh)
+{
+    if (degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
+    const int n1 = degree + 1;
+    const int64_t P = (int64_t)n1 * n1 * n1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < t->n_nodes; ++c) {
+        double* out = qh + c * 8 * P;
+        for (int64_t k = 0; k < 8 * P; ++k) out[k] = 0.0;
+        double h[3][ORACLE_MAX_DEGREE + 1], kk[3][ORACLE_MAX_DEGREE + 1];
+        for (int64_t i = t->begin[c]; i < t->begin[c] + t->count[c]; ++i) {
+            const int64_t j = t->perm[i];
+            const double yv[3] = {x[j], y[j], z[j]};
+            for (int d = 0; d < 3; ++d)
+                hermite_factors(degree, t->lo[3 * c + d], t->hi[3 * c + d], yv[d], h[d], kk[d]);
+            for (int a = 0; a < 8; ++a) {
+                const double* f1 = (a & 4) ? kk[0] : h[0];
+                const double* f2 = (a & 2) ? kk[1] : h[1];
+                const double* f3 = (a & 1) ? kk[2] : h[2];
+                for (int k1 = 0; k1 < n1; ++k1)
+                    for (int k2 = 0; k2 < n1; ++k2)
+                        for (int k3 = 0; k3 < n1; ++k3)
+                            out[a * P + (k1 * n1 + k2) * n1 + k3] += f1[k1] * f2[k2] * f3[k3] * q[j];
+            }
+        }
+    }
+    return 0;
+}
+
+typedef struct {
+    const oracle_tree *bt, *st;
+    const double *x, *y, *z, *q;
+    const double* qh;
+    double theta, kappa;
+    int32_t kernel, degree;
+    int64_t P;
+    double *phi, *phi_abs;
+} herm_ctx;
+
+static void herm_potential(herm_ctx* c, int64_t B, int64_t C)
+{
+    const double* cb = c->bt->center + 3 * B;
+    const double* cc = c->st->center + 3 * C;
+    double dx = cb[0] - cc[0];
+    double dy = cb[1] - cc[1];
+    double dz = cb[2] - cc[2];
+    double R = sqrt(dx * dx + dy * dy + dz * dz);
+    double ratio = (c->bt->radius[B] + c->st->radius[C]) / R;
+    const int geometric_ok = ratio < c->theta;
+    const int size_ok = 8 * c->P < c->st->count[C];
+    const int n1 = c->degree + 1;
+    if (geometric_ok && size_ok) {
+        double s1[ORACLE_MAX_DEGREE + 1], s2[ORACLE_MAX_DEGREE + 1], s3[ORACLE_MAX_DEGREE + 1];
+        double w[ORACLE_MAX_DEGREE + 1];
+        oracle_cheb(c->degree, c->st->lo[3 * C], c->st->hi[3 * C], s1, w);
+        oracle_cheb(c->degree, c->st->lo[3 * C + 1], c->st->hi[3 * C + 1], s2, w);
+        oracle_cheb(c->degree, c->st->lo[3 * C + 2], c->st->hi[3 * C + 2], s3, w);
+        const double* qh = c->qh + C * 8 * c->P;
+        for (int64_t i = c->bt->begin[B]; i < c->bt->begin[B] + c->bt->count[B]; ++i) {
+            const int64_t t = c->bt->perm[i];
+            double acc = c->phi[t], acc_abs = c->phi_abs ? c->phi_abs[t] : 0.0;
+            for (int k1 = 0; k1 < n1; ++k1)
+                for (int k2 = 0; k2 < n1; ++k2)
+                    for (int k3 = 0; k3 < n1; ++k3) {
+                        double dg[8];
+                        if (!kernel_dG(c->kernel, c->kappa, 2 * c->degree + 1, c->x[t], c->y[t], c->z[t],
+                                       s1[k1], s2[k2], s3[k3], dg))
+                            continue;
+                        const int64_t k = (k1 * n1 + k2) * n1 + k3;
+                        for (int a = 0; a < 8; ++a) {
+                            const double term = dg[a] * qh[a * c->P + k];
+                            acc = acc + term;
+                            acc_abs = acc_abs + fabs(term);
+                        }
+                    }
+            c->phi[t] = acc;
+            if (c->phi_abs) c->phi_abs[t] = acc_abs;
+        }
+    } else if (!geometric_ok && c->st->n_children[C] != 0) {
+        for (int k = 0; k < c->st->n_children[C]; ++k) herm_potential(c, B, c->st->children[8 * C + k]);
+    } else {
+        for (int64_t i = c->bt->begin[B]; i < c->bt->begin[B] + c->bt->count[B]; ++i) {
+            const int64_t t = c->bt->perm[i];
+            double acc = c->phi[t], acc_abs = c->phi_abs ? c->phi_abs[t] : 0.0;
+            for (int64_t m = c->st->begin[C]; m < c->st->begin[C] + c->st->count[C]; ++m) {
+                const int64_t j = c->st->perm[m];
+                double dg[8];
+                if (!kernel_dG(c->kernel, c->kappa, 2 * c->degree + 1, c->x[t], c->y[t], c->z[t],
+                               c->x[j], c->y[j], c->z[j], dg))
+                    continue;
+                const double term = dg[0] * c->q[j];
+                acc = acc + term;
+                acc_abs = acc_abs + fabs(term);
+            }
+            c->phi[t] = acc;
+            if (c->phi_abs) c->phi_abs[t] = acc_abs;
+        }
+    }
+}
+
+/* The Hermite treecode, targets = sources: Algorithm 1 with the Hermite far field above. */
+int oracle_bltc_hermite(const double* x, const double* y, const double* z, const double* q, int64_t n,
+                        double theta, int32_t degree, int32_t leaf_size, int32_t batch_size,
+                        int32_t kernel, double kappa, int32_t threads, double* phi, double* phi_abs)
+{
+    if (n < 1 || degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    oracle_tree *st = NULL, *bt = NULL;
+    if (oracle_tree_build(x, y, z, n, leaf_size, &st)) return -2;
+    if (oracle_tree_build(x, y, z, n, batch_size, &bt)) {
+        oracle_tree_free(st);
+        return -2;
+    }
+    const int64_t n1 = degree + 1, P = n1 * n1 * n1;
+    double* qh = (double*)malloc((size_t)(st->n_nodes * 8 * P) * sizeof(double));
+    int64_t nb = collect_leaves(bt, NULL);
+    int64_t* leaves = (int64_t*)malloc((size_t)nb * sizeof(int64_t));
+    if (!qh || !leaves) {
+        free(qh);
+        free(leaves);
+        oracle_tree_free(st);
+        oracle_tree_free(bt);
+        return -2;
+    }
+    oracle_hermite_charges(st, x, y, z, q, degree, threads, qh);
+    collect_leaves(bt, leaves);
+    for (int64_t i = 0; i < n; ++i) {
+        phi[i] = 0.0;
+        if (phi_abs) phi_abs[i] = 0.0;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < nb; ++b) {
+        herm_ctx c;
+        memset(&c, 0, sizeof(c));
+        c.bt = bt;
+        c.st = st;
+        c.x = x;
+        c.y = y;
+        c.z = z;
+        c.q = q;
+        c.qh = qh;
+        c.theta = theta;
+        c.kappa = kappa;
+        c.kernel = kernel;
+        c.degree = degree;
+        c.P = P;
+        c.phi = phi;
+        c.phi_abs = phi_abs;
+        herm_potential(&c, leaves[b], 0);
+    }
+    free(qh);
+    free(leaves);
+    oracle_tree_free(st);
+    oracle_tree_free(bt);
+    return 0;
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

@@ -86,6 +86,16 @@ int oracle_bltc_cc(const double* tx, const double* ty, const double* tz, int64_t
 int oracle_dual_lists_export(const oracle_tree* tt, const oracle_tree* st, double theta,
                              int32_t degree, int64_t* counts, int64_t* t_ids, int64_t* s_ids);
 
+/* Barycentric Hermite treecode (future work of Sec. V; reading in bltc_oracle.c). */
+void oracle_hermite_factors(int32_t degree, double lo, double hi, double y, double* h, double* k);
+int oracle_kernel_dG(int32_t kernel, double kappa, int32_t kdeg, const double* x, const double* y,
+                     double* out);
+int oracle_hermite_charges(const oracle_tree* t, const double* x, const double* y, const double* z,
+                           const double* q, int32_t degree, int32_t threads, double* qh);
+int oracle_bltc_hermite(const double* x, const double* y, const double* z, const double* q, int64_t n,
+                        double theta, int32_t degree, int32_t leaf_size, int32_t batch_size,
+                        int32_t kernel, double kappa, int32_t threads, double* phi, double* phi_abs);
+
 int oracle_max_threads(void);
 
 #ifdef __cplusplus

@@ -609,3 +609,74 @@ def test_cc_error_decay_and_band():
             for n in (1, 3, 5, 7)]
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
     assert 1e-9 < errs[2] < 1e-4 and errs[0] > 1e-4, errs
+
+
+# ---------------------------------------------------------------------------------------
+# Barycentric Hermite treecode (future work of Sec. V)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_hermite_basis_reproduces_degree_2n_plus_1(n):
+    rng = np.random.default_rng(n)
+    lo, hi = -0.3, 1.7
+    s, _ = oracle.cheb(n, lo, hi)
+    for deg, exact in ((2 * n + 1, True), (2 * n + 2, False)):
+        c = rng.normal(size=deg + 1)
+        p = np.polynomial.Polynomial(c)
+        dp = p.deriv()
+        errs = []
+        for yv in rng.uniform(lo, hi, 25):
+            h, k = oracle.hermite_factors(n, lo, hi, yv)
+            errs.append(abs(np.dot(p(s), h) + np.dot(dp(s), k) - p(yv)) / np.sum(np.abs(c)))
+        assert (max(errs) < 1e-12) == exact, (deg, max(errs))
+    # at a node: H = e_m, K = 0 (the exact-hit rule)
+    h, k = oracle.hermite_factors(n, lo, hi, s[n // 2])
+    assert np.array_equal(h, np.eye(n + 1)[n // 2]) and not np.any(k)
+
+
+@pytest.mark.parametrize("kernel,kappa", [(oracle.KERNEL_COULOMB, 0.0), (oracle.KERNEL_YUKAWA, 0.7),
+                                          (oracle.KERNEL_SOFT, 0.2)])
+def test_kernel_derivatives_match_finite_differences(kernel, kappa):
+    # D^a G from central differences of G itself in the source coordinates
+    x = np.array([0.3, -0.2, 0.5])
+    y0 = np.array([-0.4, 0.35, -0.15])
+    G = lambda yy: oracle.kernel_derivatives(kernel, kappa, 0, x, yy)[0]
+    hstep = 1e-3
+    got = oracle.kernel_derivatives(kernel, kappa, 0, x, y0)
+    for a in range(8):
+        dims = [l for l in range(3) if (a >> (2 - l)) & 1]
+        tot = 0.0
+        for signs in np.ndindex(*([2] * len(dims))):
+            yy = y0.copy()
+            sgn = 1.0
+            for l, sbit in zip(dims, signs):
+                yy[l] += hstep if sbit else -hstep
+                sgn *= 1.0 if sbit else -1.0
+            tot += sgn * G(yy)
+        fd = tot / (2 * hstep) ** len(dims)
+        assert abs(fd - got[a]) <= 1e-5 * max(1.0, abs(got[a])), (a, fd, got[a])
+
+
+def test_hermite_treecode_theta0_polynomial_and_decay():
+    x, y, z, q = _system(8000, 20031879)
+    pts = np.stack([x, y, z])
+    ref = oracle.direct_sum(pts, pts, q)
+    phi, _ = oracle.bltc_hermite(x, y, z, q, 0.0, 3, 300, 300)
+    assert oracle.rel_err(ref, phi) < 1e-14
+    # a kernel of degree 2n+1 in every source coordinate is reproduced exactly
+    n = 2
+    phi, _ = oracle.bltc_hermite(x, y, z, q, 0.7, n, 300, 300, oracle.KERNEL_POLY)
+    refp, refp_abs = oracle.direct_sum(pts, pts, q, oracle.KERNEL_POLY, 0.0, 2 * n + 1, with_abs=True)
+    assert np.max(np.abs(phi - refp) / refp_abs) < 1e-12
+    # the approximation is used: some cluster has more than 8 (n+1)^3 particles and passes
+    st = oracle.Tree(x, y, z, 300)
+    L = oracle.lists(st, st, 0.7, 2 * n + 1)    # (2n+2)^3 = 8 (n+1)^3 points: the same test
+    assert len(L["approx_ids"]) > 0
+    # the error falls with n; Hermite at n is more accurate than Lagrange at n
+    x2, y2, z2, q2 = _system(20000, 20031881)
+    p2 = np.stack([x2, y2, z2])
+    ref2 = oracle.direct_sum(p2, p2, q2)
+    eh = [oracle.rel_err(ref2, oracle.bltc_hermite(x2, y2, z2, q2, 0.7, n, 200, 200)[0]) for n in (1, 2, 3)]
+    assert eh[0] > eh[1] > eh[2], eh
+    el = oracle.rel_err(ref2, oracle.bltc(x2, y2, z2, q2, 0.7, 3, 200, 200)[0])
+    assert eh[2] < el, (eh, el)
