@@ -1209,7 +1209,9 @@ static int kernel_dG(int kernel, double kappa, int kdeg, double tx, double ty, d
 {
     const double d[3] = {tx - sx, ty - sy, tz - sz};
     const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (r2 == 0.0) return 0;
+    if (r2 == 0.0) {
+        return 0;
+    }
     if (kernel == ORACLE_KERNEL_POLY) {
         const double xs[3] = {tx, ty, tz}, ys[3] = {sx, sy, sz};
         double f[3], df[3];
