@@ -474,7 +474,9 @@ def run_serving(args, dist: Dist):
 
 # ---- cluster-particle and cluster-cluster variants -----------------------------------------------------------------
 
-VARIANT_NAMES = {"cp": "cluster-particle", "cc": "cluster-cluster (dual tree traversal)"}
+VARIANT_NAMES = {"cp": "cluster-particle", "cc": "cluster-cluster (dual tree traversal)",
+                 "hermite": "barycentric Hermite (FP64)"}
+HERMITE_DEGREE = 4          # Hermite interpolation on n+1 = 5 points reproduces degree 2n+1 = 9
 
 
 def run_variant(args, dist: Dist):
@@ -495,11 +497,17 @@ def run_variant(args, dist: Dist):
     X = [torch.from_numpy(a).to(f"cuda:{dev}") for a in (x, y, z, q)]
     phi = torch.empty_like(X[0])
     ctx = b.Context(dev)
+    herm = args.variant == "hermite"
+    if herm:
+        w["degree"] = HERMITE_DEGREE
     p = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
-                 b.BLTC_PRECISION_MIXED)
+                 b.BLTC_PRECISION_FP64 if herm else b.BLTC_PRECISION_MIXED)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
-    fn = b.bltc_solve_cp if args.variant == "cp" else b.bltc_solve_cc
-    solve = lambda pp, out: fn(ctx.h, *X[:3], *X, pp, out)
+    if herm:
+        solve = lambda pp, out: b.bltc_solve_hermite(ctx.h, *X, pp, out)
+    else:
+        fn = b.bltc_solve_cp if args.variant == "cp" else b.bltc_solve_cc
+        solve = lambda pp, out: fn(ctx.h, *X[:3], *X, pp, out)
     name = VARIANT_NAMES[args.variant]
     for _ in range(args.warmup):
         solve(p, phi)
@@ -527,10 +535,10 @@ def run_variant(args, dist: Dist):
            "value": agg["targets_per_s"], "unit": "targets/s", "n_gpus": dist.world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32 (f64 accumulation and interpolation)", "data": "synthetic",
+           "dtype": "f64" if herm else "f32 (f64 accumulation and interpolation)", "data": "synthetic",
            "config": {"workload": f"{name} variant on " + WORKLOAD_NAME, "n_particles": w["n"],
                       "theta": w["theta"], "degree": w["degree"], "leaf_size": w["leaf"],
-                      "batch_size": w["batch"], "kernel": "coulomb", "precision": "mixed",
+                      "batch_size": w["batch"], "kernel": "coulomb", "precision": "fp64" if herm else "mixed",
                       "l2": "flushed before every timed step (256 MiB device write)"},
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
            "clocks": clocks, "gpu_launches": int(launches)}
@@ -540,7 +548,8 @@ def run_variant(args, dist: Dist):
         phi64 = torch.empty_like(phi)
         solve(p64, phi64)
         tree = torch.empty_like(phi)
-        ctx.solve(*X, p, tree)
+        ctx.solve(*X, b.params(WORKLOAD["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
+                               b.BLTC_PRECISION_MIXED), tree)
         rng = np.random.default_rng(20031836)
         idx = torch.from_numpy(np.sort(rng.choice(w["n"], size=min(w["n"], 4096), replace=False))).cuda()
         T = [a.index_select(0, idx).contiguous() for a in X[:3]]
@@ -549,11 +558,12 @@ def run_variant(args, dist: Dist):
         torch.cuda.synchronize()
         h = lambda t: t.cpu().numpy()
         v = args.variant
-        out["error"] = {f"mixed_vs_fp64_gpu_{v}": rel_err(h(phi64), h(phi)),
-                        f"fp64_{v}_vs_direct_sampled": rel_err(h(ref), h(phi64.index_select(0, idx))),
-                        f"mixed_{v}_vs_direct_sampled": rel_err(h(ref), h(phi.index_select(0, idx))),
+        out["error"] = {f"fp64_{v}_vs_direct_sampled": rel_err(h(ref), h(phi64.index_select(0, idx))),
                         "mixed_treecode_vs_direct_sampled": rel_err(h(ref), h(tree.index_select(0, idx))),
                         "direct_sample_targets": int(idx.numel())}
+        if not herm:
+            out["error"][f"mixed_vs_fp64_gpu_{v}"] = rel_err(h(phi64), h(phi))
+            out["error"][f"mixed_{v}_vs_direct_sampled"] = rel_err(h(ref), h(phi.index_select(0, idx)))
     ctx.close()
     return out
 
@@ -603,9 +613,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
                     help="time the serving runtime on the request stream instead")
-    ap.add_argument("--variant", choices=("treecode", "cp", "cc"), default="treecode",
-                    help="cp / cc: time the cluster-particle or cluster-cluster variant on the "
-                         "same workload instead")
+    ap.add_argument("--variant", choices=("treecode", "cp", "cc", "hermite"), default="treecode",
+                    help="cp / cc / hermite: time the cluster-particle, cluster-cluster or "
+                         "barycentric Hermite (FP64, n = 4) variant on the same workload instead")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-workers", type=int, default=3)
     args = ap.parse_args(argv)
@@ -617,7 +627,7 @@ def main(argv=None):
             out = run_reference(args, dist)
         elif args.serving:
             out = run_serving(args, dist)
-        elif args.variant in ("cp", "cc"):
+        elif args.variant in ("cp", "cc", "hermite"):
             out = run_variant(args, dist)
         else:
             out = run_ours(args, dist)

@@ -120,6 +120,7 @@ _SIGNATURES = {
     "bltc_solve_host": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_cp": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_cc": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
+    "bltc_solve_hermite": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_dual_lists": ([_vp, _vp, _vp, _P, _vp, _vp, _vp], ctypes.c_int),
     "bltc_solve_targets": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                            ctypes.c_int),
@@ -413,6 +414,13 @@ def bltc_dual_lists(ctx, targets, sources, p: bltc_params):
         out[name] = (t[o:o + n].copy(), s[o:o + n].copy())
         o += int(n)
     return out
+
+
+def bltc_solve_hermite(ctx, x, y, z, q, p: bltc_params, phi):
+    """The barycentric Hermite treecode (FP64, degree <= 7); device tensors."""
+    _stream(ctx)
+    _check(ctx, lib().bltc_solve_hermite(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.numel(),
+                                         ctypes.byref(p), _ptr(phi)))
 
 
 def bltc_solve_host(ctx, x, y, z, q, p: bltc_params, phi):

@@ -488,6 +488,16 @@ bltc_status bltc_dual_lists(bltc_context* ctx, const bltc_tree* targets, const b
     });
 }
 
+bltc_status bltc_solve_hermite(bltc_context* ctx, const double* x, const double* y, const double* z,
+                               const double* q, int64_t n, const bltc_params* params, double* phi) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(x && y && z && q && phi, "solve_hermite: NULL pointer");
+        solve_device_hermite(&ctx->c, x, y, z, q, n, *params, phi);
+    });
+}
+
 bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y, const double* z,
                             const double* q, int64_t n, const bltc_params* params, double* phi) {
     if (!ctx) return BLTC_ERR_ARG;

@@ -194,6 +194,11 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual);
 void prepare_plan(Context* ctx, Lists* L, int degree, int precision);
 // Kernel evaluations the sweep performs for that plan (mutual pairs counted once).
 int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision);
+// The Hermite treecode's sweep (sweep.cu) and the whole solve (hermite.cu).
+void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
+                      const double* qh, const int32_t* qslot, double* phi);
+void solve_device_hermite(Context* c, const double* x, const double* y, const double* z, const double* q,
+                          int64_t n, const bltc_params& p, double* phi);
 // The cluster-particle variant (cp.cu): targets interpolated, sources summed exactly.
 void solve_device_cp(Context* c, const double* tx, const double* ty, const double* tz, int64_t nt,
                      const double* sx, const double* sy, const double* sz, const double* sq, int64_t ns,

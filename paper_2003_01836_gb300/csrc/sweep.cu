@@ -75,6 +75,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp64(SweepArgs a) {
     sweep_fp64_body<KER>(a);
 }
 
+template <int KER>
+__global__ void __launch_bounds__(kThreads, 2) k_sweep_hermite(SweepArgs a) {
+    sweep_hermite_body<KER>(a);
+}
+
 // ---- work plan ------------------------------------------------------------------------
 
 struct PlanArgs {
@@ -554,6 +559,45 @@ void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc
         bt->leaves.p, bt->begin.p, bt->count.p, bt->perm.p, pl.n_chunks.p, pl.part_off.p,
         partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi); ++ctx->launches;
     BLTC_LAUNCH_CHECK("finalize");
+    ctx->mark(Context::kEnd);
+}
+
+// The Hermite treecode's sweep (FP64): Hermite far field with charges qh [slot][8][(n+1)^3],
+// the plain near field, then the finalize.  The lists were built with degree 2n+1, whose
+// (2n+2)^3 = 8 (n+1)^3 points give the Hermite size test and the cost of an approximation.
+void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
+                      const double* qh, const int32_t* qslot, double* phi) {
+    cudaStream_t s = ctx->stream;
+    require(L->bt == bt && L->st == st, "hermite: lists were built for other trees");
+    require(L->degree == 2 * p.degree + 1, "hermite: lists were built for another degree");
+    prepare_plan(ctx, L, L->degree, BLTC_PRECISION_FP64);
+    Plan& pl = L->plan;
+    DBuf<double> partials(ctx, pl.partial_len);
+    DBuf<unsigned int> counter(ctx, 1);
+    BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
+    bltc_params pp = p;
+    pp.precision = BLTC_PRECISION_FP64;
+    SweepArgs a = make_args(ctx, L, bt, st, pp, partials.p, counter.p);
+    a.np1 = p.degree + 1;
+    a.qhat64 = qh;
+    a.qslot = qslot;
+    a.qhat32 = nullptr;
+    const unsigned grid = static_cast<unsigned>(
+        std::min<int64_t>(pl.n_items, 2 * static_cast<int64_t>(std::max(1, ctx->sm_count))));
+    ctx->mark(Context::kSweepBegin);
+    if (pl.n_items > 0) {
+        if (p.kernel == BLTC_KERNEL_YUKAWA) {
+            k_sweep_hermite<BLTC_KERNEL_YUKAWA><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+        } else {
+            k_sweep_hermite<BLTC_KERNEL_COULOMB><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+        }
+        BLTC_LAUNCH_CHECK("sweep hermite");
+    }
+    ctx->mark(Context::kSweepEnd);
+    k_finalize<<<static_cast<unsigned>(L->n_batches), 256, 0, s>>>(
+        bt->leaves.p, bt->begin.p, bt->count.p, bt->perm.p, pl.n_chunks.p, pl.part_off.p,
+        partials.p, L->dir_off.p, pl.dir_sel.p, nullptr, nullptr, phi); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("finalize hermite");
     ctx->mark(Context::kEnd);
 }
 

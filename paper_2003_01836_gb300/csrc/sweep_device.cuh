@@ -713,5 +713,113 @@ __device__ __forceinline__ void sweep_fp64_body(const SweepArgs& a) {
     }
 }
 
+// ---- barycentric Hermite far field (FP64) ------------------------------------------------
+
+// The radial factors G_m(r), m = 0..3, of the mixed derivatives D^a G = prod_{a_l} d_l G_|a|
+// (d = x - y; G_{m+1} = -G_m'/r): Coulomb 1/r, 1/r^3, 3/r^5, 15/r^7 and Yukawa
+// e^{-kr}(1, 1 + kr, 3 + 3kr + (kr)^2, 15 + 15kr + 6(kr)^2 + (kr)^3) / r^(2m+1).
+template <int KER>
+__device__ __forceinline__ void hermite_radial(double r2, double kappa, double (&g)[4]) {
+    const double ri = rsqrt(r2);
+    const double ri2 = ri * ri;
+    double e = 1.0, kr = 0.0;
+    if (KER == BLTC_KERNEL_YUKAWA) {
+        kr = kappa * (r2 * ri);
+        e = exp(-kr);
+    }
+    g[0] = e * ri;
+    g[1] = g[0] * ri2 * (1.0 + kr);
+    g[2] = e * ri * ri2 * ri2 * (3.0 + 3.0 * kr + kr * kr);
+    g[3] = e * ri * ri2 * ri2 * ri2 * (15.0 + 15.0 * kr + 6.0 * kr * kr + kr * kr * kr);
+}
+
+// Far field of cluster C with Hermite modified charges qhat^a_k (a = a1*4 + a2*2 + a3, 8 rows
+// of (n+1)^3 in a.qhat64 at slot a.qslot[C]): phi_i += sum_k sum_a D^a G(x_i, s_k) qhat^a_k.
+template <int KER, int T>
+__device__ void far_hermite_fp64(const SweepArgs& a, int C, const double (&xt)[T], const double (&yt)[T],
+                                 const double (&zt)[T], double (&acc)[T], double* sm) {
+    const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1;
+    const double* qh = a.qhat64 + static_cast<int64_t>(a.qslot[C]) * 8 * P;
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * np1; k += kThreads) {
+        const int d = k / np1, kk = k - d * np1;
+        sm[k] = cheb_point(a.cheb_t, kk, n, a.s_lo[3 * C + d], a.s_hi[3 * C + d]);
+    }
+    double* sq = sm + 3 * np1;
+    for (int k = threadIdx.x; k < 8 * P; k += kThreads) sq[k] = qh[k];
+    __syncthreads();
+    for (int k1 = 0; k1 < np1; ++k1) {
+        for (int k2 = 0; k2 < np1; ++k2) {
+            for (int k3 = 0; k3 < np1; ++k3) {
+                const int k = (k1 * np1 + k2) * np1 + k3;
+                double qa[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) qa[c] = sq[c * P + k];
+#pragma unroll
+                for (int u = 0; u < T; ++u) {
+                    const double d0 = xt[u] - sm[k1], d1 = yt[u] - sm[np1 + k2], d2 = zt[u] - sm[2 * np1 + k3];
+                    const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                    if (r2 == 0.0) continue;                    // as the direct sum (skipped pair)
+                    double g[4];
+                    hermite_radial<KER>(r2, a.kappa, g);
+                    const double d01 = d0 * d1, d02 = d0 * d2, d12 = d1 * d2;
+                    acc[u] += g[0] * qa[0] + g[1] * (d2 * qa[1] + d1 * qa[2] + d0 * qa[4]) +
+                              g[2] * (d12 * qa[3] + d02 * qa[5] + d01 * qa[6]) + g[3] * (d01 * d2) * qa[7];
+                }
+            }
+        }
+    }
+}
+
+template <int KER, int T>
+__device__ void item_hermite(const SweepArgs& a, int4 it, D4* sm) {
+    const int b = it.x;
+    const int B = a.b_leaves[b];
+    const int tb = a.b_begin[B], nb = a.b_count[B];
+    const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
+    double* out = a.partials + a.part_off[b] + static_cast<int64_t>(it.w) * nb;
+    for (int t0 = 0; t0 < nb; t0 += kThreads * T) {
+        double xt[T], yt[T], zt[T], acc[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const int t = min(t0 + static_cast<int>(threadIdx.x) + kThreads * u, nb - 1);
+            xt[u] = a.tx[tb + t];
+            yt[u] = a.ty[tb + t];
+            zt[u] = a.tz[tb + t];
+            acc[u] = 0.0;
+        }
+        for (int e = it.y; e < it.z; ++e) {
+            if (e < na)
+                far_hermite_fp64<KER, T>(a, a.app_ids[a0 + e], xt, yt, zt, acc, reinterpret_cast<double*>(sm));
+            else
+                near_fp64<KER, T>(a, a.dir_ids[d0 + e - na], xt, yt, zt, acc, sm);
+        }
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const int t = t0 + static_cast<int>(threadIdx.x) + kThreads * u;
+            if (t < nb) out[t] = acc[u];
+        }
+    }
+}
+
+template <int KER>
+__device__ __forceinline__ void sweep_hermite_body(const SweepArgs& a) {
+    __shared__ __align__(16) D4 sm[kSmemBytes / sizeof(D4)];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(a.counter, 1u));
+        __syncthreads();
+        const int i = s_item;
+        if (i >= a.n_items) return;
+        const int4 it = a.items[i];
+        const int nb = a.b_count[a.b_leaves[it.x]];
+        if (nb <= kThreads)
+            item_hermite<KER, 1>(a, it, sm);
+        else
+            item_hermite<KER, 2>(a, it, sm);
+    }
+}
+
 }  // namespace sweepdev
 }  // namespace bltc
