@@ -29,6 +29,14 @@ MUTANTS = [
     ("far_field_uses_wrong_axis", "s1[k1], s2[k2], s3[k3], &g))", "s1[k1], s2[k3], s3[k2], &g))"),
     ("self_pair_not_skipped", "if (r2 == 0.0) return 0;", "if (r2 < 0.0) return 0;"),
     ("mac_ignores_size", "int size_ok = c->P < c->st->count[C];", "int size_ok = 1;"),
+    # cluster-particle variant
+    ("cp_point_potential_axes", "s1[k1], s2[k2], s3[k3], sx[j], sy[j],", "s1[k1], s2[k3], s3[k2], sx[j], sy[j],"),
+    # barycentric Hermite treecode
+    ("hermite_H_sign", "h[j] = (1.0 - 2.0 * dl * (y - s[j])) * l2;", "h[j] = (1.0 + 2.0 * dl * (y - s[j])) * l2;"),
+    ("hermite_K_dropped", "k[j] = (y - s[j]) * l2;", "k[j] = 0.0 * l2;"),
+    ("hermite_G2_yukawa_term", "g[2] = e * (3.0 + 3.0 * kr + kr * kr)", "g[2] = e * (3.0 + 2.0 * kr + kr * kr)"),
+    ("hermite_derivative_axis", "if (a & 4) p = p * d[0];", "if (a & 4) p = p * d[2];"),
+    ("hermite_charge_axis", "const double* f1 = (a & 4) ? kk[0] : h[0];", "const double* f1 = (a & 1) ? kk[0] : h[0];"),
 ]
 
 FAST = "not decays and not band and not degenerates"
