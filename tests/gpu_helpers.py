@@ -5,7 +5,7 @@ import oracle
 import paper_2003_01836_gb300 as b
 from paper_2003_01836_gb300 import inputs
 
-# Tolerances ("Parity bars"):
+# Tolerances of the parity tests:
 #   FP64 GPU path vs FP64 oracle: relative 2-norm <= 1e-12, and per target
 #   |phi_gpu - phi_oracle| <= 1e-12 * sum_j |G_ij q_j| (the absolute-value sum of the same terms).
 #   MIXED vs FP64 GPU path: relative 2-norm <= 1e-6, per target <= 2e-5 * the same absolute sum.
