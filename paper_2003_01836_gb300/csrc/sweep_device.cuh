@@ -417,8 +417,9 @@ __device__ void near_mutual(const SweepArgs& a, int C, float tau2, const double 
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += kThreads) {
             const int w0 = ((j / kBlock) % G) * wpg;
-            double sum = 0.0;
-            for (int w = w0; w < w0 + wpg; ++w) sum += static_cast<double>(sbuf[w * kTile + j]);
+            float hs = 0.f, ls = 0.f;       // TwoSum pair: about twice the FP32 precision
+            for (int w = w0; w < w0 + wpg; ++w) two_sum_add(hs, ls, sbuf[w * kTile + j]);
+            const double sum = static_cast<double>(hs) + static_cast<double>(ls);
             if (t0 == 0) mrow[j0 + j] = sum; else mrow[j0 + j] += sum;
         }
     }
@@ -428,10 +429,12 @@ __device__ void near_mutual(const SweepArgs& a, int C, float tau2, const double 
 // memory holds (s, s) pairs of the 3(n+1) point coordinates relative to the batch centre,
 // then (qhat, qhat) pairs of the (n+1)^3 modified charges.  Within a (k1, k2) row the
 // partial r^2 of a target is reused over the n+1 values of k3; runs of rows holding about
-// kBlock terms are summed in FP32 and folded into a TwoSum accumulator.
+// kBlock terms are summed in FP32 and folded into the caller's TwoSum accumulator (hi, lo),
+// which spans all far-field clusters of the work item and is converted to FP64 once: FP64
+// adds run at a small fraction of the FP32 rate on this GPU.
 template <int KER>
 __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const Targets& tg,
-                          double* acc, float2* sm, int g, int G) {
+                          float (&hi)[kT], float (&lo)[kT], float2* sm, int g, int G) {
     const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1;
     const float* qh = a.qhat32 + static_cast<int64_t>(a.qslot[C]) * P;
     __syncthreads();
@@ -450,9 +453,6 @@ __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const T
     const float2* sxp = sm;
     const float2* syp = sm + np1;
     const float2* szp = sm + 2 * np1;
-    float hi[kT], lo[kT];
-#pragma unroll
-    for (int u = 0; u < kT; ++u) hi[u] = lo[u] = 0.f;
     // rows are summed in FP32 in runs of about kBlock terms, then folded by TwoSum
     const int R = np1 * np1, run = max(1, kBlock / np1) * G;
     int k1 = g / np1, k2 = g - k1 * np1;          // (k1, k2) of the current row, stepped by G
@@ -488,8 +488,6 @@ __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const T
             two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
         }
     }
-#pragma unroll
-    for (int u = 0; u < kT; ++u) acc[u * kThreads] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
 }
 
 template <int KER>
@@ -523,30 +521,35 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
             }
             acc[u * kThreads] = 0.0;
         }
-        for (int e = it.y; e < it.z; ++e) {
-            if (e < na)
-                far_mixed<KER>(a, a.app_ids[a0 + e], cb, tg, acc, reinterpret_cast<float2*>(sm), g, G);
-            else {
-                const int de = d0 + e - na;
-                const int C = a.dir_ids[de];
-                const float tau2 = a.dir_tau2[de];
-                const uint8_t sel = a.dir_sel[de];
-                if (sel & kSelSkip) continue;            // evaluated by the partner's mutual entry
-                if (sel & kSelMutual) {
-                    float* sbuf = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + kSmemBytes + kAccBytes);
-                    double* mrow = a.mpart + a.dir_moff[de];
-                    switch (sel & (kSelZero | kSelClose)) {
-                        case 0: near_mutual<KER, false, false>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
-                        case kSelClose: near_mutual<KER, false, true>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
-                        default: near_mutual<KER, true, true>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
-                    }
-                    continue;
-                }
+        {   // far field: an item lists its approximated clusters (e < na) before its leaves
+            float fh[kT], fl[kT];
+#pragma unroll
+            for (int u = 0; u < kT; ++u) fh[u] = fl[u] = 0.f;
+            for (int e = it.y; e < min(it.z, na); ++e)
+                far_mixed<KER>(a, a.app_ids[a0 + e], cb, tg, fh, fl, reinterpret_cast<float2*>(sm), g, G);
+#pragma unroll
+            for (int u = 0; u < kT; ++u) acc[u * kThreads] += static_cast<double>(fh[u]) + static_cast<double>(fl[u]);
+        }
+        for (int e = max(it.y, na); e < it.z; ++e) {
+            const int de = d0 + e - na;
+            const int C = a.dir_ids[de];
+            const float tau2 = a.dir_tau2[de];
+            const uint8_t sel = a.dir_sel[de];
+            if (sel & kSelSkip) continue;            // evaluated by the partner's mutual entry
+            if (sel & kSelMutual) {
+                float* sbuf = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + kSmemBytes + kAccBytes);
+                double* mrow = a.mpart + a.dir_moff[de];
                 switch (sel & (kSelZero | kSelClose)) {
-                    case 0: near_mixed<KER, false, false>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
-                    case kSelClose: near_mixed<KER, false, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
-                    default: near_mixed<KER, true, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                    case 0: near_mutual<KER, false, false>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
+                    case kSelClose: near_mutual<KER, false, true>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
+                    default: near_mutual<KER, true, true>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
                 }
+                continue;
+            }
+            switch (sel & (kSelZero | kSelClose)) {
+                case 0: near_mixed<KER, false, false>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                case kSelClose: near_mixed<KER, false, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                default: near_mixed<KER, true, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
             }
         }
         if (G == 1) {
