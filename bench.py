@@ -568,6 +568,83 @@ def run_variant(args, dist: Dist):
     return out
 
 
+# ---- fixed positions, new charges: the solve replayed as one CUDA graph ---------------------
+
+def run_graph(args, dist: Dist):
+    """Iterative use: the positions stay, every step brings new charges.  The setup (trees,
+    lists, plans) is built once and captured with the charge-dependent launches in one CUDA
+    graph; a step writes the step's charges into the bound tensor and launches the graph."""
+    import torch
+
+    import paper_2003_01836_gb300 as b
+    from paper_2003_01836_gb300 import build, inputs
+    build.build()
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+    x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"] + dist.rank)
+    X = [torch.from_numpy(a).to(f"cuda:{dev}") for a in (x, y, z, q)]
+    charges = [X[3].clone(), torch.from_numpy(np.random.default_rng(20031836 + dist.rank)
+                                              .uniform(-1.0, 1.0, w["n"])).to(f"cuda:{dev}")]
+    qd = X[3].clone()
+    ctx = b.Context(dev)
+    p = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
+                 b.BLTC_PRECISION_MIXED)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = b.Graph(ctx, *X[:3], qd, p)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    for i in range(args.warmup):
+        qd.copy_(charges[i % 2])
+        g.launch()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    step_ms = []
+    launches0 = b.bltc_context_launch_count(ctx.h)
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        qd.copy_(charges[i % 2])
+        g.launch()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    launches = b.bltc_context_launch_count(ctx.h) - launches0
+    agg = aggregate(sum(step_ms) / len(step_ms), w["n"], dist)
+    out = {"metric": "graph variant: re-evaluation with fixed positions and new charges, targets/s",
+           "value": agg["targets_per_s"], "unit": "targets/s", "n_gpus": dist.world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 (f64 accumulation)", "data": "synthetic",
+           "config": {"workload": "solve replayed as one CUDA graph on " + WORKLOAD_NAME, "n_particles": w["n"],
+                      "theta": w["theta"], "degree": w["degree"], "leaf_size": w["leaf"],
+                      "batch_size": w["batch"], "kernel": "coulomb", "precision": "mixed",
+                      "l2": "flushed before every timed step (256 MiB device write)"},
+           "setup_ms": setup_ms, "kernels_per_launch": g.kernels,
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+           "clocks": clocks, "gpu_launches": int(launches)}
+    if not args.no_check:
+        phi_g = g.phi.clone()
+        ref = torch.empty_like(phi_g)
+        ctx.solve(*X[:3], qd, p, ref)
+        torch.cuda.synchronize()
+        out["bits_equal_to_solve"] = bool(torch.equal(phi_g, ref))
+    g.close()
+    ctx.close()
+    return out
+
+
 # ---- reference arm: the oracle --------------------------------------------------------------
 
 def run_reference(args, dist: Dist):
@@ -613,9 +690,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
                     help="time the serving runtime on the request stream instead")
-    ap.add_argument("--variant", choices=("treecode", "cp", "cc", "hermite"), default="treecode",
+    ap.add_argument("--variant", choices=("treecode", "cp", "cc", "hermite", "graph"), default="treecode",
                     help="cp / cc / hermite: time the cluster-particle, cluster-cluster or "
-                         "barycentric Hermite (FP64, n = 4) variant on the same workload instead")
+                         "barycentric Hermite (FP64, n = 4) variant on the same workload instead; "
+                         "graph: replays with fixed positions and new charges")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-workers", type=int, default=3)
     args = ap.parse_args(argv)
@@ -627,6 +705,8 @@ def main(argv=None):
             out = run_reference(args, dist)
         elif args.serving:
             out = run_serving(args, dist)
+        elif args.variant == "graph":
+            out = run_graph(args, dist)
         elif args.variant in ("cp", "cc", "hermite"):
             out = run_variant(args, dist)
         else:

@@ -88,6 +88,7 @@ typedef struct bltc_params {
 typedef struct bltc_context bltc_context;
 typedef struct bltc_tree bltc_tree;
 typedef struct bltc_lists bltc_lists;
+typedef struct bltc_graph bltc_graph;
 
 /* Optional allocator hooks.  alloc returns device memory of >= bytes usable in stream order
  * on `stream`, or NULL; free releases it in stream order.  Default: a CUDA memory pool of
@@ -273,6 +274,30 @@ bltc_status bltc_dual_lists(bltc_context* ctx, const bltc_tree* targets, const b
  * caller's order.  Errors: as bltc_solve (ARG for the restrictions above). */
 bltc_status bltc_solve_hermite(bltc_context* ctx, const double* x, const double* y, const double* z,
                                const double* q, int64_t n, const bltc_params* params, double* phi);
+
+/* A solve with fixed positions, replayed as one CUDA graph (Algorithm 1 with its setup done
+ * once).  Trees (Sec. II-D), lists (Eq. 13) and the work plans depend only on the positions;
+ * the upward pass (Eq. 12) and the sweep (Eq. 9, 11) depend on the charges.  Iterative methods
+ * that apply the same interaction to a new charge vector at every step replay only the latter.
+ *
+ * bltc_graph_create builds the trees and lists for x, y, z (device, n particles, targets =
+ * sources), runs one solve with the charges q into phi (as bltc_solve), allocates every buffer a
+ * replay needs and captures on a private stream: the gather of q into tree order, the upward
+ * pass, the sweep and the finalize into phi.  q and phi (device, n, caller order) are BOUND: each
+ * bltc_graph_launch reads the charges currently in q and overwrites phi, as one cudaGraphLaunch on
+ * the context's stream, with no host synchronisation and no allocation.  The positions are copied
+ * at creation; later changes to x, y, z are not seen.  Parameters as bltc_solve (built-in or
+ * registered kernels, FP64 or mixed); results of a launch are the bits bltc_solve gives for the
+ * same positions and charges.  The graph holds device memory of the context and must be destroyed
+ * before it; q and phi must stay allocated while the graph is launched.
+ * Errors: ARG (parameters, NULL pointers), OOM, CUDA; STATE if launched on another context.
+ * bltc_graph_kernels returns the kernels one launch runs (-1 for NULL). */
+bltc_status bltc_graph_create(bltc_context* ctx, const double* x, const double* y, const double* z,
+                              const double* q, int64_t n, const bltc_params* params, double* phi,
+                              bltc_graph** out);
+bltc_status bltc_graph_launch(bltc_context* ctx, bltc_graph* graph);
+int64_t bltc_graph_kernels(const bltc_graph* graph);
+void bltc_graph_destroy(bltc_graph* graph);
 
 /* bltc_solve for HOST buffers x, y, z, q, phi (pinned memory recommended): copies the
  * inputs to the device, solves, copies phi back.  Synchronizes.  Errors: as bltc_solve. */

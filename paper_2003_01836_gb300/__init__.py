@@ -121,6 +121,10 @@ _SIGNATURES = {
     "bltc_solve_cp": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_cc": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
     "bltc_solve_hermite": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp], ctypes.c_int),
+    "bltc_graph_create": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, _pp], ctypes.c_int),
+    "bltc_graph_launch": ([_vp, _vp], ctypes.c_int),
+    "bltc_graph_kernels": ([_vp], _i64),
+    "bltc_graph_destroy": ([_vp], None),
     "bltc_dual_lists": ([_vp, _vp, _vp, _P, _vp, _vp, _vp], ctypes.c_int),
     "bltc_solve_targets": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                            ctypes.c_int),
@@ -423,6 +427,29 @@ def bltc_solve_hermite(ctx, x, y, z, q, p: bltc_params, phi):
                                          ctypes.byref(p), _ptr(phi)))
 
 
+def bltc_graph_create(ctx, x, y, z, q, p: bltc_params, phi):
+    """Capture a solve with fixed positions; q and phi (device tensors) are bound to the graph."""
+    _stream(ctx)
+    h = ctypes.c_void_p()
+    _check(ctx, lib().bltc_graph_create(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.numel(),
+                                        ctypes.byref(p), _ptr(phi), ctypes.byref(h)))
+    return h.value
+
+
+def bltc_graph_launch(ctx, graph):
+    """Replay: reads the charges now in the bound q, overwrites the bound phi."""
+    _stream(ctx)
+    _check(ctx, lib().bltc_graph_launch(ctx, graph))
+
+
+def bltc_graph_kernels(graph):
+    return int(lib().bltc_graph_kernels(graph))
+
+
+def bltc_graph_destroy(graph):
+    lib().bltc_graph_destroy(graph)
+
+
 def bltc_solve_host(ctx, x, y, z, q, p: bltc_params, phi):
     """Host buffers (numpy arrays or CPU tensors, pinned recommended)."""
     _stream(ctx)
@@ -577,6 +604,38 @@ def bltc_direct_sum_noalloc(ctx, tx, ty, tz, sx, sy, sz, sq, p: bltc_params, phi
 
 
 # ---- convenience owner of a context ----------------------------------------------------
+
+class Graph:
+    """A solve with fixed positions, replayed as one CUDA graph (bltc_graph_*).  The charges
+    tensor ``q`` and the output ``phi`` are bound: write new charges into ``q`` (in place), call
+    ``launch()``, read ``phi``."""
+
+    def __init__(self, ctx, x, y, z, q, p, phi=None):
+        import torch
+        self.ctx = ctx
+        self.q = q
+        self.phi = torch.empty_like(x) if phi is None else phi
+        self.h = bltc_graph_create(ctx.h, x, y, z, q, p, self.phi)
+
+    @property
+    def kernels(self):
+        return bltc_graph_kernels(self.h)
+
+    def launch(self):
+        bltc_graph_launch(self.ctx.h, self.h)
+        return self.phi
+
+    def close(self):
+        if self.h:
+            bltc_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class Context:
     """Owns a bltc context on ``device``; by default the library allocates its working

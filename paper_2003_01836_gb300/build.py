@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbltc.so")
 
 SOURCES = ["api.cu", "scan.cu", "tree.cu", "lists.cu", "upward.cu", "sweep.cu", "direct.cu",
-           "server.cu", "user_kernel.cu", "cp.cu", "hermite.cu"]
+           "server.cu", "user_kernel.cu", "cp.cu", "hermite.cu", "graph.cu"]
 # the sweep device code, embedded as text for run-time compilation of user kernels
 EMBED = ("sweep_device.cuh", "kSweepDeviceSource")
 NO_FMAD = {"tree.cu", "lists.cu"}

@@ -21,11 +21,16 @@ struct bltc_tree {
 struct bltc_lists {
     bltc::Lists l;
 };
+struct bltc_graph {
+    bltc::GraphSolve* g = nullptr;
+    bltc_context* ctx = nullptr;
+};
 
 namespace bltc {
 
 void* Context::dalloc(size_t bytes) {
     void* p = nullptr;
+    if (capturing) throw Error(BLTC_ERR_STATE, "device allocation inside a graph capture");
     if (alloc_fn) {
         p = alloc_fn(bytes, stream, alloc_user);
         if (!p) throw Error(BLTC_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
@@ -496,6 +501,40 @@ bltc_status bltc_solve_hermite(bltc_context* ctx, const double* x, const double*
         require(x && y && z && q && phi, "solve_hermite: NULL pointer");
         solve_device_hermite(&ctx->c, x, y, z, q, n, *params, phi);
     });
+}
+
+bltc_status bltc_graph_create(bltc_context* ctx, const double* x, const double* y, const double* z,
+                              const double* q, int64_t n, const bltc_params* params, double* phi,
+                              bltc_graph** out) {
+    if (!ctx || !out) return BLTC_ERR_ARG;
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(x && y && z && q && phi, "graph_create: NULL pointer");
+        std::unique_ptr<bltc_graph> h(new bltc_graph());
+        h->g = graph_create(&ctx->c, x, y, z, q, n, *params, phi);
+        h->ctx = ctx;
+        *out = h.release();
+    });
+}
+
+bltc_status bltc_graph_launch(bltc_context* ctx, bltc_graph* graph) {
+    if (!ctx) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        require(graph != nullptr && graph->g != nullptr, "graph_launch: NULL graph");
+        if (graph->ctx != ctx) throw Error(BLTC_ERR_STATE, "graph_launch: the graph belongs to another context");
+        graph_launch(&ctx->c, graph->g);
+    });
+}
+
+int64_t bltc_graph_kernels(const bltc_graph* graph) {
+    return graph && graph->g ? graph_kernels(graph->g) : -1;
+}
+
+void bltc_graph_destroy(bltc_graph* graph) {
+    if (!graph) return;
+    graph_destroy(graph->g);
+    delete graph;
 }
 
 bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y, const double* z,

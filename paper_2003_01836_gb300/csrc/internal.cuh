@@ -51,6 +51,7 @@ struct Context {
     int64_t* pinned = nullptr;                  // small pinned host buffer for counters
     static constexpr int kPinnedWords = 64;
     int64_t launches = 0;                       // kernels launched through this context
+    bool capturing = false;                     // inside a graph capture: no allocation allowed
     uint64_t next_serial = 1;
     // Optional phase timing: CUDA events recorded on the stream at the phase boundaries.
     enum Mark { kStart, kTrees, kLists, kUpward, kSweepBegin, kSweepEnd, kEnd, kMarks };
@@ -185,8 +186,39 @@ void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int
                  Lists* out);
 void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int degree,
                               int precision);
+// The upward pass in two parts: prepare_upward marks the clusters, allocates the modified
+// charges in the tree and the pass's work lists (host synchronisation); run_upward only
+// launches kernels (no allocation, no synchronisation), so it can be captured in a graph.
+struct UpwardPlan {
+    int degree = 0, precision = 0;
+    int32_t n_slots = 0, n_items = 0, chunk = 1;
+    DBuf<int32_t> slot_node, item0, list;
+    DBuf<int4> items;
+    DBuf<double> partial, scratch;
+    std::vector<int32_t> h, off;     // marked internal nodes per level and their offsets in list
+};
+void prepare_upward(Context* ctx, Tree* st, const Lists* lists, int degree, int precision,
+                    UpwardPlan* up);
+void run_upward(Context* ctx, Tree* st, const UpwardPlan& up);
+
+// A solve with fixed positions captured as one CUDA graph (graph.cu).
+struct GraphSolve;
+GraphSolve* graph_create(Context* c, const double* x, const double* y, const double* z, const double* q,
+                         int64_t n, const bltc_params& p, double* phi);
+void graph_launch(Context* c, GraphSolve* g);
+int64_t graph_kernels(const GraphSolve* g);
+void graph_destroy(GraphSolve* g);
 void evaluate(Context* ctx, Lists* lists, const Tree* bt, const Tree* st,
               const bltc_params& p, double* phi);
+// evaluate in parts: the work plan (prepare_plan), the sweep's scratch, and the launches
+// alone (run_sweep: no allocation, no synchronisation), for capture in a graph.
+struct SweepBuffers {
+    DBuf<double> partials, mpart;
+    DBuf<unsigned int> counter;
+};
+void alloc_sweep_buffers(Context* ctx, const Lists* lists, SweepBuffers* b);
+void run_sweep(Context* ctx, Lists* lists, const Tree* bt, const Tree* st, const bltc_params& p,
+               double* phi, const SweepBuffers& b);
 void interaction_counts(Context* ctx, const Lists* lists, int64_t* n_dir, int64_t* n_app);
 // Work plan of a list set (items, partial layout, self-pair flags); built once per degree.
 void build_plan(Context* ctx, Lists* L, int degree, bool mutual);

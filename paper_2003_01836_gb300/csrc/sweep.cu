@@ -513,15 +513,26 @@ void prepare_plan(Context* ctx, Lists* L, int degree, int precision) {
 void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
               double* phi) {
     check_eval(L, bt, st, p, phi);
-    cudaStream_t s = ctx->stream;
     prepare_plan(ctx, L, p.degree, p.precision);
-    Plan& pl = L->plan;
-    DBuf<double> partials(ctx, pl.partial_len);
-    DBuf<double> mpart(ctx, pl.mutual ? pl.mpart_len : 0);
-    DBuf<unsigned int> counter(ctx, 1);
-    BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
-    SweepArgs a = make_args(ctx, L, bt, st, p, partials.p, counter.p);
-    a.mpart = pl.mutual ? mpart.p : nullptr;
+    SweepBuffers b;
+    alloc_sweep_buffers(ctx, L, &b);
+    run_sweep(ctx, L, bt, st, p, phi, b);
+}
+
+void alloc_sweep_buffers(Context* ctx, const Lists* L, SweepBuffers* b) {
+    const Plan& pl = L->plan;
+    b->partials = DBuf<double>(ctx, pl.partial_len);
+    b->mpart = DBuf<double>(ctx, pl.mutual ? pl.mpart_len : 0);
+    b->counter = DBuf<unsigned int>(ctx, 1);
+}
+
+void run_sweep(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
+               double* phi, const SweepBuffers& b) {
+    cudaStream_t s = ctx->stream;
+    const Plan& pl = L->plan;
+    BLTC_CUDA(cudaMemsetAsync(b.counter.p, 0, sizeof(unsigned int), s));
+    SweepArgs a = make_args(ctx, L, bt, st, p, b.partials.p, b.counter.p);
+    a.mpart = pl.mutual ? b.mpart.p : nullptr;
     const int per_sm = p.precision == BLTC_PRECISION_MIXED ? kMinBlocks : 2;
     const unsigned grid = static_cast<unsigned>(
         std::min<int64_t>(pl.n_items, per_sm * static_cast<int64_t>(std::max(1, ctx->sm_count))));
@@ -557,7 +568,7 @@ void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc
     ctx->mark(Context::kSweepEnd);
     k_finalize<<<static_cast<unsigned>(L->n_batches), 256, 0, s>>>(
         bt->leaves.p, bt->begin.p, bt->count.p, bt->perm.p, pl.n_chunks.p, pl.part_off.p,
-        partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi); ++ctx->launches;
+        b.partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi); ++ctx->launches;
     BLTC_LAUNCH_CHECK("finalize");
     ctx->mark(Context::kEnd);
 }

@@ -471,8 +471,8 @@ void launch_partial(const UpArgs& a, int32_t n_items, size_t smem, cudaStream_t 
 
 }  // namespace
 
-void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int degree,
-                              int precision) {
+void prepare_upward(Context* ctx, Tree* st, const Lists* lists, int degree, int precision,
+                    UpwardPlan* up) {
     require(degree >= 1 && degree <= BLTC_MAX_DEGREE, "modified charges: degree out of range");
     require(precision == BLTC_PRECISION_FP64 || precision == BLTC_PRECISION_MIXED,
             "modified charges: bad precision");
@@ -483,6 +483,8 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
     const int np1 = degree + 1;
     const int P = np1 * np1 * np1;
     const int64_t m = st->n_nodes;
+    up->degree = degree;
+    up->precision = precision;
 
     DBuf<int32_t> flag(ctx, m), pos(ctx, m), tot(ctx, 2);
     if (lists) {
@@ -511,19 +513,57 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
     st->qhat32 = precision == BLTC_PRECISION_MIXED
                      ? DBuf<float>(ctx, static_cast<int64_t>(n_slots) * P)
                      : DBuf<float>();
-    DBuf<int32_t> slot_node(ctx, n_slots), slot_items(ctx, n_slots), item0(ctx, n_slots + 1);
+    up->n_slots = n_slots;
+    up->slot_node = DBuf<int32_t>(ctx, n_slots);
+    up->item0 = DBuf<int32_t>(ctx, n_slots + 1);
+    DBuf<int32_t> slot_items(ctx, n_slots);
     k_slots<<<grid_for(m, 256), 256, 0, s>>>(flag.p, pos.p, st->count.p, st->nch.p, m, st->qslot.p,
-                                             slot_node.p, slot_items.p); ++ctx->launches;
+                                             up->slot_node.p, slot_items.p); ++ctx->launches;
     BLTC_LAUNCH_CHECK("upward slots");
     if (n_slots == 0) return;
-    exclusive_scan_i32(ctx, slot_items.p, item0.p, n_slots, tot.p + 1);
-    k_append_total<<<1, 1, 0, s>>>(item0.p, n_slots, tot.p + 1); ++ctx->launches;
+    exclusive_scan_i32(ctx, slot_items.p, up->item0.p, n_slots, tot.p + 1);
+    k_append_total<<<1, 1, 0, s>>>(up->item0.p, n_slots, tot.p + 1); ++ctx->launches;
     const int32_t n_items = reinterpret_cast<const int32_t*>(ctx->read_words(tot.p, 1))[1];
-    DBuf<int4> items(ctx, std::max<int32_t>(n_items, 1));
-    k_items<<<grid_for(n_slots, 128), 128, 0, s>>>(slot_node.p, item0.p, st->begin.p,
-                                                   st->count.p, n_slots, items.p); ++ctx->launches;
-    DBuf<double> partial(ctx, static_cast<int64_t>(n_items) * P);
+    up->n_items = n_items;
+    up->items = DBuf<int4>(ctx, std::max<int32_t>(n_items, 1));
+    k_items<<<grid_for(n_slots, 128), 128, 0, s>>>(up->slot_node.p, up->item0.p, st->begin.p,
+                                                   st->count.p, n_slots, up->items.p); ++ctx->launches;
+    up->partial = DBuf<double>(ctx, static_cast<int64_t>(n_items) * P);
+    ctx->cheb_table(degree);
+    // M2M: marked internal nodes per level, deepest level first
+    const int nl = st->n_levels;
+    up->h.assign(static_cast<size_t>(nl), 0);
+    up->off.assign(static_cast<size_t>(nl) + 1, 0);
+    if (nl > 1) {
+        DBuf<int32_t> hist(ctx, 2 * nl + 1);
+        up->list = DBuf<int32_t>(ctx, m);
+        BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * (2 * nl + 1), s));
+        k_level_hist<<<grid_for(m, 256), 256, 0, s>>>(flag.p, st->nch.p, st->level.p, m, hist.p); ++ctx->launches;
+        BLTC_CUDA(cudaMemcpyAsync(up->h.data(), hist.p, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, s));
+        BLTC_CUDA(cudaStreamSynchronize(s));
+        for (int L = 0; L < nl; ++L) up->off[L + 1] = up->off[L] + up->h[L];
+        if (up->off[nl] > 0) {
+            BLTC_CUDA(cudaMemcpyAsync(hist.p + nl, up->off.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, s));
+            BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * nl, s));
+            k_level_fill<<<grid_for(m, 256), 256, 0, s>>>(flag.p, st->nch.p, st->level.p, m, hist.p + nl,
+                                                          hist.p, up->list.p); ++ctx->launches;
+            BLTC_CUDA(cudaStreamSynchronize(s));     // the offsets are read from host memory
+            // scratch rows for 8 children per parent, at most ~32 MB at a time
+            int32_t hmax = 0;
+            for (int L = 0; L < nl; ++L) hmax = std::max(hmax, up->h[L]);
+            up->chunk = static_cast<int32_t>(std::max<int64_t>(
+                1, std::min<int64_t>(hmax, (int64_t(32) << 20) / (8 * static_cast<int64_t>(P) * 8))));
+            up->scratch = DBuf<double>(ctx, static_cast<int64_t>(up->chunk) * 8 * P);
+        }
+    }
+}
 
+void run_upward(Context* ctx, Tree* st, const UpwardPlan& up) {
+    if (up.n_slots == 0) return;
+    cudaStream_t s = ctx->stream;
+    const int degree = up.degree, precision = up.precision;
+    const int np1 = degree + 1;
+    const int P = np1 * np1 * np1;
     UpArgs a{};
     a.px = st->px.p;
     a.py = st->py.p;
@@ -534,66 +574,51 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
     a.lo = st->lo.p;
     a.hi = st->hi.p;
     a.cheb_t = ctx->cheb_table(degree);
-    a.slot_node = slot_node.p;
-    a.items = items.p;
-    a.partial = partial.p;
+    a.slot_node = up.slot_node.p;
+    a.items = up.items.p;
+    a.partial = up.partial.p;
     a.np1 = np1;
-    if (n_items > 0) {
+    if (up.n_items > 0) {
         if (precision == BLTC_PRECISION_MIXED) {
             const size_t sm = upward_smem<float>(np1);
-            if (np1 <= 9) launch_partial<float, 9>(a, n_items, sm, s);
-            else launch_partial<float, BLTC_MAX_DEGREE + 1>(a, n_items, sm, s);
+            if (np1 <= 9) launch_partial<float, 9>(a, up.n_items, sm, s);
+            else launch_partial<float, BLTC_MAX_DEGREE + 1>(a, up.n_items, sm, s);
         } else {
             const size_t sm = upward_smem<double>(np1);
-            if (np1 <= 9) launch_partial<double, 9>(a, n_items, sm, s);
-            else launch_partial<double, BLTC_MAX_DEGREE + 1>(a, n_items, sm, s);
+            if (np1 <= 9) launch_partial<double, 9>(a, up.n_items, sm, s);
+            else launch_partial<double, BLTC_MAX_DEGREE + 1>(a, up.n_items, sm, s);
         }
         ++ctx->launches;
         BLTC_LAUNCH_CHECK("upward partial");
     }
-    k_upward_reduce<<<n_slots, 256, 0, s>>>(partial.p, item0.p, P, st->qhat64.p,
-                                             precision == BLTC_PRECISION_MIXED ? st->qhat32.p
-                                                                               : nullptr); ++ctx->launches;
+    k_upward_reduce<<<up.n_slots, 256, 0, s>>>(up.partial.p, up.item0.p, P, st->qhat64.p,
+                                                precision == BLTC_PRECISION_MIXED ? st->qhat32.p
+                                                                                  : nullptr); ++ctx->launches;
     BLTC_LAUNCH_CHECK("upward reduce");
-    // M2M: marked internal nodes, deepest level first
-    const int nl = st->n_levels;
-    if (nl > 1) {
-        DBuf<int32_t> hist(ctx, 2 * nl + 1), list(ctx, m);
-        BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * (2 * nl + 1), s));
-        k_level_hist<<<grid_for(m, 256), 256, 0, s>>>(flag.p, st->nch.p, st->level.p, m, hist.p); ++ctx->launches;
-        std::vector<int32_t> h(static_cast<size_t>(nl));
-        BLTC_CUDA(cudaMemcpyAsync(h.data(), hist.p, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, s));
-        BLTC_CUDA(cudaStreamSynchronize(s));
-        std::vector<int32_t> off(static_cast<size_t>(nl) + 1, 0);
-        for (int L = 0; L < nl; ++L) off[L + 1] = off[L] + h[L];
-        if (off[nl] > 0) {
-            BLTC_CUDA(cudaMemcpyAsync(hist.p + nl, off.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, s));
-            BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * nl, s));
-            k_level_fill<<<grid_for(m, 256), 256, 0, s>>>(flag.p, st->nch.p, st->level.p, m, hist.p + nl,
-                                                          hist.p, list.p); ++ctx->launches;
-            BLTC_CUDA(cudaStreamSynchronize(s));     // `off` lives on the host stack
-            M2MArgs ma{st->nch.p, st->child.p, st->qslot.p, st->lo.p, st->hi.p, a.cheb_t, st->qhat64.p,
-                       precision == BLTC_PRECISION_MIXED ? st->qhat32.p : nullptr, np1};
-            const size_t sm = m2m_smem_bytes(np1);
-            BLTC_CUDA(cudaFuncSetAttribute(k_m2m_child, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(m2m_smem_bytes(BLTC_MAX_DEGREE + 1))));
-            // scratch rows for 8 children per parent, at most ~32 MB at a time
-            int32_t hmax = 0;
-            for (int L = 0; L < nl; ++L) hmax = std::max(hmax, h[L]);
-            const int32_t chunk = static_cast<int32_t>(std::max<int64_t>(
-                1, std::min<int64_t>(hmax, (int64_t(32) << 20) / (8 * static_cast<int64_t>(P) * 8))));
-            DBuf<double> scratch(ctx, static_cast<int64_t>(chunk) * 8 * P);
-            for (int L = nl - 1; L >= 0; --L) {
-                for (int32_t p0 = 0; p0 < h[L]; p0 += chunk) {
-                    const int32_t np = std::min(chunk, h[L] - p0);
-                    const int32_t* nodes = list.p + off[L] + p0;
-                    k_m2m_child<<<8 * np, 256, sm, s>>>(ma, nodes, scratch.p); ++ctx->launches;
-                    k_m2m_sum<<<np, 256, 0, s>>>(ma, nodes, scratch.p); ++ctx->launches;
-                }
+    const int nl = static_cast<int>(up.h.size());
+    if (nl > 1 && up.off[nl] > 0) {
+        M2MArgs ma{st->nch.p, st->child.p, st->qslot.p, st->lo.p, st->hi.p, a.cheb_t, st->qhat64.p,
+                   precision == BLTC_PRECISION_MIXED ? st->qhat32.p : nullptr, np1};
+        const size_t sm = m2m_smem_bytes(np1);
+        BLTC_CUDA(cudaFuncSetAttribute(k_m2m_child, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(m2m_smem_bytes(BLTC_MAX_DEGREE + 1))));
+        for (int L = nl - 1; L >= 0; --L) {
+            for (int32_t p0 = 0; p0 < up.h[L]; p0 += up.chunk) {
+                const int32_t np = std::min(up.chunk, up.h[L] - p0);
+                const int32_t* nodes = up.list.p + up.off[L] + p0;
+                k_m2m_child<<<8 * np, 256, sm, s>>>(ma, nodes, up.scratch.p); ++ctx->launches;
+                k_m2m_sum<<<np, 256, 0, s>>>(ma, nodes, up.scratch.p); ++ctx->launches;
             }
-            BLTC_LAUNCH_CHECK("upward m2m");
         }
+        BLTC_LAUNCH_CHECK("upward m2m");
     }
+}
+
+void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int degree,
+                              int precision) {
+    UpwardPlan up;
+    prepare_upward(ctx, st, lists, degree, precision, &up);
+    run_upward(ctx, st, up);
 }
 
 }  // namespace bltc
