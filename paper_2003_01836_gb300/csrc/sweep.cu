@@ -466,6 +466,8 @@ static SweepArgs make_args(Context* ctx, const Lists* L, const Tree* bt, const T
     a.b_begin = bt->begin.p;
     a.b_count = bt->count.p;
     a.b_center = bt->center.p;
+    a.b_lo = bt->lo.p;
+    a.b_hi = bt->hi.p;
     a.tx = bt->px.p;
     a.ty = bt->py.p;
     a.tz = bt->pz.p;

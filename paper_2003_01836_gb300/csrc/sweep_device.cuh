@@ -28,6 +28,7 @@ struct SweepArgs {
     const int32_t* b_begin;
     const int32_t* b_count;
     const double* b_center;
+    const double *b_lo, *b_hi;         // batch boxes (close-pair screening)
     const double *tx, *ty, *tz;
     // source clusters
     const int32_t* s_begin;
@@ -175,28 +176,100 @@ __device__ __forceinline__ int groups_for(int nb) {
     return nb > 128 * kT ? 1 : (nb > 64 * kT ? 2 : (nb > 32 * kT ? 4 : 8));
 }
 
-// Near field (Eq. 9) of cluster C.  Shared memory holds each staged source as two float4:
-// (x, x, y, y) and (z, z, q, q), relative to the batch centre, so a packed operand is one
-// aligned register pair.  Sums run over blocks of kBlock sources in FP32, folded into a
-// TwoSum accumulator, then into FP64 per staged tile.
-template <int KER, bool SEL, bool CHECK>
-__device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double cb[3], const Targets& tg,
-                           double* acc, float4* sm, int g, int G, int tb, int nb, int t0,
-                           int l, int tpg) {
-    constexpr int kTile = kNearTile;
-    const int cs = a.s_begin[C], nc = a.s_count[C];
-    for (int j0 = 0; j0 < nc; j0 += kTile) {
-        const int m = min(kTile, nc - j0);
-        __syncthreads();
-        for (int j = threadIdx.x; j < m; j += kThreads) {
-            const int p = cs + j0 + j;
+// Close-pair screening per block of kBlock staged sources.  A source farther than tau from the
+// batch box is farther than tau from every target, so a block of such sources needs no
+// running minimum of r^2.  The test runs on the FP32 batch-relative coordinates with the
+// distance doubled (4 tau^2), far above their rounding (about 2^-24 of the box extent).
+constexpr bool kCloseBlockScreen = true;
+
+// Batch box relative to the batch centre, FP32: lo in .x/.y/.z of bl, hi in bh.
+__device__ __forceinline__ void batch_box_rel(const SweepArgs& a, int B, const double cb[3], float3& bl, float3& bh) {
+    bl = make_float3(__double2float_rn(a.b_lo[3 * B] - cb[0]), __double2float_rn(a.b_lo[3 * B + 1] - cb[1]),
+                     __double2float_rn(a.b_lo[3 * B + 2] - cb[2]));
+    bh = make_float3(__double2float_rn(a.b_hi[3 * B] - cb[0]), __double2float_rn(a.b_hi[3 * B + 1] - cb[1]),
+                     __double2float_rn(a.b_hi[3 * B + 2] - cb[2]));
+}
+
+// Stages sources [j0, j0 + m) of cluster C as (x, x, y, y), (z, z, q, q) relative to the batch
+// centre; with SCREEN, blk[b] = 1 when block b of kBlock staged sources holds a source within
+// 2 tau of the batch box.  Every thread of the block calls it (the flags are warp votes).
+template <bool SCREEN>
+__device__ __forceinline__ void stage_near(const SweepArgs& a, int p0, int m, const double cb[3], float4* sm,
+                                           uint8_t* blk, float3 bl, float3 bh, float tau2) {
+    for (int j0 = 0; j0 < m; j0 += kThreads) {
+        const int j = j0 + static_cast<int>(threadIdx.x);
+        bool close = false;
+        if (j < m) {
+            const int p = p0 + j;
             const float sx = __double2float_rn(a.sx[p] - cb[0]);
             const float sy = __double2float_rn(a.sy[p] - cb[1]);
             const float sz = __double2float_rn(a.sz[p] - cb[2]);
             const float sq = __double2float_rn(a.sq[p]);
             sm[2 * j] = make_float4(sx, sx, sy, sy);
             sm[2 * j + 1] = make_float4(sz, sz, sq, sq);
+            if (SCREEN) {
+                const float gx = fmaxf(fmaxf(bl.x - sx, sx - bh.x), 0.f);
+                const float gy = fmaxf(fmaxf(bl.y - sy, sy - bh.y), 0.f);
+                const float gz = fmaxf(fmaxf(bl.z - sz, sz - bh.z), 0.f);
+                close = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < 4.f * tau2;
+            }
         }
+        if (SCREEN) {
+            static_assert(kBlock == 32, "one warp vote per block of staged sources");
+            const unsigned v = __ballot_sync(0xffffffffu, close);
+            const int first = j0 + (static_cast<int>(threadIdx.x) & ~31);
+            if ((threadIdx.x & 31) == 0 && first < m) blk[first / kBlock] = v != 0u;
+        }
+    }
+}
+
+// One block [jb, je) of staged sources against this thread's targets: packed FP32 sums in f,
+// and with CHK the smallest non-zero r^2 met, for the close-pair correction.
+template <int KER, bool SEL, bool CHK>
+__device__ __forceinline__ void near_block(const SweepArgs& a, const float4* sm, int jb, int je, const Targets& tg,
+                                           float2 (&f)[kH], float& rmin) {
+#pragma unroll 4
+    for (int j = jb; j < je; ++j) {
+        const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
+        const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
+        const float2 sz = make_float2(p1.x, p1.y), sq = make_float2(p1.z, p1.w);
+#pragma unroll
+        for (int v = 0; v < kH; ++v) {
+            const float2 dx = add2(sx, tg.x[v]);
+            const float2 dy = add2(sy, tg.y[v]);
+            const float2 dz = add2(sz, tg.z[v]);
+            const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+            if (CHK) {
+                if (SEL) {
+                    rmin = fminf(rmin, r2.x > 0.f ? r2.x : 3.0e38f);
+                    rmin = fminf(rmin, r2.y > 0.f ? r2.y : 3.0e38f);
+                } else {
+                    rmin = fminf(rmin, fminf(r2.x, r2.y));
+                }
+            }
+            f[v] = fma2(sq, ri2_mixed<KER>(r2, a.neg_kappa_log2e, a.param32, SEL), f[v]);
+        }
+    }
+}
+
+// Near field (Eq. 9) of cluster C.  Shared memory holds each staged source as two float4:
+// (x, x, y, y) and (z, z, q, q), relative to the batch centre, so a packed operand is one
+// aligned register pair.  Sums run over blocks of kBlock sources in FP32, folded into a
+// TwoSum accumulator, then into FP64 per staged tile.
+template <int KER, bool SEL, bool CHECK>
+__device__ void near_mixed(const SweepArgs& a, int C, int B, float tau2, const double cb[3], const Targets& tg,
+                           double* acc, float4* sm, int g, int G, int tb, int nb, int t0,
+                           int l, int tpg) {
+    constexpr int kTile = kNearTile;
+    constexpr bool SCREEN = CHECK && kCloseBlockScreen;
+    __shared__ uint8_t blk[kTile / kBlock];
+    const int cs = a.s_begin[C], nc = a.s_count[C];
+    float3 bl = make_float3(0.f, 0.f, 0.f), bh = bl;
+    if (SCREEN) batch_box_rel(a, B, cb, bl, bh);
+    for (int j0 = 0; j0 < nc; j0 += kTile) {
+        const int m = min(kTile, nc - j0);
+        __syncthreads();
+        stage_near<SCREEN>(a, cs + j0, m, cb, sm, blk, bl, bh, tau2);
         __syncthreads();
         float hi[kT], lo[kT];
 #pragma unroll
@@ -207,28 +280,10 @@ __device__ void near_mixed(const SweepArgs& a, int C, float tau2, const double c
 #pragma unroll
             for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
             float rmin = 3.0e38f;      // smallest non-zero r^2 this thread met in the block
-#pragma unroll 4
-            for (int j = jb; j < je; ++j) {
-                const float4 p0 = sm[2 * j], p1 = sm[2 * j + 1];
-                const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
-                const float2 sz = make_float2(p1.x, p1.y), sq = make_float2(p1.z, p1.w);
-#pragma unroll
-                for (int v = 0; v < kH; ++v) {
-                    const float2 dx = add2(sx, tg.x[v]);
-                    const float2 dy = add2(sy, tg.y[v]);
-                    const float2 dz = add2(sz, tg.z[v]);
-                    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                    if (CHECK) {
-                        if (SEL) {
-                            rmin = fminf(rmin, r2.x > 0.f ? r2.x : 3.0e38f);
-                            rmin = fminf(rmin, r2.y > 0.f ? r2.y : 3.0e38f);
-                        } else {
-                            rmin = fminf(rmin, fminf(r2.x, r2.y));
-                        }
-                    }
-                    f[v] = fma2(sq, ri2_mixed<KER>(r2, a.neg_kappa_log2e, a.param32, SEL), f[v]);
-                }
-            }
+            if (CHECK && (!SCREEN || blk[jb / kBlock]))
+                near_block<KER, SEL, CHECK>(a, sm, jb, je, tg, f, rmin);
+            else
+                near_block<KER, SEL, false>(a, sm, jb, je, tg, f, rmin);
 #pragma unroll
             for (int v = 0; v < kH; ++v) {
                 two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
@@ -293,6 +348,50 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
     return y;
 }
 
+// One block [jb, je) of staged sources of a mutual pair: packed sums for this thread's targets
+// in f, each source's sum over the warp's targets into sbuf, and with CHK the smallest
+// non-zero r^2 met.
+template <int KER, bool SEL, bool CHK>
+__device__ __forceinline__ void near_mutual_block(const SweepArgs& a, const float4* sm, int jb, int je,
+                                                  const Targets& tg, const float2 (&qt)[kH], float2 (&f)[kH],
+                                                  float& rmin, float* sbuf, int warp, int lane) {
+    constexpr int kTile = kNearTile;
+    for (int j8 = jb; j8 < je; j8 += 8) {
+        float gs[8];
+#pragma unroll
+        for (int s8 = 0; s8 < 8; ++s8) {
+            gs[s8] = 0.f;
+            if (j8 + s8 < je) {
+                const float4 p0 = sm[2 * (j8 + s8)], p1 = sm[2 * (j8 + s8) + 1];
+                const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
+                const float2 sz = make_float2(p1.x, p1.y), sq = make_float2(p1.z, p1.w);
+                float2 g2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int v = 0; v < kH; ++v) {
+                    const float2 dx = add2(sx, tg.x[v]);
+                    const float2 dy = add2(sy, tg.y[v]);
+                    const float2 dz = add2(sz, tg.z[v]);
+                    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                    if (CHK) {
+                        if (SEL) {
+                            rmin = fminf(rmin, r2.x > 0.f ? r2.x : 3.0e38f);
+                            rmin = fminf(rmin, r2.y > 0.f ? r2.y : 3.0e38f);
+                        } else {
+                            rmin = fminf(rmin, fminf(r2.x, r2.y));
+                        }
+                    }
+                    const float2 ri = ri2_mixed<KER>(r2, a.neg_kappa_log2e, a.param32, SEL);
+                    f[v] = fma2(sq, ri, f[v]);
+                    g2 = fma2(qt[v], ri, g2);
+                }
+                gs[s8] = g2.x + g2.y;
+            }
+        }
+        const float wsum = warp_sum8(gs, lane);
+        if ((lane & 3) == 0 && j8 + (lane >> 2) < je) sbuf[warp * kTile + j8 + (lane >> 2)] = wsum;
+    }
+}
+
 // Near field of a mutual pair: batch B (the targets) and leaf C are each in the other's
 // direct list and are the same particles as sources and targets, so one evaluation of
 // G(x_i, y_j) serves both phi_i += G q_j (as in near_mixed) and phi_j += G q_i (Eq. 9 for C's
@@ -301,11 +400,15 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
 // warp adds its lanes (warp_sum8), and after the tile the group's warps are added in warp
 // order into C's mutual row (FP64), so the result does not depend on scheduling.
 template <int KER, bool SEL, bool CHECK>
-__device__ void near_mutual(const SweepArgs& a, int C, float tau2, const double cb[3], const Targets& tg,
+__device__ void near_mutual(const SweepArgs& a, int C, int B, float tau2, const double cb[3], const Targets& tg,
                             double* acc, float4* sm, float* sbuf, double* mrow, int g, int G, int tb,
                             int nb, int t0, int l, int tpg) {
     constexpr int kTile = kNearTile;
+    constexpr bool SCREEN = CHECK && kCloseBlockScreen;
+    __shared__ uint8_t blk[kTile / kBlock];
     const int cs = a.s_begin[C], nc = a.s_count[C];
+    float3 bl = make_float3(0.f, 0.f, 0.f), bh = bl;
+    if (SCREEN) batch_box_rel(a, B, cb, bl, bh);
     const int lane = static_cast<int>(threadIdx.x) & 31, warp = static_cast<int>(threadIdx.x) >> 5;
     const int wpg = tpg >> 5;                            // warps per group
     // this thread's target charges (0 for the padding slots past the batch)
@@ -319,15 +422,7 @@ __device__ void near_mutual(const SweepArgs& a, int C, float tau2, const double 
     for (int j0 = 0; j0 < nc; j0 += kTile) {
         const int m = min(kTile, nc - j0);
         __syncthreads();
-        for (int j = threadIdx.x; j < m; j += kThreads) {
-            const int p = cs + j0 + j;
-            const float sx = __double2float_rn(a.sx[p] - cb[0]);
-            const float sy = __double2float_rn(a.sy[p] - cb[1]);
-            const float sz = __double2float_rn(a.sz[p] - cb[2]);
-            const float sq = __double2float_rn(a.sq[p]);
-            sm[2 * j] = make_float4(sx, sx, sy, sy);
-            sm[2 * j + 1] = make_float4(sz, sz, sq, sq);
-        }
+        stage_near<SCREEN>(a, cs + j0, m, cb, sm, blk, bl, bh, tau2);
         __syncthreads();
         float hi[kT], lo[kT];
 #pragma unroll
@@ -338,40 +433,10 @@ __device__ void near_mutual(const SweepArgs& a, int C, float tau2, const double 
 #pragma unroll
             for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
             float rmin = 3.0e38f;
-            for (int j8 = jb; j8 < je; j8 += 8) {
-                float gs[8];
-#pragma unroll
-                for (int s8 = 0; s8 < 8; ++s8) {
-                    gs[s8] = 0.f;
-                    if (j8 + s8 < je) {
-                        const float4 p0 = sm[2 * (j8 + s8)], p1 = sm[2 * (j8 + s8) + 1];
-                        const float2 sx = make_float2(p0.x, p0.y), sy = make_float2(p0.z, p0.w);
-                        const float2 sz = make_float2(p1.x, p1.y), sq = make_float2(p1.z, p1.w);
-                        float2 g2 = make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int v = 0; v < kH; ++v) {
-                            const float2 dx = add2(sx, tg.x[v]);
-                            const float2 dy = add2(sy, tg.y[v]);
-                            const float2 dz = add2(sz, tg.z[v]);
-                            const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                            if (CHECK) {
-                                if (SEL) {
-                                    rmin = fminf(rmin, r2.x > 0.f ? r2.x : 3.0e38f);
-                                    rmin = fminf(rmin, r2.y > 0.f ? r2.y : 3.0e38f);
-                                } else {
-                                    rmin = fminf(rmin, fminf(r2.x, r2.y));
-                                }
-                            }
-                            const float2 ri = ri2_mixed<KER>(r2, a.neg_kappa_log2e, a.param32, SEL);
-                            f[v] = fma2(sq, ri, f[v]);
-                            g2 = fma2(qt[v], ri, g2);
-                        }
-                        gs[s8] = g2.x + g2.y;
-                    }
-                }
-                const float wsum = warp_sum8(gs, lane);
-                if ((lane & 3) == 0 && j8 + (lane >> 2) < je) sbuf[warp * kTile + j8 + (lane >> 2)] = wsum;
-            }
+            if (CHECK && (!SCREEN || blk[jb / kBlock]))
+                near_mutual_block<KER, SEL, CHECK>(a, sm, jb, je, tg, qt, f, rmin, sbuf, warp, lane);
+            else
+                near_mutual_block<KER, SEL, false>(a, sm, jb, je, tg, qt, f, rmin, sbuf, warp, lane);
 #pragma unroll
             for (int v = 0; v < kH; ++v) {
                 two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
@@ -540,16 +605,16 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
                 float* sbuf = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + kSmemBytes + kAccBytes);
                 double* mrow = a.mpart + a.dir_moff[de];
                 switch (sel & (kSelZero | kSelClose)) {
-                    case 0: near_mutual<KER, false, false>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
-                    case kSelClose: near_mutual<KER, false, true>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
-                    default: near_mutual<KER, true, true>(a, C, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
+                    case 0: near_mutual<KER, false, false>(a, C, B, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
+                    case kSelClose: near_mutual<KER, false, true>(a, C, B, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
+                    default: near_mutual<KER, true, true>(a, C, B, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
                 }
                 continue;
             }
             switch (sel & (kSelZero | kSelClose)) {
-                case 0: near_mixed<KER, false, false>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
-                case kSelClose: near_mixed<KER, false, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
-                default: near_mixed<KER, true, true>(a, C, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                case 0: near_mixed<KER, false, false>(a, C, B, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                case kSelClose: near_mixed<KER, false, true>(a, C, B, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
+                default: near_mixed<KER, true, true>(a, C, B, tau2, cb, tg, acc, sm, g, G, tb, nb, t0, l, tpg); break;
             }
         }
         if (G == 1) {
