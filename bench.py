@@ -337,12 +337,26 @@ def check_errors(ctx, b, X, p, w, phi_mixed):
     ref = torch.empty_like(T[0])
     b.bltc_direct_sum(ctx.h, *T, *X[:3], X[3], p64, ref)
     torch.cuda.synchronize()
+    # the GPU direct sum (Eq. 1) over all targets, FP32 evaluation with FP64 accumulation: the
+    # time-to-solution the treecode is compared with (the FP64 direct sum over all 1e6 targets
+    # would take tens of seconds on this GPU's FP64 rate, so only its sample is run)
+    pmx = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
+                   b.BLTC_PRECISION_MIXED)
+    dmx = torch.empty_like(phi_mx)
+    b.bltc_direct_sum(ctx.h, *T, *X[:3], X[3], pmx, ref.clone())       # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.bltc_direct_sum(ctx.h, *X[:3], *X[:3], X[3], pmx, dmx)
+    e1.record()
+    e1.synchronize()
     h = lambda t: t.cpu().numpy()
     e_mx_64 = rel_err(h(phi64), h(phi_mx))
     return {"mixed_vs_fp64_gpu_bltc": e_mx_64, "meets_1e-6": bool(e_mx_64 <= 1e-6),
             "fp64_bltc_vs_direct_sampled": rel_err(h(ref), h(phi64.index_select(0, idx))),
             "mixed_bltc_vs_direct_sampled": rel_err(h(ref), h(phi_mx.index_select(0, idx))),
-            "fp64_gpu_bltc_seconds": t64, "direct_sample_targets": int(idx.numel())}
+            "fp64_gpu_bltc_seconds": t64, "direct_sample_targets": int(idx.numel()),
+            "gpu_direct_sum_mixed_seconds": e0.elapsed_time(e1) * 1e-3,
+            "gpu_direct_sum_mixed_vs_fp64_sampled": rel_err(h(ref), h(dmx.index_select(0, idx)))}
 
 
 def run_e2e(ctx, b, x, y, z, q, p, args, dist, w):
