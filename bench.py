@@ -489,7 +489,7 @@ def run_serving(args, dist: Dist):
 # ---- cluster-particle and cluster-cluster variants -----------------------------------------------------------------
 
 VARIANT_NAMES = {"cp": "cluster-particle", "cc": "cluster-cluster (dual tree traversal)",
-                 "hermite": "barycentric Hermite (FP64)"}
+                 "hermite": "barycentric Hermite"}
 HERMITE_DEGREE = 4          # Hermite interpolation on n+1 = 5 points reproduces degree 2n+1 = 9
 
 
@@ -515,7 +515,7 @@ def run_variant(args, dist: Dist):
     if herm:
         w["degree"] = HERMITE_DEGREE
     p = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
-                 b.BLTC_PRECISION_FP64 if herm else b.BLTC_PRECISION_MIXED)
+                 b.BLTC_PRECISION_MIXED)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
     if herm:
         solve = lambda pp, out: b.bltc_solve_hermite(ctx.h, *X, pp, out)
@@ -549,10 +549,10 @@ def run_variant(args, dist: Dist):
            "value": agg["targets_per_s"], "unit": "targets/s", "n_gpus": dist.world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if herm else "f32 (f64 accumulation and interpolation)", "data": "synthetic",
+           "dtype": "f32 (f64 accumulation and interpolation)", "data": "synthetic",
            "config": {"workload": f"{name} variant on " + WORKLOAD_NAME, "n_particles": w["n"],
                       "theta": w["theta"], "degree": w["degree"], "leaf_size": w["leaf"],
-                      "batch_size": w["batch"], "kernel": "coulomb", "precision": "fp64" if herm else "mixed",
+                      "batch_size": w["batch"], "kernel": "coulomb", "precision": "mixed",
                       "l2": "flushed before every timed step (256 MiB device write)"},
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
            "clocks": clocks, "gpu_launches": int(launches)}
@@ -574,10 +574,9 @@ def run_variant(args, dist: Dist):
         v = args.variant
         out["error"] = {f"fp64_{v}_vs_direct_sampled": rel_err(h(ref), h(phi64.index_select(0, idx))),
                         "mixed_treecode_vs_direct_sampled": rel_err(h(ref), h(tree.index_select(0, idx))),
-                        "direct_sample_targets": int(idx.numel())}
-        if not herm:
-            out["error"][f"mixed_vs_fp64_gpu_{v}"] = rel_err(h(phi64), h(phi))
-            out["error"][f"mixed_{v}_vs_direct_sampled"] = rel_err(h(ref), h(phi.index_select(0, idx)))
+                        "direct_sample_targets": int(idx.numel()),
+                        f"mixed_vs_fp64_gpu_{v}": rel_err(h(phi64), h(phi)),
+                        f"mixed_{v}_vs_direct_sampled": rel_err(h(ref), h(phi.index_select(0, idx)))}
     ctx.close()
     return out
 
@@ -706,7 +705,7 @@ def main(argv=None):
                     help="time the serving runtime on the request stream instead")
     ap.add_argument("--variant", choices=("treecode", "cp", "cc", "hermite", "graph"), default="treecode",
                     help="cp / cc / hermite: time the cluster-particle, cluster-cluster or "
-                         "barycentric Hermite (FP64, n = 4) variant on the same workload instead; "
+                         "barycentric Hermite (n = 4) variant on the same workload instead; "
                          "graph: replays with fixed positions and new charges")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-workers", type=int, default=3)

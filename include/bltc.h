@@ -263,15 +263,17 @@ bltc_status bltc_dual_lists(bltc_context* ctx, const bltc_tree* targets, const b
                             const bltc_params* params, int64_t* counts, int64_t* target_ids,
                             int64_t* source_ids);
 
-/* The barycentric Hermite treecode (the paper's future work, Sec. V), FP64, targets =
+/* The barycentric Hermite treecode (the paper's future work, Sec. V), targets =
  * sources.  On the n+1 Chebyshev points of each approximated cluster the kernel is
  * interpolated with values and first derivatives (H_k = (1 - 2 L_k'(s_k)(y - s_k)) L_k^2,
  * K_k = (y - s_k) L_k^2; exact hits give H = e_m, K = 0), exact for degree 2n+1:
  * phi(x_i) ~ sum_k sum_a D^a G(x_i, s_k) qhat^a_k over the 8 mixed derivatives
  * a in {0,1}^3, with qhat^a_k = sum_j q_j B^a1_k1 B^a2_k2 B^a3_k3 (y_j), B^0 = H, B^1 = K.
- * The MAC is Eq. 13 with the size test 8 (n+1)^3 < N_C.  params->precision must be FP64,
- * 1 <= params->degree <= 7, kernel Coulomb or Yukawa.  Device pointers, phi[n] in the
- * caller's order.  Errors: as bltc_solve (ARG for the restrictions above). */
+ * The MAC is Eq. 13 with the size test 8 (n+1)^3 < N_C.  params->precision FP64, or MIXED
+ * (the far field's 8 terms in FP32 on batch-relative coordinates with FP32 charges, the
+ * treecode's mixed near field, FP64 accumulation); 1 <= params->degree <= 7, kernel Coulomb or
+ * Yukawa.  Device pointers, phi[n] in the caller's order.  Errors: as bltc_solve (ARG for the
+ * restrictions above). */
 bltc_status bltc_solve_hermite(bltc_context* ctx, const double* x, const double* y, const double* z,
                                const double* q, int64_t n, const bltc_params* params, double* phi);
 

@@ -421,7 +421,7 @@ def bltc_dual_lists(ctx, targets, sources, p: bltc_params):
 
 
 def bltc_solve_hermite(ctx, x, y, z, q, p: bltc_params, phi):
-    """The barycentric Hermite treecode (FP64, degree <= 7); device tensors."""
+    """The barycentric Hermite treecode (FP64 or mixed, degree <= 7); device tensors."""
     _stream(ctx)
     _check(ctx, lib().bltc_solve_hermite(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.numel(),
                                          ctypes.byref(p), _ptr(phi)))

@@ -11,9 +11,11 @@
 // builder applies when given degree 2n+1 ((2n+2)^3 = 8 (n+1)^3).
 //
 // GPU mapping: the lists and the work plan are the treecode's; the modified charges of each
-// approximated cluster are summed from its particles (k_herm_partial, one block per chunk of
-// a cluster's particles, a fixed-order reduction per cluster); the sweep's far field
-// evaluates the 8 derivative terms per point (far_hermite_fp64).
+// approximated cluster are summed from its particles in FP64 (k_herm_partial, one block per
+// chunk of a cluster's particles, a fixed-order reduction per cluster, an FP32 copy for the
+// mixed path); the sweep's far field evaluates the 8 derivative terms per point
+// (far_hermite_fp64, or far_hermite_mixed in FP32 on batch-relative coordinates beside the
+// treecode's mixed near field).
 #include <algorithm>
 
 #include "internal.cuh"
@@ -162,13 +164,14 @@ __global__ void __launch_bounds__(kHThreads) k_herm_partial(const double* __rest
 }
 
 __global__ void k_h_reduce(const double* __restrict__ partial, const int32_t* __restrict__ item0, int Q,
-                           double* qh) {
+                           double* qh, float* qh32) {
     const int slot = blockIdx.x;
     const int i0 = item0[slot], i1 = item0[slot + 1];
     for (int k = threadIdx.x; k < Q; k += blockDim.x) {
         double sum = 0.0;
         for (int i = i0; i < i1; ++i) sum += partial[static_cast<int64_t>(i) * Q + k];
         qh[static_cast<int64_t>(slot) * Q + k] = sum;
+        if (qh32) qh32[static_cast<int64_t>(slot) * Q + k] = __double2float_rn(sum);
     }
 }
 
@@ -176,7 +179,8 @@ __global__ void k_h_reduce(const double* __restrict__ partial, const int32_t* __
 
 void solve_device_hermite(Context* c, const double* x, const double* y, const double* z, const double* q,
                           int64_t n, const bltc_params& p, double* phi) {
-    require(p.precision == BLTC_PRECISION_FP64, "hermite: FP64 only");
+    require(p.precision == BLTC_PRECISION_FP64 || p.precision == BLTC_PRECISION_MIXED, "hermite: bad precision");
+    const bool mixed = p.precision == BLTC_PRECISION_MIXED;
     require(p.degree >= 1 && 2 * p.degree + 1 <= BLTC_MAX_DEGREE, "hermite: degree must be in [1, 7]");
     require(p.kernel == BLTC_KERNEL_COULOMB || p.kernel == BLTC_KERNEL_YUKAWA,
             "hermite: the Coulomb and Yukawa kernels only (derivatives are built in)");
@@ -207,6 +211,7 @@ void solve_device_hermite(Context* c, const double* x, const double* y, const do
     k_h_slots<<<grid_for(m, 256), 256, 0, s>>>(flag.p, pos.p, st.count.p, m, qslot.p, slot_node.p,
                                                slot_items.p); ++c->launches;
     DBuf<double> qh(c, static_cast<int64_t>(n_slots) * Q);
+    DBuf<float> qh32(c, mixed ? static_cast<int64_t>(n_slots) * Q : 0);
     if (n_slots > 0) {
         exclusive_scan_i32(c, slot_items.p, item0.p, n_slots, tot.p + 1);
         k_h_total<<<1, 1, 0, s>>>(item0.p, n_slots, tot.p + 1); ++c->launches;
@@ -221,11 +226,11 @@ void solve_device_hermite(Context* c, const double* x, const double* y, const do
         k_herm_partial<<<n_items, kHThreads, smem, s>>>(st.px.p, st.py.p, st.pz.p, st.pq.p, st.lo.p, st.hi.p,
                                                         c->cheb_table(p.degree), slot_node.p, items.p, np1,
                                                         partial.p); ++c->launches;
-        k_h_reduce<<<n_slots, 256, 0, s>>>(partial.p, item0.p, Q, qh.p); ++c->launches;
+        k_h_reduce<<<n_slots, 256, 0, s>>>(partial.p, item0.p, Q, qh.p, mixed ? qh32.p : nullptr); ++c->launches;
         BLTC_LAUNCH_CHECK("hermite charges");
     }
     c->mark(Context::kUpward);
-    evaluate_hermite(c, &L, bt, &st, p, qh.p, qslot.p, phi);
+    evaluate_hermite(c, &L, bt, &st, p, qh.p, mixed ? qh32.p : nullptr, qslot.p, phi);
 }
 
 }  // namespace bltc

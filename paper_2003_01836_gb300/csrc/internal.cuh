@@ -228,7 +228,7 @@ void prepare_plan(Context* ctx, Lists* L, int degree, int precision);
 int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision);
 // The Hermite treecode's sweep (sweep.cu) and the whole solve (hermite.cu).
 void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
-                      const double* qh, const int32_t* qslot, double* phi);
+                      const double* qh64, const float* qh32, const int32_t* qslot, double* phi);
 void solve_device_hermite(Context* c, const double* x, const double* y, const double* z, const double* q,
                           int64_t n, const bltc_params& p, double* phi);
 // The cluster-particle variant (cp.cu): targets interpolated, sources summed exactly.

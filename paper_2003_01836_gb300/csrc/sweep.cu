@@ -76,6 +76,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp64(SweepArgs a) {
 }
 
 template <int KER>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_hermite_mixed(SweepArgs a) {
+    sweep_mixed_body<KER, true>(a);
+}
+
+template <int KER>
 __global__ void __launch_bounds__(kThreads, 2) k_sweep_hermite(SweepArgs a) {
     sweep_hermite_body<KER>(a);
 }
@@ -575,31 +580,42 @@ void run_sweep(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const blt
     ctx->mark(Context::kEnd);
 }
 
-// The Hermite treecode's sweep (FP64): Hermite far field with charges qh [slot][8][(n+1)^3],
-// the plain near field, then the finalize.  The lists were built with degree 2n+1, whose
-// (2n+2)^3 = 8 (n+1)^3 points give the Hermite size test and the cost of an approximation.
+// The Hermite treecode's sweep: Hermite far field with charges [slot][8][(n+1)^3] (qh64 for
+// FP64, qh32 for mixed precision), the treecode's near field, then the finalize.  The lists
+// were built with degree 2n+1, whose (2n+2)^3 = 8 (n+1)^3 points give the Hermite size test
+// and the cost of an approximation.
 void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
-                      const double* qh, const int32_t* qslot, double* phi) {
+                      const double* qh64, const float* qh32, const int32_t* qslot, double* phi) {
     cudaStream_t s = ctx->stream;
     require(L->bt == bt && L->st == st, "hermite: lists were built for other trees");
     require(L->degree == 2 * p.degree + 1, "hermite: lists were built for another degree");
-    prepare_plan(ctx, L, L->degree, BLTC_PRECISION_FP64);
+    const bool mixed = p.precision == BLTC_PRECISION_MIXED;
+    prepare_plan(ctx, L, L->degree, p.precision);
     Plan& pl = L->plan;
     DBuf<double> partials(ctx, pl.partial_len);
+    DBuf<double> mpart(ctx, pl.mutual ? pl.mpart_len : 0);
     DBuf<unsigned int> counter(ctx, 1);
     BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
-    bltc_params pp = p;
-    pp.precision = BLTC_PRECISION_FP64;
-    SweepArgs a = make_args(ctx, L, bt, st, pp, partials.p, counter.p);
+    SweepArgs a = make_args(ctx, L, bt, st, p, partials.p, counter.p);
     a.np1 = p.degree + 1;
-    a.qhat64 = qh;
+    a.qhat64 = qh64;
+    a.qhat32 = qh32;
     a.qslot = qslot;
-    a.qhat32 = nullptr;
+    a.mpart = pl.mutual ? mpart.p : nullptr;
+    const int per_sm = mixed ? kMinBlocks : 2;
     const unsigned grid = static_cast<unsigned>(
-        std::min<int64_t>(pl.n_items, 2 * static_cast<int64_t>(std::max(1, ctx->sm_count))));
+        std::min<int64_t>(pl.n_items, per_sm * static_cast<int64_t>(std::max(1, ctx->sm_count))));
     ctx->mark(Context::kSweepBegin);
     if (pl.n_items > 0) {
-        if (p.kernel == BLTC_KERNEL_YUKAWA) {
+        if (mixed && p.kernel == BLTC_KERNEL_YUKAWA) {
+            BLTC_CUDA(cudaFuncSetAttribute(k_sweep_hermite_mixed<BLTC_KERNEL_YUKAWA>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+            k_sweep_hermite_mixed<BLTC_KERNEL_YUKAWA><<<grid, kThreads, kMixedSmem, s>>>(a); ++ctx->launches;
+        } else if (mixed) {
+            BLTC_CUDA(cudaFuncSetAttribute(k_sweep_hermite_mixed<BLTC_KERNEL_COULOMB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+            k_sweep_hermite_mixed<BLTC_KERNEL_COULOMB><<<grid, kThreads, kMixedSmem, s>>>(a); ++ctx->launches;
+        } else if (p.kernel == BLTC_KERNEL_YUKAWA) {
             k_sweep_hermite<BLTC_KERNEL_YUKAWA><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
         } else {
             k_sweep_hermite<BLTC_KERNEL_COULOMB><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
@@ -609,7 +625,7 @@ void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, co
     ctx->mark(Context::kSweepEnd);
     k_finalize<<<static_cast<unsigned>(L->n_batches), 256, 0, s>>>(
         bt->leaves.p, bt->begin.p, bt->count.p, bt->perm.p, pl.n_chunks.p, pl.part_off.p,
-        partials.p, L->dir_off.p, pl.dir_sel.p, nullptr, nullptr, phi); ++ctx->launches;
+        partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi); ++ctx->launches;
     BLTC_LAUNCH_CHECK("finalize hermite");
     ctx->mark(Context::kEnd);
 }

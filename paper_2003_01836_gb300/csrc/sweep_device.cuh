@@ -555,7 +555,103 @@ __device__ void far_mixed(const SweepArgs& a, int C, const double cb[3], const T
     }
 }
 
+// Far field of cluster C with barycentric Hermite charges, mixed precision.  With e = s - x
+// (the source point minus the target, batch-relative FP32) the mixed derivatives are
+// D^a G = (-1)^|a| prod_{a_l = 1} e_l G_|a|(r), so each charge row qhat^a is staged times
+// c_a = (-1)^|a| (1, 1, 1, 3, 1, 3, 3, 15)_a and the radial factors lose those constants:
+// Coulomb G_0 = 1/r, G_1 = 1/r^3, G_2 / 3 = 1/r^5, G_3 / 15 = 1/r^7; Yukawa multiplies them by
+// e^{-kr} (1, 1 + kr, 1 + kr + (kr)^2/3, 1 + kr + (2/5)(kr)^2 + (kr)^3/15).  The tensor grid
+// is walked as in far_mixed (e_x^2 + e_y^2 and e_x e_y per (k1, k2) row); runs of rows are
+// summed in FP32 and folded into the caller's TwoSum accumulator.
 template <int KER>
+__device__ void far_hermite_mixed(const SweepArgs& a, int C, const double cb[3], const Targets& tg,
+                                  float (&hi)[kT], float (&lo)[kT], float2* sm, int g, int G) {
+    const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1;
+    const float* qh = a.qhat32 + static_cast<int64_t>(a.qslot[C]) * 8 * P;
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * np1; k += kThreads) {
+        const int d = k / np1, kk = k - d * np1;
+        const double s = cheb_point(a.cheb_t, kk, n, a.s_lo[3 * C + d], a.s_hi[3 * C + d]);
+        const float v = __double2float_rn(s - (d == 0 ? cb[0] : (d == 1 ? cb[1] : cb[2])));
+        sm[k] = make_float2(v, v);
+    }
+    float2* sq = sm + 3 * np1;
+    for (int k = threadIdx.x; k < 8 * P; k += kThreads) {
+        const int c = k / P;
+        const float w = (c == 0) ? 1.f : (c == 7) ? -15.f : (c == 3 || c == 5 || c == 6) ? 3.f : -1.f;
+        const float v = w * qh[k];
+        sq[k] = make_float2(v, v);
+    }
+    __syncthreads();
+    const float2* sxp = sm;
+    const float2* syp = sm + np1;
+    const float2* szp = sm + 2 * np1;
+    const float2 nk = make_float2(a.neg_kappa_log2e, a.neg_kappa_log2e);
+    const float2 kp = make_float2(a.param32, a.param32);
+    const int R = np1 * np1, run = max(1, kBlock / (8 * np1)) * G;
+    int k1 = g / np1, k2 = g - k1 * np1;
+    for (int row0 = g; row0 < R; row0 += run) {
+        float2 f[kH];
+#pragma unroll
+        for (int v = 0; v < kH; ++v) f[v] = make_float2(0.f, 0.f);
+        for (int row = row0; row < min(R, row0 + run); row += G) {
+            const float2 sx = sxp[k1], sy = syp[k2];
+            float2 ex[kH], ey[kH], t[kH];
+#pragma unroll
+            for (int v = 0; v < kH; ++v) {
+                ex[v] = add2(sx, tg.x[v]);
+                ey[v] = add2(sy, tg.y[v]);
+                t[v] = fma2(ey[v], ey[v], mul2(ex[v], ex[v]));
+            }
+            const float2* qrow = sq + row * np1;
+            for (int k3 = 0; k3 < np1; ++k3) {
+                const float2 sz = szp[k3];
+                float2 q[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) q[c] = qrow[c * P + k3];
+#pragma unroll
+                for (int v = 0; v < kH; ++v) {
+                    const float2 ez = add2(sz, tg.z[v]);
+                    const float2 r2 = fma2(ez, ez, t[v]);
+                    float2 g0 = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                    const float2 ri2 = mul2(g0, g0);
+                    float2 g1 = mul2(g0, ri2), g2 = mul2(g1, ri2), g3 = mul2(g2, ri2);
+                    if (KER == BLTC_KERNEL_YUKAWA) {
+                        const float2 r = mul2(r2, g0);
+                        const float2 x = mul2(nk, r);
+                        const float2 e = make_float2(ex2_approx(x.x), ex2_approx(x.y));
+                        const float2 kr = mul2(kp, r);
+                        const float2 one = make_float2(1.f, 1.f);
+                        const float2 p1 = add2(one, kr);
+                        const float2 p2 = fma2(mul2(kr, kr), make_float2(1.f / 3.f, 1.f / 3.f), p1);
+                        const float2 p3 = fma2(mul2(kr, kr), fma2(kr, make_float2(1.f / 15.f, 1.f / 15.f),
+                                                                  make_float2(0.4f, 0.4f)), p1);
+                        g0 = mul2(g0, e);
+                        g1 = mul2(mul2(g1, e), p1);
+                        g2 = mul2(mul2(g2, e), p2);
+                        g3 = mul2(mul2(g3, e), p3);
+                    }
+                    const float2 s1 = fma2(ez, q[1], fma2(ey[v], q[2], mul2(ex[v], q[4])));
+                    const float2 exy = mul2(ex[v], ey[v]);
+                    const float2 s2 = fma2(ez, fma2(ey[v], q[3], mul2(ex[v], q[5])), mul2(exy, q[6]));
+                    const float2 s3 = mul2(mul2(exy, ez), q[7]);
+                    f[v] = fma2(g0, q[0], f[v]);
+                    f[v] = fma2(g1, s1, f[v]);
+                    f[v] = fma2(g2, s2, f[v]);
+                    f[v] = fma2(g3, s3, f[v]);
+                }
+            }
+            for (k2 += G; k2 >= np1; k2 -= np1) ++k1;
+        }
+#pragma unroll
+        for (int v = 0; v < kH; ++v) {
+            two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
+            two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
+        }
+    }
+}
+
+template <int KER, bool HERM = false>
 __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
     const int b = it.x;
     const int B = a.b_leaves[b];
@@ -590,8 +686,12 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
             float fh[kT], fl[kT];
 #pragma unroll
             for (int u = 0; u < kT; ++u) fh[u] = fl[u] = 0.f;
-            for (int e = it.y; e < min(it.z, na); ++e)
-                far_mixed<KER>(a, a.app_ids[a0 + e], cb, tg, fh, fl, reinterpret_cast<float2*>(sm), g, G);
+            for (int e = it.y; e < min(it.z, na); ++e) {
+                if constexpr (HERM)
+                    far_hermite_mixed<KER>(a, a.app_ids[a0 + e], cb, tg, fh, fl, reinterpret_cast<float2*>(sm), g, G);
+                else
+                    far_mixed<KER>(a, a.app_ids[a0 + e], cb, tg, fh, fl, reinterpret_cast<float2*>(sm), g, G);
+            }
 #pragma unroll
             for (int u = 0; u < kT; ++u) acc[u * kThreads] += static_cast<double>(fh[u]) + static_cast<double>(fl[u]);
         }
@@ -642,7 +742,7 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
 
 
 // The persistent mixed sweep: blocks pull (batch, list range) items from an atomic counter.
-template <int KER>
+template <int KER, bool HERM = false>
 __device__ __forceinline__ void sweep_mixed_body(const SweepArgs& a) {
     extern __shared__ __align__(16) float4 sm_dyn[];
     float4* sm = sm_dyn;
@@ -653,7 +753,7 @@ __device__ __forceinline__ void sweep_mixed_body(const SweepArgs& a) {
         __syncthreads();
         const int i = s_item;
         if (i >= a.n_items) return;
-        item_mixed<KER>(a, a.items[i], sm);
+        item_mixed<KER, HERM>(a, a.items[i], sm);
     }
 }
 

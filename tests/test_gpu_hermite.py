@@ -1,13 +1,14 @@
 """The barycentric Hermite treecode (future work of Sec. V) on the GPU: bltc_solve_hermite
 matches the oracle's algorithm element by element (FP64, 1e-12 of the absolute-value sum),
 including clusters with exact hits, ragged batches, batch != leaf and systems where no
-cluster passes the size test 8 (n+1)^3 < N_C; unsupported arguments are rejected."""
+cluster passes the size test 8 (n+1)^3 < N_C; the mixed-precision path is within the mixed
+bar (1e-6) of the FP64 path; unsupported arguments are rejected."""
 import numpy as np
 import pytest
 
 import oracle
 import paper_2003_01836_gb300 as b
-from gpu_helpers import FP64_ELEM, FP64_REL2, assert_close_abs, dev, host, system
+from gpu_helpers import FP64_ELEM, FP64_REL2, MIXED_ELEM, MIXED_REL2, assert_close_abs, dev, host, system
 
 pytestmark = pytest.mark.gpu
 
@@ -80,12 +81,31 @@ def test_hermite_is_more_accurate_than_the_treecode_at_equal_degree(gpu):
     assert oracle.rel_err(ref, herm) < oracle.rel_err(ref, host(lag))
 
 
-@pytest.mark.parametrize("bad", ["mixed", "degree", "kernel"])
+MIXED_CASES = [
+    # kind, N, leaf, batch, theta, n, kernel, kappa
+    ("cube", 30011, 700, 700, 0.7, 2, 0, 0.0),
+    ("plummer", 40000, 1000, 1000, 0.8, 3, 1, 0.5),
+    ("cube", 25000, 1200, 400, 0.6, 4, 0, 0.0),          # batch != leaf (no mutual pairs)
+    ("plummer", 60000, 5000, 5000, 0.9, 7, 1, 0.3),      # largest degree, Yukawa
+]
+
+
+@pytest.mark.parametrize("case", MIXED_CASES, ids=lambda c: f"{c[0]}{c[1]}-n{c[5]}-k{c[6]}-b{c[3]}")
+def test_hermite_mixed_vs_fp64(gpu, case):
+    kind, n, leaf, batch, theta, deg, ker, kappa = case
+    x, y, z, q = system(kind, n, 20031935 + n)
+    _, want_abs = oracle.bltc_hermite(x, y, z, q, theta, deg, leaf, batch, ker, kappa, with_abs=True)
+    got64 = _solve(gpu, x, y, z, q, b.params(deg, theta, leaf, batch, ker, kappa, b.BLTC_PRECISION_FP64))
+    gotmx = _solve(gpu, x, y, z, q, b.params(deg, theta, leaf, batch, ker, kappa, b.BLTC_PRECISION_MIXED))
+    assert_close_abs(got64, gotmx, want_abs, MIXED_REL2, MIXED_ELEM, "hermite mixed vs fp64")
+
+
+@pytest.mark.parametrize("bad", ["precision", "degree", "kernel"])
 def test_hermite_rejects(gpu, bad):
     x, y, z, q = system("cube", 2000, 20031934)
     p = b.params(3, 0.7, 200, 200, 0, 0.0, b.BLTC_PRECISION_FP64)
-    if bad == "mixed":
-        p.precision = b.BLTC_PRECISION_MIXED
+    if bad == "precision":
+        p.precision = 7
     elif bad == "degree":
         p.degree = 8
     else:
