@@ -437,3 +437,28 @@ def test_bltc_degenerate_systems(gpu):
     for prec in (b.BLTC_PRECISION_FP64, b.BLTC_PRECISION_MIXED):
         got = gpu_solve(gpu, x, x.copy(), x.copy(), q, b.params(4, 0.7, 100, precision=prec))
         assert np.all(got == 0.0)
+
+
+def test_empty_inputs_rejected(gpu):
+    """N < 1 is an argument error (BLTC_ERR_ARG) at every entry point, raised before any
+    device work; a non-empty set beside an empty one is rejected the same way."""
+    import torch
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    X = dev(*system("cube", 100, 3))
+    phi = torch.empty_like(X[0])
+    p = b.params(4, 0.7, 10, 10)
+    calls = [
+        lambda: b.bltc_solve(gpu.h, e, e, e, e, p, e),
+        lambda: b.bltc_solve_targets(gpu.h, e, e, e, *X, p, e),
+        lambda: b.bltc_solve_targets(gpu.h, *X[:3], e, e, e, e, p, phi),
+        lambda: b.bltc_solve_cp(gpu.h, e, e, e, *X, p, e),
+        lambda: b.bltc_solve_cc(gpu.h, *X[:3], e, e, e, e, p, phi),
+        lambda: b.bltc_solve_hermite(gpu.h, e, e, e, e, p, e),
+        lambda: b.bltc_direct_sum(gpu.h, e, e, e, *X, p, e),
+        lambda: b.bltc_graph_create(gpu.h, e, e, e, e, p, e),
+    ]
+    for i, call in enumerate(calls):
+        with pytest.raises(b.BltcError) as err:
+            call()
+        assert err.value.status == b.BLTC_ERR_ARG, i
+    torch.cuda.synchronize()
