@@ -169,6 +169,25 @@ class ClockSampler:
 
 # ---- the CPU oracle on a bounded sample ----------------------------------------------------
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def oracle_sample(x, y, z, q, w, budget_batches=None):
     """Algorithm 1 on the host cores: full trees and modified charges, ComputePotential on a
     sample of batches; time-to-solution extrapolated by target count."""
@@ -187,6 +206,7 @@ def oracle_sample(x, y, z, q, w, budget_batches=None):
     t_est = tm["setup"] + tm["precompute"] + tm["compute"] * (n / targets)
     # the sampled batches run one per thread: threads beyond the sample idle in the compute phase
     return {"targets_per_s": n / t_est, "t_est_s": t_est, "wall_s": wall, "cores": min(cores, len(pick)),
+            "cpu_model": cpu_model(),
             "sample": (f"full source/batch trees and modified charges of the {n}-particle "
                        f"system, ComputePotential on {len(pick)} of {nl} batches "
                        f"({targets} targets); time extrapolated by target count"),
@@ -308,7 +328,7 @@ def run_ours(args, dist: Dist):
         cb = oracle_sample(x, y, z, q, w)
         out["cpu_baseline"] = {"value": cb["targets_per_s"], "unit": "targets/s",
                                "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"],
-                               "t_est_s": cb["t_est_s"], "wall_s": cb["wall_s"]}
+                               "cpu_model": cb["cpu_model"], "t_est_s": cb["t_est_s"], "wall_s": cb["wall_s"]}
     ctx.close()
     return out
 
@@ -686,6 +706,7 @@ def run_reference(args, dist: Dist):
                        "n_particles": w["n"], "theta": w["theta"], "degree": w["degree"],
                        "leaf_size": w["leaf"], "batch_size": w["batch"]},
             "cpu_baseline": {"value": v, "unit": "targets/s", "cores": runs[0]["cores"],
+                             "cpu_model": runs[0]["cpu_model"],
                              "kind": "oracle", "sample": runs[0]["sample"]},
             "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
