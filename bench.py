@@ -188,15 +188,16 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def oracle_sample(x, y, z, q, w, budget_batches=None):
+def oracle_sample(x, y, z, q, w, budget_batches=None, threads=None):
     """Algorithm 1 on the host cores: full trees and modified charges, ComputePotential on a
     sample of batches; time-to-solution extrapolated by target count."""
     import oracle
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     st = oracle.Tree(x, y, z, w["leaf"])
     nl = len(st.leaves)
     k = budget_batches or max(2, min(nl, cores))
-    pick = np.unique(np.linspace(0, nl - 1, k).astype(np.int64))
+    pick = (np.array([nl // 2], dtype=np.int64) if k == 1
+            else np.unique(np.linspace(0, nl - 1, k).astype(np.int64)))
     targets = int(st.count[st.leaves[pick]].sum())
     t0 = time.perf_counter()
     _, _, tm = oracle.bltc(x, y, z, q, w["theta"], w["degree"], w["leaf"], w["batch"],
@@ -326,9 +327,13 @@ def run_ours(args, dist: Dist):
         out["e2e"] = run_e2e(ctx, b, x, y, z, q, p, args, dist, w)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(x, y, z, q, w)
+        one = oracle_sample(x, y, z, q, w, budget_batches=1, threads=1)
         out["cpu_baseline"] = {"value": cb["targets_per_s"], "unit": "targets/s",
                                "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"],
-                               "cpu_model": cb["cpu_model"], "t_est_s": cb["t_est_s"], "wall_s": cb["wall_s"]}
+                               "cpu_model": cb["cpu_model"], "t_est_s": cb["t_est_s"], "wall_s": cb["wall_s"],
+                               "single_thread": {"value": one["targets_per_s"], "cores": 1,
+                                                 "sample": one["sample"], "t_est_s": one["t_est_s"],
+                                                 "wall_s": one["wall_s"]}}
     ctx.close()
     return out
 
