@@ -12,12 +12,13 @@
  * Conventions, for every entry point unless its comment says otherwise:
  *   - Pointers named x, y, z, q, phi, tx, ... are DEVICE pointers owned by the caller
  *     (for example torch tensors' data_ptr()), FP64, contiguous, one value per particle in
- *     the caller's order.  The library never frees or keeps them past the call.
+ *     the caller's order.  The library never frees them and keeps them past the call only
+ *     where the entry point says so (bltc_graph_create binds q and phi to the graph).
  *   - Work is enqueued on the context's stream (bltc_context_set_stream) and may still be
  *     running when the call returns.  Calls whose comment says "synchronizes" wait for the
  *     stream before returning.  A call that needs a count computed on the device (tree
  *     build, list build, evaluate, solve) synchronizes the stream internally.
- *   - Handles (bltc_tree, bltc_lists) own their device memory, allocated through the
+ *   - Handles (bltc_tree, bltc_lists, bltc_graph) own their device memory, allocated through the
  *     context's allocator; only the matching *_destroy frees it.  A handle must not
  *     outlive its context.
  *   - Every call returns a bltc_status; on failure nothing observable was written to the
