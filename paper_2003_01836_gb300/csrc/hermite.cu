@@ -1,4 +1,4 @@
-// hermite.cu -- the barycentric Hermite treecode (future work of Sec. V), FP64.
+// hermite.cu -- the barycentric Hermite treecode (future work of Sec. V), FP64 or mixed precision.
 //
 // Reading (the paper names the method without defining it): on the n+1 Chebyshev points of
 // Eq. 6 a cluster's kernel is interpolated with values and first derivatives, the classical
