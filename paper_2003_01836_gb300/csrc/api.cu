@@ -54,6 +54,21 @@ void Context::dfree(void* p, size_t bytes) {
     cudaFreeAsync(p, stream);
 }
 
+void Context::fork() {
+    if (!side) {
+        BLTC_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        BLTC_CUDA(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+        BLTC_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+    }
+    BLTC_CUDA(cudaEventRecord(fork_ev, stream));
+    BLTC_CUDA(cudaStreamWaitEvent(side, fork_ev, 0));
+}
+
+void Context::join() {
+    BLTC_CUDA(cudaEventRecord(join_ev, side));
+    BLTC_CUDA(cudaStreamWaitEvent(stream, join_ev, 0));
+}
+
 const int64_t* Context::read_words(const void* dev, int words) {
     if (words > kPinnedWords) throw Error(BLTC_ERR_ARG, "read_words: too many words");
     BLTC_CUDA(cudaMemcpyAsync(pinned, dev, sizeof(int64_t) * words, cudaMemcpyDeviceToHost, stream));
@@ -115,6 +130,34 @@ static bltc_status guarded(bltc_context* ctx, F&& f) {
     }
 }
 
+// The upward pass (Eq. 12) and the sweep's work plan both follow the lists and are
+// independent: the pass's kernels run on the side stream while the plan, whose steps wait on
+// device counts, is built on the main stream.  The pass's scratch is freed on the main stream
+// after the join, so no buffer is reused while the side stream may still read it.
+static void upward_beside_plan(Context* c, Tree* st, Lists* L, const bltc_params& p) {
+    UpwardPlan up;
+    prepare_upward(c, st, L, p.degree, p.precision, &up);
+    c->mark(Context::kUpward);
+    c->fork();
+    cudaStream_t main_stream = c->stream;
+    c->stream = c->side;
+    try {
+        run_upward(c, st, up);
+    } catch (...) {
+        c->stream = main_stream;
+        c->join();
+        throw;
+    }
+    c->stream = main_stream;
+    try {
+        prepare_plan(c, L, p.degree, p.precision);
+    } catch (...) {
+        c->join();
+        throw;
+    }
+    c->join();
+}
+
 static void solve_device(Context* c, const double* x, const double* y, const double* z,
                          const double* q, int64_t n, const bltc_params& p, double* phi) {
     c->mark(Context::kStart);
@@ -131,8 +174,7 @@ static void solve_device(Context* c, const double* x, const double* y, const dou
     Lists L;
     build_lists(c, bt, &st, p.theta, p.degree, &L);
     c->mark(Context::kLists);
-    compute_modified_charges(c, &st, &L, p.degree, p.precision);
-    c->mark(Context::kUpward);
+    upward_beside_plan(c, &st, &L, p);
     evaluate(c, &L, bt, &st, p, phi);
 }
 
@@ -149,8 +191,7 @@ static void solve_device_targets(Context* c, const double* tx, const double* ty,
     Lists L;
     build_lists(c, &bt, &st, p.theta, p.degree, &L);
     c->mark(Context::kLists);
-    compute_modified_charges(c, &st, &L, p.degree, p.precision);
-    c->mark(Context::kUpward);
+    upward_beside_plan(c, &st, &L, p);
     evaluate(c, &L, &bt, &st, p, phi);
 }
 
@@ -219,6 +260,12 @@ void bltc_context_destroy(bltc_context* ctx) {
         if (e) cudaEventDestroy(e);
     for (Context::UserKernel& k : c.user_kernels)
         if (k.lib) cudaLibraryUnload(k.lib);
+    if (c.side) {
+        cudaStreamSynchronize(c.side);
+        cudaStreamDestroy(c.side);
+    }
+    if (c.fork_ev) cudaEventDestroy(c.fork_ev);
+    if (c.join_ev) cudaEventDestroy(c.join_ev);
     if (c.pinned) cudaFreeHost(c.pinned);
     if (c.pool) cudaMemPoolDestroy(c.pool);
     delete ctx;

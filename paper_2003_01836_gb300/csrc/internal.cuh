@@ -52,6 +52,13 @@ struct Context {
     static constexpr int kPinnedWords = 64;
     int64_t launches = 0;                       // kernels launched through this context
     bool capturing = false;                     // inside a graph capture: no allocation allowed
+    // A second stream for work that overlaps the host-synchronising setup of the main stream
+    // (created on first use): fork() makes it wait for the main stream's work so far, join()
+    // makes the main stream wait for it.
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    void fork();
+    void join();
     uint64_t next_serial = 1;
     // Optional phase timing: CUDA events recorded on the stream at the phase boundaries.
     enum Mark { kStart, kTrees, kLists, kUpward, kSweepBegin, kSweepEnd, kEnd, kMarks };
