@@ -285,33 +285,76 @@ __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* 
                            const double* __restrict__ partials, const int32_t* __restrict__ dir_off,
                            const uint8_t* __restrict__ dir_sel, const int64_t* __restrict__ dir_moff,
                            const double* __restrict__ mpart, double* __restrict__ phi) {
-    constexpr int U = 8;
+    constexpr int U = 8;          // targets per thread
+    constexpr int kRows = 256;    // row pointers gathered per round
+    constexpr int kAhead = 4;     // rows loaded before they are added
+    __shared__ const double* s_row[kRows];
+    __shared__ int s_n;
+    __shared__ bool s_more;
     const int b = blockIdx.x;
     const int B = b_leaves[b];
     const int tb = b_begin[B], nb = b_count[B], K = n_chunks[b];
     const double* p = partials + part_off[b];
+    const int e1 = dir_off[b + 1];
+    const int lane = static_cast<int>(threadIdx.x) & 31;
     for (int t0 = 0; t0 < nb; t0 += U * static_cast<int>(blockDim.x)) {
         double s[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) s[u] = 0.0;
-        for (int c = 0; c < K; ++c) {
-            const double* row = p + static_cast<int64_t>(c) * nb;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
-                if (t < nb) s[u] += row[t];
+        // The rows are added in a fixed order: the item partials, then (mutual pairs) the partner
+        // rows of the skipped entries in list order.  Warp 0 gathers their addresses in rounds
+        // (its own progress in r0 and e); every thread then loads kAhead rows before adding them.
+        int r0 = 0, e = dir_off[b];
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                int n = 0;
+                for (; r0 < K && n < kRows; ++r0, ++n)
+                    if (lane == 0) s_row[n] = p + static_cast<int64_t>(r0) * nb;
+                if (mpart && r0 >= K) {
+                    while (e < e1 && n <= kRows - 32) {
+                        const int ee = e + lane;
+                        const bool skip = ee < e1 && (dir_sel[ee] & kSelSkip);
+                        const unsigned v = __ballot_sync(0xffffffffu, skip);
+                        if (skip) s_row[n + __popc(v & ((1u << lane) - 1u))] = mpart + dir_moff[ee];
+                        n += __popc(v);
+                        e += 32;
+                    }
+                }
+                if (lane == 0) {
+                    s_n = n;
+                    s_more = r0 < K || (mpart != nullptr && e < e1);
+                }
             }
-        }
-        if (mpart) {
-            for (int e = dir_off[b]; e < dir_off[b + 1]; ++e) {
-                if (!(dir_sel[e] & kSelSkip)) continue;
-                const double* row = mpart + dir_moff[e];
+            __syncthreads();
+            const int n = s_n;
+            const bool more = s_more;
+            int r = 0;
+            for (; r + kAhead <= n; r += kAhead) {
+                double v[kAhead][U];
+#pragma unroll
+                for (int k = 0; k < kAhead; ++k) {
+                    const double* row = s_row[r + k];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
+                        v[k][u] = t < nb ? row[t] : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kAhead; ++k)
+#pragma unroll
+                    for (int u = 0; u < U; ++u) s[u] += v[k][u];
+            }
+            for (; r < n; ++r) {
+                const double* row = s_row[r];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
                     if (t < nb) s[u] += row[t];
                 }
             }
+            if (!more) break;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
