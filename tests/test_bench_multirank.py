@@ -51,3 +51,20 @@ def test_single_process_aggregate():
     assert d.world == 1 and d.pg is None
     agg = bench.aggregate(20.0, 500, d)
     assert agg["targets_per_s"] == pytest.approx(500 / 0.02)
+
+
+def test_reference_arm_line(capsys):
+    """`bench.py --impl reference` on CPU: one JSON line with the contract's keys, the oracle
+    timed on a bounded sample (a small system here), no device traffic in its e2e."""
+    import json
+
+    import bench
+    bench.main(["--impl", "reference", "--n", "20000", "--steps", "1", "--warmup", "3"])
+    line = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")][-1]
+    d = json.loads(line)
+    assert d["impl"] == "reference" and d["unit"] == "targets/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert isinstance(cb["cpu_model"], str) and cb["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
