@@ -31,6 +31,11 @@ MUTANTS = [
     ("mac_ignores_size", "int size_ok = c->P < c->st->count[C];", "int size_ok = 1;"),
     # cluster-particle variant
     ("cp_point_potential_axes", "s1[k1], s2[k2], s3[k3], sx[j], sy[j],", "s1[k1], s2[k3], s3[k2], sx[j], sy[j],"),
+    # cluster-cluster variant
+    ("cc_source_grid_axes", "t1[k1], t2[k2], t3[k3], s1[m1],\n                                                  s2[m2], s3[m3], &g))",
+     "t1[k1], t2[k2], t3[k3], s1[m1],\n                                                  s3[m3], s2[m2], &g))"),
+    ("cc_cp_target_grid_axes", "t1[k1], t2[k2], t3[k3], sx[j], sy[j],\n                                          sz[j], &g))",
+     "t1[k1], t3[k3], t2[k2], sx[j], sy[j],\n                                          sz[j], &g))"),
     # barycentric Hermite treecode
     ("hermite_H_sign", "h[j] = (1.0 - 2.0 * dl * (y - s[j])) * l2;", "h[j] = (1.0 + 2.0 * dl * (y - s[j])) * l2;"),
     ("hermite_K_dropped", "k[j] = (y - s[j]) * l2;", "k[j] = 0.0 * l2;"),
