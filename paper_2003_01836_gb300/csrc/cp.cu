@@ -577,7 +577,8 @@ struct DualArgs {
 
 enum { kCC = 0, kCP = 1, kPC = 2, kPP = 3, kSplitT = 4, kSplitS = 5 };
 
-// One frontier pair's decision (FP64 with explicit rounding, in the oracle's order).
+// One frontier pair's decision: Eq. 13's geometric test, then the size tests, then the split rule
+// of the dual traversal (FP64 with explicit rounding, evaluated left to right).
 __device__ __forceinline__ int dual_decide(const DualArgs& a, int T, int S) {
     const double dx = __dsub_rn(a.t_center[3 * T], a.s_center[3 * S]);
     const double dy = __dsub_rn(a.t_center[3 * T + 1], a.s_center[3 * S + 1]);
