@@ -680,3 +680,14 @@ def test_hermite_treecode_theta0_polynomial_and_decay():
     assert eh[0] > eh[1] > eh[2], eh
     el = oracle.rel_err(ref2, oracle.bltc(x2, y2, z2, q2, 0.7, 3, 200, 200)[0])
     assert eh[2] < el, (eh, el)
+
+
+def test_hermite_factors_n1_are_the_cubic_hermite_basis():
+    # n = 1 on [0, 1]: points s_0 = 1, s_1 = 0 and the textbook cubic Hermite basis
+    # H_0 = (3 - 2y) y^2, K_0 = (y - 1) y^2, H_1 = (1 + 2y)(1 - y)^2, K_1 = y (1 - y)^2
+    for yv in (0.25, 0.5, 0.875):
+        h, k = oracle.hermite_factors(1, 0.0, 1.0, yv)
+        want_h = [(3 - 2 * yv) * yv * yv, (1 + 2 * yv) * (1 - yv) ** 2]
+        want_k = [(yv - 1) * yv * yv, yv * (1 - yv) ** 2]
+        assert np.allclose(h, want_h, rtol=0, atol=1e-15), (yv, h, want_h)
+        assert np.allclose(k, want_k, rtol=0, atol=1e-15), (yv, k, want_k)
