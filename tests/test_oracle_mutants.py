@@ -13,7 +13,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "bltc_oracle.c")
 
-# (name, text in the source, replacement): one mistake each.
+# (name, text in the source, replacement[, occurrence, occurrences]): one mistake each.  An
+# anchor that occurs more than once names which occurrence is replaced and how many there are.
 MUTANTS = [
     ("dropped_dz_term", "double r2 = dx * dx + dy * dy + dz * dz;", "double r2 = dx * dx + dy * dy;"),
     ("yukawa_sign", "exp(-kappa * r) / r", "exp(kappa * r) / r"),
@@ -42,6 +43,39 @@ MUTANTS = [
     ("hermite_G2_yukawa_term", "g[2] = e * (3.0 + 3.0 * kr + kr * kr)", "g[2] = e * (3.0 + 2.0 * kr + kr * kr)"),
     ("hermite_derivative_axis", "if (a & 4) p = p * d[0];", "if (a & 4) p = p * d[2];"),
     ("hermite_charge_axis", "const double* f1 = (a & 4) ? kk[0] : h[0];", "const double* f1 = (a & 1) ? kk[0] : h[0];"),
+    # absolute-value sums (the scale of the per-target parity bars)
+    ("direct_sum_abs_of_g_only",
+     "            acc_abs = acc_abs + fabs(g * sq[j]);\n        }\n        phi[i] = acc;",
+     "            acc_abs = acc_abs + fabs(g) * sq[j];\n        }\n        phi[i] = acc;"),
+    ("direct_sum_abs_doubled",
+     "            acc_abs = acc_abs + fabs(g * sq[j]);\n        }\n        phi[i] = acc;",
+     "            acc_abs = acc_abs + 2.0 * fabs(g * sq[j]);\n        }\n        phi[i] = acc;"),
+    ("far_field_abs_dropped",
+     "                    acc_abs = acc_abs + fabs(term);\n                }\n        c->phi[t] = acc;",
+     "                    acc_abs = acc_abs + 0.0 * fabs(term);\n                }\n        c->phi[t] = acc;"),
+    ("near_field_abs_signed",
+     "            double term = g * c->sq[j];\n            acc = acc + term;\n            acc_abs = acc_abs + fabs(term);",
+     "            double term = g * c->sq[j];\n            acc = acc + term;\n            acc_abs = acc_abs + term;"),
+    ("cp_near_abs_signed",
+     "                acc_abs = acc_abs + fabs(g * sq[j]);\n            }\n        }\n        int64_t chain[128];",
+     "                acc_abs = acc_abs + g * sq[j];\n            }\n        }\n        int64_t chain[128];"),
+    ("cp_point_abs_signed", "phat_abs[T * P + (k1 * n1 + k2) * n1 + k3] = acc_abs;",
+     "phat_abs[T * P + (k1 * n1 + k2) * n1 + k3] = acc;", 0, 2),
+    ("cp_interpolant_abs_signed", "acc_abs = acc_abs + fabs(l) * phat_abs[T * P + k];",
+     "acc_abs = acc_abs + l * phat_abs[T * P + k];", 0, 2),
+    ("cc_point_abs_signed", "phat_abs[T * P + (k1 * n1 + k2) * n1 + k3] = acc_abs;",
+     "phat_abs[T * P + (k1 * n1 + k2) * n1 + k3] = acc;", 1, 2),
+    ("cc_interpolant_abs_dropped", "acc_abs = acc_abs + fabs(l) * phat_abs[T * P + k];",
+     "acc_abs = acc_abs + 0.0 * phat_abs[T * P + k];", 1, 2),
+    ("cc_pc_abs_dropped",
+     "                            acc_abs = acc_abs + fabs(term);\n                        }\n            }\n            for (int64_t e = off[3][T]",
+     "                            acc_abs = acc_abs + 0.0 * fabs(term);\n                        }\n            }\n            for (int64_t e = off[3][T]"),
+    ("hermite_far_abs_dropped",
+     "                            acc_abs = acc_abs + fabs(term);\n                        }\n                    }\n            c->phi[t] = acc;",
+     "                            acc_abs = acc_abs + 0.0 * fabs(term);\n                        }\n                    }\n            c->phi[t] = acc;"),
+    ("hermite_near_abs_signed",
+     "                const double term = dg[0] * c->q[j];\n                acc = acc + term;\n                acc_abs = acc_abs + fabs(term);",
+     "                const double term = dg[0] * c->q[j];\n                acc = acc + term;\n                acc_abs = acc_abs + term;"),
 ]
 
 FAST = "not decays and not band and not degenerates"
@@ -66,9 +100,15 @@ def test_unmodified_copy_passes(tmp_path):
         assert _run_pins(tmp_path, f.read()) == 0
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_mutant_is_caught(tmp_path, name, old, new):
+@pytest.mark.parametrize("mutant", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, mutant):
+    name, old, new = mutant[:3]
+    which, count = mutant[3:] if len(mutant) > 3 else (0, 1)
     with open(SRC) as f:
         text = f.read()
-    assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
-    assert _run_pins(tmp_path, text.replace(old, new)) != 0, f"pins missed mutant {name}"
+    assert text.count(old) == count, f"mutation anchor for {name} not found {count} time(s)"
+    at = -1
+    for _ in range(which + 1):
+        at = text.index(old, at + 1)
+    mutated = text[:at] + new + text[at + len(old):]
+    assert _run_pins(tmp_path, mutated) != 0, f"pins missed mutant {name}"

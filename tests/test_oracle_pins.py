@@ -219,6 +219,16 @@ def test_lagrange_reproduces_polynomials(n):
     assert abs(a @ (s ** (n + 1)) - yv ** (n + 1)) > 1e-10
 
 
+def test_lagrange_factors_stay_below_1_031():
+    # On Chebyshev points of the second kind no Lagrange factor exceeds 1.031 in magnitude for
+    # n <= 16 (it reaches 1 at its own node); the mixed modified-charge bar of the GPU tests
+    # bounds each term by |q| max|L|^3 with this constant.
+    ys = np.linspace(-1.0, 1.0, 8001)
+    for n in (1, 2, 4, 8, 12, 16):
+        m = max(np.abs(oracle.lagrange(n, -1.0, 1.0, yv)).max() for yv in ys)
+        assert 1.0 <= m < 1.031, (n, m)
+
+
 def test_lagrange_matches_scipy_barycentric():
     scipy_interp = pytest.importorskip("scipy.interpolate")
     n, lo, hi = 9, 0.2, 1.7
@@ -691,3 +701,184 @@ def test_hermite_factors_n1_are_the_cubic_hermite_basis():
         want_k = [(yv - 1) * yv * yv, yv * (1 - yv) ** 2]
         assert np.allclose(h, want_h, rtol=0, atol=1e-15), (yv, h, want_h)
         assert np.allclose(k, want_k, rtol=0, atol=1e-15), (yv, k, want_k)
+
+
+# ---------------------------------------------------------------------------------------
+# Absolute-value sums sum_j |G(x_i, y_j) q_j| over the terms each path adds (the scale of
+# every per-target parity bar of the GPU tests)
+# ---------------------------------------------------------------------------------------
+
+def test_direct_abs_sum_closed_forms():
+    # two charges of opposite sign at distance 0.5: each sees |q_other| / d (Eq. 1-2)
+    pts = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.5]]).T
+    q = np.array([0.75, -0.25])
+    phi, phi_abs = oracle.direct_sum(pts, pts, q, with_abs=True)
+    assert phi.tolist() == [-0.5, 1.5] and phi_abs.tolist() == [0.5, 1.5]
+    kappa = 0.5
+    _, phi_abs = oracle.direct_sum(pts, pts, q, oracle.KERNEL_YUKAWA, kappa, with_abs=True)
+    e = math.exp(-kappa * 0.5) / 0.5
+    assert phi_abs[0] == pytest.approx(0.25 * e, rel=1e-15)
+    assert phi_abs[1] == pytest.approx(0.75 * e, rel=1e-15)
+    # 5-12-13 triangle with charges of both signs: exact rationals
+    pts = np.array([[0, 0, 0], [3, 4, 0], [3, 4, 12]], dtype=np.float64).T
+    phi, phi_abs = oracle.direct_sum(pts, pts, np.array([1.0, -2.0, 3.0]), with_abs=True)
+    want = [Fraction(2, 5) + Fraction(3, 13), Fraction(1, 5) + Fraction(3, 12),
+            Fraction(1, 13) + Fraction(2, 12)]
+    want_phi = [-Fraction(2, 5) + Fraction(3, 13), Fraction(1, 5) + Fraction(3, 12),
+                Fraction(1, 13) - Fraction(2, 12)]
+    for p, pa, w, wp in zip(phi, phi_abs, want, want_phi):
+        assert abs(Fraction(pa) - w) <= Fraction(1, 2 ** 50)
+        assert abs(Fraction(p) - wp) <= Fraction(1, 2 ** 50)
+    # cube corners with checkerboard charges: every corner has 3 neighbours of the other
+    # sign at a, 3 of its own sign at a sqrt2 and 1 of the other sign at a sqrt3
+    a = 0.75
+    pts = np.array([[a * i, a * j, a * k] for i in (0, 1) for j in (0, 1) for k in (0, 1)]).T
+    q = np.array([(-1.0) ** (i + j + k) for i in (0, 1) for j in (0, 1) for k in (0, 1)])
+    phi, phi_abs = oracle.direct_sum(pts, pts, q, with_abs=True)
+    np.testing.assert_allclose(phi_abs, 3 / a + 3 / (a * math.sqrt(2)) + 1 / (a * math.sqrt(3)),
+                               rtol=2e-16 * 8)
+    np.testing.assert_allclose(phi * q, -3 / a + 3 / (a * math.sqrt(2)) - 1 / (a * math.sqrt(3)),
+                               rtol=2e-16 * 16)
+
+
+def test_abs_sums_at_theta_zero_equal_the_direct_sums():
+    # theta = 0: every path is the direct sum (no cluster passes the MAC), so the absolute
+    # sums hold the same positive terms in another order; with positive charges every term
+    # is positive and the absolute sum is the potential itself, bit for bit
+    x, y, z, q = _system(3000, 20031893)
+    pts = np.stack([x, y, z])
+    _, ref_abs = oracle.direct_sum(pts, pts, q, with_abs=True)
+    got = {"bltc": oracle.bltc(x, y, z, q, 0.0, 4, 200, 200, with_abs=True)[1],
+           "ts": oracle.bltc_ts((x, y, z), (x, y, z), q, 0.0, 4, 200, 150, with_abs=True)[1],
+           "cp": oracle.bltc_cp((x, y, z), (x, y, z), q, 0.0, 4, 200, 150, with_abs=True)[1],
+           "cc": oracle.bltc_cc((x, y, z), (x, y, z), q, 0.0, 4, 200, 150, with_abs=True)[1],
+           "hermite": oracle.bltc_hermite(x, y, z, q, 0.0, 2, 200, 200, with_abs=True)[1]}
+    # two orders of a sum of 3000 positive terms differ by at most 2 * 3000 * 2^-53 relative
+    for name, pa in got.items():
+        assert np.max(np.abs(pa - ref_abs) / ref_abs) < 1e-12, name
+    qp = np.abs(q)
+    phi, phi_abs = oracle.direct_sum(pts, pts, qp, with_abs=True)
+    assert np.array_equal(phi, phi_abs)
+    phi, phi_abs, _ = oracle.bltc(x, y, z, qp, 0.0, 4, 200, 200, with_abs=True)
+    assert np.array_equal(phi, phi_abs)
+
+
+def _corner_clusters(per_corner, seed=20031895, degree=1):
+    """Four clusters in opposite corners of [-1, 1]^3, each with `per_corner` particles on
+    each of its (degree+1)^3 interpolation points and one charge sign per point.  The boxes
+    are the minimal ones; at degree 1 their Chebyshev points are the box corners (s_0 = hi,
+    s_1 = lo), at degree 2 also the box midpoints (cos(pi/2) + 1 rounds to 1, so s_1 =
+    lo + (hi - lo)/2, exact for these boxes of width 1/4).  Every particle is an exact hit
+    (Sec. II-C): a modified charge is the sum of the charges at its point, one sign, and
+    each far-field term G(x, s_k) qhat_k equals the direct terms of those particles,
+    absolute values included."""
+    rng = np.random.default_rng(seed)
+    X, Q = [], []
+    for c in ((-1, -1, -1), (1, 1, 1), (-1, 1, -1), (1, -1, 1)):
+        lo = [0.75 if ci > 0 else -1.0 for ci in c]
+        hi = [1.0 if ci > 0 else -0.75 for ci in c]
+        axes = [[lo[d], hi[d]] if degree == 1 else [lo[d], lo[d] + 0.125, hi[d]]
+                for d in range(3)]
+        for point in np.ndindex(*([degree + 1] * 3)):
+            sign = 1.0 if rng.random() < 0.5 else -1.0
+            for _ in range(per_corner):
+                X.append([axes[d][point[d]] for d in range(3)])
+                Q.append(sign * rng.uniform(0.25, 1.0))
+    order = rng.permutation(len(Q))
+    X = np.array(X)[order]
+    return X[:, 0].copy(), X[:, 1].copy(), X[:, 2].copy(), np.array(Q)[order]
+
+
+def _assert_matches_direct(phi, phi_abs, ref, ref_abs, what):
+    # sums of at most a few hundred terms in another order and grouping
+    assert np.max(np.abs(phi - ref) / ref_abs) < 1e-13, what
+    assert np.max(np.abs(phi_abs - ref_abs) / ref_abs) < 1e-13, what
+
+
+def test_abs_sums_of_exact_far_fields_equal_the_direct_sums():
+    # with the particles on their clusters' interpolation points the far fields are exact,
+    # so every path's potential AND absolute sum equal the direct sum's, while clusters are
+    # approximated (theta 0.5 passes every pair of the four clusters)
+    x, y, z, q = _corner_clusters(2)
+    pts = np.stack([x, y, z])
+    ref, ref_abs = oracle.direct_sum(pts, pts, q, with_abs=True)
+    st = oracle.Tree(x, y, z, 16)
+    assert len(st.leaves) == 4 and len(oracle.lists(st, st, 0.5, 1)["approx_ids"]) == 12
+    phi, phi_abs, _ = oracle.bltc(x, y, z, q, 0.5, 1, 16, 16, with_abs=True)
+    _assert_matches_direct(phi, phi_abs, ref, ref_abs, "bltc")
+    phi, phi_abs = oracle.bltc_cp((x, y, z), (x, y, z), q, 0.5, 1, 16, 16, with_abs=True)
+    _assert_matches_direct(phi, phi_abs, ref, ref_abs, "cp")
+    phi, phi_abs = oracle.bltc_cc((x, y, z), (x, y, z), q, 0.5, 1, 16, 16, with_abs=True)
+    _assert_matches_direct(phi, phi_abs, ref, ref_abs, "cc")
+    assert len(oracle.dual_lists(st, st, 0.5, 1)["cc"][0]) > 0
+    # distinct targets scattered through the cube: the batches near a cluster sum it
+    # directly, the far ones approximate it
+    tx, ty, tz, _ = inputs.uniform_cube(400, 20031897)
+    tp = np.stack([tx, ty, tz])
+    ref, ref_abs = oracle.direct_sum(tp, pts, q, with_abs=True)
+    phi, phi_abs, _ = oracle.bltc_ts((tx, ty, tz), (x, y, z), q, 0.5, 1, 16, 25, with_abs=True)
+    _assert_matches_direct(phi, phi_abs, ref, ref_abs, "ts")
+    L = oracle.lists(oracle.Tree(tx, ty, tz, 25), st, 0.5, 1)
+    assert len(L["approx_ids"]) > 0 and len(L["direct_ids"]) > 0
+    # Hermite: the size test is 8 (n+1)^3 = 64 < N_C; at a node H = e_m and K = 0, so only
+    # the value charges are nonzero and the far field is again the direct sum term by term
+    x, y, z, q = _corner_clusters(9, 20031899)
+    pts = np.stack([x, y, z])
+    ref, ref_abs = oracle.direct_sum(pts, pts, q, with_abs=True)
+    st = oracle.Tree(x, y, z, 72)
+    assert len(oracle.lists(st, st, 0.5, 3)["approx_ids"]) == 12
+    phi, phi_abs = oracle.bltc_hermite(x, y, z, q, 0.5, 1, 72, 72, with_abs=True)
+    _assert_matches_direct(phi, phi_abs, ref, ref_abs, "hermite")
+
+
+def _lagrange_basis(nodes, x):
+    """L_k(x) = prod_{m != k} (x - s_m) / (s_k - s_m): Eq. 4's definition, term by term."""
+    out = np.ones(len(nodes))
+    for k in range(len(nodes)):
+        for m in range(len(nodes)):
+            if m != k:
+                out[k] *= (x - nodes[m]) / (nodes[k] - nodes[m])
+    return out
+
+
+def test_abs_sums_of_interpolated_targets():
+    # Targets far from four on-grid source clusters, a kernel of degree n = 2 in every
+    # coordinate (non-negative for even n): the cluster-particle and cluster-cluster
+    # variants interpolate the point potentials of the one target cluster exactly, and
+    # their absolute sums are sum_k |L_k1(x) L_k2(x) L_k3(x)| psi(t_k) with
+    # psi(t) = sum_j G(t, y_j) |q_j| at the target box's Chebyshev points t_k.  The
+    # Lagrange factors here come from Eq. 4's product form, psi from the direct sum.
+    n = 2
+    sx, sy, sz, q = _corner_clusters(2, 20031901, degree=n)
+    tx, ty, tz, _ = inputs.uniform_cube(300, 20031903)
+    tx, ty, tz = 3.15 + 0.15 * tx, 0.15 * ty, 0.15 * tz
+    T, S = (tx, ty, tz), (sx, sy, sz)
+    ref, ref_abs = oracle.direct_sum(np.stack(T), np.stack(S), q, oracle.KERNEL_POLY, 0.0, n,
+                                     with_abs=True)
+    grids = [oracle.cheb(n, a.min(), a.max())[0] for a in T]
+    g = np.array([[u, v, w] for u in grids[0] for v in grids[1] for w in grids[2]]).T
+    psi = oracle.direct_sum(g, np.stack(S), np.abs(q), oracle.KERNEL_POLY, 0.0, n)
+    want_abs = np.array([np.sum(np.abs(np.einsum("a,b,c->abc", *[_lagrange_basis(grids[d], p[d])
+                                                                 for d in range(3)])).ravel() * psi)
+                         for p in zip(tx, ty, tz)])
+    assert np.all(want_abs > ref_abs * (1 + 1e-6))      # some factors are negative off the nodes
+    tt, st = oracle.Tree(tx, ty, tz, 50), oracle.Tree(sx, sy, sz, 54)
+    assert len(oracle.lists(st, tt, 0.5, n)["approx_ids"]) == 4
+    assert len(oracle.dual_lists(tt, st, 0.5, n)["cc"][0]) > 0
+    for name, fn in (("cp", oracle.bltc_cp), ("cc", oracle.bltc_cc)):
+        lb = (50, 54) if name == "cp" else (54, 50)
+        phi, phi_abs = fn(T, S, q, 0.5, n, *lb, oracle.KERNEL_POLY, with_abs=True)
+        assert np.max(np.abs(phi - ref) / ref_abs) < 1e-13, name
+        assert np.max(np.abs(phi_abs - want_abs) / want_abs) < 1e-13, name
+    # the treecode approximates the source clusters (exactly, on their nodes) instead
+    phi, phi_abs, _ = oracle.bltc_ts(T, S, q, 0.5, n, 54, 50, oracle.KERNEL_POLY, with_abs=True)
+    _assert_matches_direct(phi, phi_abs, ref, ref_abs, "ts")
+    # 20 far targets form one leaf too small to interpolate ((n+1)^3 = 27 points): the
+    # dual traversal pairs it with the source clusters as particle-cluster (PC) terms,
+    # exact on the source nodes, absolute values included
+    T20 = tuple(a[:20].copy() for a in T)
+    ref, ref_abs = oracle.direct_sum(np.stack(T20), np.stack(S), q, oracle.KERNEL_POLY, 0.0, n,
+                                     with_abs=True)
+    assert len(oracle.dual_lists(oracle.Tree(*T20, 50), st, 0.5, n)["pc"][0]) == 4
+    phi, phi_abs = oracle.bltc_cc(T20, S, q, 0.5, n, 54, 50, oracle.KERNEL_POLY, with_abs=True)
+    _assert_matches_direct(phi, phi_abs, ref, ref_abs, "cc particle-cluster")
