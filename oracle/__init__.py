@@ -96,6 +96,18 @@ def _load():
                                        c.c_int32, c.c_double, c.c_int32, c.c_void_p, c.c_int64,
                                        _f64, c.c_void_p, _f64]
         lib.oracle_bltc_ts.restype = c.c_int
+        lib.oracle_bltc_prepare.argtypes = [_f64, _f64, _f64, c.c_int64, _f64, _f64, _f64, _f64,
+                                            c.c_int64, c.c_double, c.c_int32, c.c_int32, c.c_int32,
+                                            c.c_int32, c.c_double, c.c_int32, c.POINTER(c.c_void_p),
+                                            _f64]
+        lib.oracle_bltc_prepare.restype = c.c_int
+        lib.oracle_bltc_num_batches.argtypes = [c.c_void_p]
+        lib.oracle_bltc_num_batches.restype = c.c_int64
+        lib.oracle_bltc_evaluate.argtypes = [c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, _f64,
+                                             c.c_void_p, c.POINTER(c.c_double)]
+        lib.oracle_bltc_evaluate.restype = c.c_int
+        lib.oracle_bltc_release.argtypes = [c.c_void_p]
+        lib.oracle_bltc_release.restype = None
         lib.oracle_bltc_cp.argtypes = [_f64, _f64, _f64, c.c_int64, _f64, _f64, _f64, _f64,
                                        c.c_int64, c.c_double, c.c_int32, c.c_int32, c.c_int32,
                                        c.c_int32, c.c_double, c.c_int32, _f64, c.c_void_p]
@@ -217,7 +229,7 @@ def modified_charges(tree: Tree, q, degree, threads=0):
 
 
 def lists(batches: Tree, sources: Tree, theta, degree):
-    """Algorithm 1's ComputePotential recursion for every batch (leaves of ``batches`` in DFS
+    """Algorithm 1's walk of the source tree for every batch (leaves of ``batches`` in DFS
     order), recording the approximation and direct lists as CSR arrays of node ids."""
     lib = _load()
     na, nd = ctypes.c_int64(), ctypes.c_int64()
@@ -260,6 +272,50 @@ def bltc(x, y, z, q, theta, degree, leaf_size, batch_size, kernel=KERNEL_COULOMB
     if rc:
         raise ValueError(f"oracle_bltc failed ({rc})")
     return phi, phi_abs, {"setup": tm[0], "precompute": tm[1], "compute": tm[2]}
+
+
+class Prepared:
+    """Algorithm 1's setup for targets = sources (trees and modified charges), kept for
+    evaluations of all or some batches: ``evaluate(batches=None, threads=0, with_abs=False)``
+    returns (phi, phi_abs or None, seconds).  ``timings`` holds the setup's two phases."""
+
+    def __init__(self, x, y, z, q, theta, degree, leaf_size, batch_size, kernel=KERNEL_COULOMB,
+                 kappa=0.0, threads=0):
+        lib = _load()
+        self._arrays = [_c(x), _c(y), _c(z), _c(q)]     # read by every evaluation
+        x, y, z, q = self._arrays
+        self.n = x.shape[0]
+        tm = np.zeros(2)
+        h = ctypes.c_void_p()
+        rc = lib.oracle_bltc_prepare(x, y, z, self.n, x, y, z, q, self.n, float(theta), int(degree),
+                                     int(leaf_size), int(batch_size), int(kernel), float(kappa),
+                                     int(threads), ctypes.byref(h), tm)
+        if rc:
+            raise ValueError(f"oracle_bltc_prepare failed ({rc})")
+        self._h = h.value
+        self.timings = {"setup": tm[0], "precompute": tm[1]}
+        self.n_batches = int(lib.oracle_bltc_num_batches(self._h))
+
+    def evaluate(self, batches=None, threads=0, with_abs=False):
+        phi = np.empty(self.n)
+        phi_abs = np.empty(self.n) if with_abs else None
+        sub = None if batches is None else _c(batches, np.int64)
+        sec = ctypes.c_double()
+        rc = _load().oracle_bltc_evaluate(self._h, None if sub is None else sub.ctypes.data,
+                                          0 if sub is None else sub.shape[0], int(threads), phi,
+                                          None if phi_abs is None else phi_abs.ctypes.data,
+                                          ctypes.byref(sec))
+        if rc:
+            raise ValueError(f"oracle_bltc_evaluate failed ({rc})")
+        return phi, phi_abs, sec.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().oracle_bltc_release(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def bltc_ts(targets, sources, q, theta, degree, leaf_size, batch_size,

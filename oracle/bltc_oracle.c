@@ -499,8 +499,13 @@ static void direct_interaction(cp_ctx* c, int64_t B, int64_t C)
     }
 }
 
-/* ComputePotential(batch, cluster) of Algorithm 1. */
-static void compute_potential(cp_ctx* c, int64_t B, int64_t C)
+/* Where Algorithm 1 puts the pair (batch B, cluster C), from the two conditions of Eq. 13:
+ * both hold -> C is approximated for B (Eq. 11); the geometric one holds but C has too few
+ * particles to interpolate -> the whole of C is summed directly (reading R5); the geometric
+ * one fails -> a leaf C is summed directly (Eq. 9), otherwise its children are examined. */
+enum { PAIR_APPROX, PAIR_DIRECT, PAIR_CHILDREN };
+
+static int classify_pair(const cp_ctx* c, int64_t B, int64_t C)
 {
     const double* cb = c->bt->center + 3 * B;
     const double* cc = c->st->center + 3 * C;
@@ -511,22 +516,42 @@ static void compute_potential(cp_ctx* c, int64_t B, int64_t C)
     double ratio = (c->bt->radius[B] + c->st->radius[C]) / R;
     int geometric_ok = ratio < c->theta;      /* Eq. 13, first condition (R4) */
     int size_ok = c->P < c->st->count[C];      /* Eq. 13, second condition */
-    if (geometric_ok && size_ok) {
-        if (c->app) list_push(&c->app, &c->n_app, &c->cap_app, C, &c->fail);
-        if (c->phi) approx_interaction(c, B, C);
-    } else if (!geometric_ok) {
-        if (c->st->n_children[C] == 0) {
+    if (geometric_ok) return size_ok ? PAIR_APPROX : PAIR_DIRECT;
+    return c->st->n_children[C] == 0 ? PAIR_DIRECT : PAIR_CHILDREN;
+}
+
+/* Algorithm 1 for one batch B: the source tree is examined depth first from the root with
+ * an explicit stack (children pushed last to first, so they are examined in stored order);
+ * every approximated or directly summed cluster is recorded and summed in that order. */
+static void batch_potential(cp_ctx* c, int64_t B)
+{
+    int32_t depth = 0;
+    for (int64_t v = 0; v < c->st->n_nodes; ++v)
+        if (c->st->level[v] > depth) depth = c->st->level[v];
+    int64_t cap = 8 * ((int64_t)depth + 1) + 1, top = 0;
+    int64_t* stack = (int64_t*)malloc((size_t)cap * sizeof(int64_t));
+    if (!stack) {
+        c->fail = 1;
+        return;
+    }
+    stack[top++] = 0;
+    while (top > 0) {
+        const int64_t C = stack[--top];
+        switch (classify_pair(c, B, C)) {
+        case PAIR_APPROX:
+            if (c->app) list_push(&c->app, &c->n_app, &c->cap_app, C, &c->fail);
+            if (c->phi) approx_interaction(c, B, C);
+            break;
+        case PAIR_DIRECT:
             if (c->dir) list_push(&c->dir, &c->n_dir, &c->cap_dir, C, &c->fail);
             if (c->phi) direct_interaction(c, B, C);
-        } else {
-            for (int k = 0; k < c->st->n_children[C]; ++k)
-                compute_potential(c, B, c->st->children[8 * C + k]);
+            break;
+        default:
+            for (int k = c->st->n_children[C] - 1; k >= 0; --k) stack[top++] = c->st->children[8 * C + k];
+            break;
         }
-    } else {
-        /* (n+1)^3 >= N_C: the whole cluster is summed directly (R5). */
-        if (c->dir) list_push(&c->dir, &c->n_dir, &c->cap_dir, C, &c->fail);
-        if (c->phi) direct_interaction(c, B, C);
     }
+    free(stack);
 }
 
 /* Leaves of a tree in DFS order (these are the target batches of a batch tree). */
@@ -576,7 +601,7 @@ int oracle_lists(const oracle_tree* bt, const oracle_tree* st, double theta, int
             free(leaves);
             return -2;
         }
-        compute_potential(&c, leaves[b], 0);
+        batch_potential(&c, leaves[b]);
         if (c.fail) {
             free(c.app);
             free(c.dir);
@@ -607,12 +632,134 @@ static double now_seconds(void)
 #endif
 }
 
-/* Algorithm 1 for nt targets (tx, ty, tz) and ns sources (sx, sy, sz, sq), which may be
- * different particle sets (Sec. II: the method needs only the target and source
- * positions).  The source tree uses leaf_size (N_L), the batch tree of the targets
- * batch_size (N_B).  If batch_subset is non-NULL, only those batches (indices into the
- * DFS-ordered leaves of the batch tree) are evaluated; phi of the other targets is left at 0.
- * timings receives setup (trees), precompute (modified charges) and compute seconds. */
+/* Algorithm 1's setup for nt targets (tx, ty, tz) and ns sources (sx, sy, sz, sq), which
+ * may be different particle sets (Sec. II: the method needs only the target and source
+ * positions): the source tree (leaf_size, N_L), the batch tree of the targets (batch_size,
+ * N_B) and the modified charges of every source cluster (Eq. 12).  The arrays are read
+ * again by oracle_bltc_evaluate and must outlive the handle.  timings (may be NULL)
+ * receives setup (trees) and precompute (modified charges) seconds. */
+struct oracle_prepared {
+    oracle_tree *st, *bt;
+    const double *tx, *ty, *tz, *sx, *sy, *sz, *sq;
+    int64_t nt, nb;
+    int64_t* leaves;
+    double* qhat;
+    double theta, kappa;
+    int32_t kernel, degree;
+};
+
+void oracle_bltc_release(oracle_prepared* p)
+{
+    if (!p) return;
+    free(p->leaves);
+    free(p->qhat);
+    oracle_tree_free(p->st);
+    oracle_tree_free(p->bt);
+    free(p);
+}
+
+int oracle_bltc_prepare(const double* tx, const double* ty, const double* tz, int64_t nt,
+                        const double* sx, const double* sy, const double* sz, const double* sq,
+                        int64_t ns, double theta, int32_t degree, int32_t leaf_size,
+                        int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
+                        oracle_prepared** out, double* timings)
+{
+    *out = NULL;
+    if (nt < 1 || ns < 1 || degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    oracle_prepared* p = (oracle_prepared*)calloc(1, sizeof(oracle_prepared));
+    if (!p) return -2;
+    double t0 = now_seconds();
+    if (oracle_tree_build(sx, sy, sz, ns, leaf_size, &p->st) ||
+        oracle_tree_build(tx, ty, tz, nt, batch_size, &p->bt)) {
+        oracle_bltc_release(p);
+        return -2;
+    }
+    double t1 = now_seconds();
+    const int64_t n1 = degree + 1, P = n1 * n1 * n1;
+    p->qhat = (double*)malloc((size_t)(p->st->n_nodes * P) * sizeof(double));
+    p->nb = collect_leaves(p->bt, NULL);
+    p->leaves = (int64_t*)malloc((size_t)p->nb * sizeof(int64_t));
+    if (!p->qhat || !p->leaves) {
+        oracle_bltc_release(p);
+        return -2;
+    }
+    collect_leaves(p->bt, p->leaves);
+    oracle_modified_charges(p->st, sx, sy, sz, sq, degree, threads, p->qhat);
+    double t2 = now_seconds();
+    p->tx = tx; p->ty = ty; p->tz = tz;
+    p->sx = sx; p->sy = sy; p->sz = sz; p->sq = sq;
+    p->nt = nt;
+    p->theta = theta;
+    p->kappa = kappa;
+    p->kernel = kernel;
+    p->degree = degree;
+    if (timings) {
+        timings[0] = t1 - t0;
+        timings[1] = t2 - t1;
+    }
+    *out = p;
+    return 0;
+}
+
+int64_t oracle_bltc_num_batches(const oracle_prepared* p) { return p ? p->nb : 0; }
+
+/* Algorithm 1's evaluation over the prepared setup: every batch (or only batch_subset, indices
+ * into the DFS-ordered leaves of the batch tree; phi of the other targets is left at 0), in
+ * parallel over batches.  *seconds (may be NULL) receives the time taken. */
+int oracle_bltc_evaluate(const oracle_prepared* p, const int64_t* batch_subset, int64_t n_subset,
+                         int32_t threads, double* phi, double* phi_abs, double* seconds)
+{
+    if (!p) return -1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    double t0 = now_seconds();
+    const int64_t n1 = p->degree + 1, P = n1 * n1 * n1;
+    for (int64_t i = 0; i < p->nt; ++i) {
+        phi[i] = 0.0;
+        if (phi_abs) phi_abs[i] = 0.0;
+    }
+    int64_t todo = batch_subset ? n_subset : p->nb;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t u = 0; u < todo; ++u) {
+        int64_t b = batch_subset ? batch_subset[u] : u;
+        if (b < 0 || b >= p->nb) {
+            bad = 1;
+            continue;
+        }
+        cp_ctx c;
+        memset(&c, 0, sizeof(c));
+        c.bt = p->bt;
+        c.st = p->st;
+        c.tx = p->tx;
+        c.ty = p->ty;
+        c.tz = p->tz;
+        c.sx = p->sx;
+        c.sy = p->sy;
+        c.sz = p->sz;
+        c.sq = p->sq;
+        c.qhat = p->qhat;
+        c.theta = p->theta;
+        c.kappa = p->kappa;
+        c.kernel = p->kernel;
+        c.degree = p->degree;
+        c.P = P;
+        c.phi = phi;
+        c.phi_abs = phi_abs;
+        batch_potential(&c, p->leaves[b]);
+        if (c.fail) bad = 1;
+    }
+    if (seconds) *seconds = now_seconds() - t0;
+    return bad ? -1 : 0;
+}
+
+/* Algorithm 1 for distinct target and source sets: the setup, the evaluation of every batch
+ * (or of batch_subset), and the release.  timings receives setup (trees), precompute
+ * (modified charges) and compute seconds. */
 int oracle_bltc_ts(const double* tx, const double* ty, const double* tz, int64_t nt,
                    const double* sx, const double* sy, const double* sz, const double* sq,
                    int64_t ns, double theta, int32_t degree, int32_t leaf_size,
@@ -620,76 +767,19 @@ int oracle_bltc_ts(const double* tx, const double* ty, const double* tz, int64_t
                    const int64_t* batch_subset, int64_t n_subset, double* phi, double* phi_abs,
                    double* timings)
 {
-    if (nt < 1 || ns < 1 || degree < 1 || degree > ORACLE_MAX_DEGREE) return -1;
-#ifdef _OPENMP
-    if (threads > 0) omp_set_num_threads(threads);
-#endif
-    double t0 = now_seconds();
-    oracle_tree *st = NULL, *bt = NULL;
-    if (oracle_tree_build(sx, sy, sz, ns, leaf_size, &st)) return -2;
-    if (oracle_tree_build(tx, ty, tz, nt, batch_size, &bt)) {
-        oracle_tree_free(st);
-        return -2;
-    }
-    double t1 = now_seconds();
-    const int64_t n1 = degree + 1, P = n1 * n1 * n1;
-    double* qhat = (double*)malloc((size_t)(st->n_nodes * P) * sizeof(double));
-    if (!qhat) {
-        oracle_tree_free(st);
-        oracle_tree_free(bt);
-        return -2;
-    }
-    oracle_modified_charges(st, sx, sy, sz, sq, degree, threads, qhat);
-    double t2 = now_seconds();
-
-    int64_t nb = collect_leaves(bt, NULL);
-    int64_t* leaves = (int64_t*)malloc((size_t)nb * sizeof(int64_t));
-    collect_leaves(bt, leaves);
-    for (int64_t i = 0; i < nt; ++i) {
-        phi[i] = 0.0;
-        if (phi_abs) phi_abs[i] = 0.0;
-    }
-    int64_t todo = batch_subset ? n_subset : nb;
-    int bad = 0;
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t u = 0; u < todo; ++u) {
-        int64_t b = batch_subset ? batch_subset[u] : u;
-        if (b < 0 || b >= nb) {
-            bad = 1;
-            continue;
-        }
-        cp_ctx c;
-        memset(&c, 0, sizeof(c));
-        c.bt = bt;
-        c.st = st;
-        c.tx = tx;
-        c.ty = ty;
-        c.tz = tz;
-        c.sx = sx;
-        c.sy = sy;
-        c.sz = sz;
-        c.sq = sq;
-        c.qhat = qhat;
-        c.theta = theta;
-        c.kappa = kappa;
-        c.kernel = kernel;
-        c.degree = degree;
-        c.P = P;
-        c.phi = phi;
-        c.phi_abs = phi_abs;
-        compute_potential(&c, leaves[b], 0);
-    }
-    double t3 = now_seconds();
+    oracle_prepared* p = NULL;
+    double tm[2] = {0.0, 0.0}, tc = 0.0;
+    int rc = oracle_bltc_prepare(tx, ty, tz, nt, sx, sy, sz, sq, ns, theta, degree, leaf_size,
+                                 batch_size, kernel, kappa, threads, &p, tm);
+    if (rc) return rc;
+    rc = oracle_bltc_evaluate(p, batch_subset, n_subset, threads, phi, phi_abs, &tc);
     if (timings) {
-        timings[0] = t1 - t0;
-        timings[1] = t2 - t1;
-        timings[2] = t3 - t2;
+        timings[0] = tm[0];
+        timings[1] = tm[1];
+        timings[2] = tc;
     }
-    free(leaves);
-    free(qhat);
-    oracle_tree_free(st);
-    oracle_tree_free(bt);
-    return bad ? -1 : 0;
+    oracle_bltc_release(p);
+    return rc;
 }
 
 /* Algorithm 1 with targets = sources (x, y, z, q), as in all of the paper's runs. */
@@ -708,7 +798,7 @@ int oracle_bltc(const double* x, const double* y, const double* z, const double*
 /* which are summed exactly.                                                              */
 /* ------------------------------------------------------------------------------------ */
 
-/* Per source batch S (a leaf of the source tree, DFS order), ComputePotential walks the
+/* Per source batch S (a leaf of the source tree, DFS order), Algorithm 1's walk covers the
  * target tree with the same MAC (Eq. 13, here (r_S + r_T)/R < theta and (n+1)^3 < N_T):
  *   - approximated target cluster T: the potential at T's Chebyshev points,
  *       phihat_T[k] += sum_{y_j in S} G(t_k, y_j) q_j,        t_k = (s1[k1], s2[k2], s3[k3]);

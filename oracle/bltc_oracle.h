@@ -47,7 +47,7 @@ int oracle_modified_charges(const oracle_tree* t, const double* x, const double*
                             const double* z, const double* q, int32_t degree,
                             int32_t threads, double* qhat);
 
-/* Algorithm 1's ComputePotential recursion, recording the lists only. */
+/* Algorithm 1's walk of every batch, recording the lists only. */
 int oracle_lists(const oracle_tree* bt, const oracle_tree* st, double theta, int32_t degree,
                  int64_t* app_off, int64_t* app_ids, int64_t* dir_off, int64_t* dir_ids,
                  int64_t* n_app_total, int64_t* n_dir_total);
@@ -57,6 +57,19 @@ int oracle_bltc(const double* x, const double* y, const double* z, const double*
                 double theta, int32_t degree, int32_t leaf_size, int32_t batch_size,
                 int32_t kernel, double kappa, int32_t threads, const int64_t* batch_subset,
                 int64_t n_subset, double* phi, double* phi_abs, double* timings);
+
+/* Algorithm 1 in parts: the setup (trees and modified charges) once, then evaluations of
+ * all or some batches over it.  The input arrays must outlive the handle. */
+typedef struct oracle_prepared oracle_prepared;
+int oracle_bltc_prepare(const double* tx, const double* ty, const double* tz, int64_t nt,
+                        const double* sx, const double* sy, const double* sz, const double* sq,
+                        int64_t ns, double theta, int32_t degree, int32_t leaf_size,
+                        int32_t batch_size, int32_t kernel, double kappa, int32_t threads,
+                        oracle_prepared** out, double* timings);
+int64_t oracle_bltc_num_batches(const oracle_prepared* p);
+int oracle_bltc_evaluate(const oracle_prepared* p, const int64_t* batch_subset, int64_t n_subset,
+                         int32_t threads, double* phi, double* phi_abs, double* seconds);
+void oracle_bltc_release(oracle_prepared* p);
 
 /* Algorithm 1 for distinct target and source sets (nt targets, ns sources). */
 int oracle_bltc_ts(const double* tx, const double* ty, const double* tz, int64_t nt,
