@@ -12,7 +12,11 @@ Prints one JSON line (rank 0).  Under torchrun each rank solves its own independ
 on its own GPU (replicas: the treecode of one system needs no exchange); the value is the
 whole job's targets per second over the slowest rank.  ``--impl reference`` times the FP64
 CPU oracle (Algorithm 1 as written, on the host cores) on a bounded sample of the same
-workload, extrapolated to the whole system by target count.
+workload in every step: the evaluation of two batches per core.
+
+The default run adds sub-records for the 8e6 Plummer (Yukawa) and 2.56e8 uniform (n = 10)
+configurations under "configs", and the oracle's measured time for the whole 1e6 system under
+"cpu_baseline".
 """
 from __future__ import annotations
 
@@ -40,6 +44,9 @@ WORKLOAD_NAME = ("uniform cube N=1e6 (q in [-1,1]), Coulomb, theta=0.7, n=8, N_L
 # Roofline of the sweep: one interaction of the Coulomb kernel costs one MUFU.RSQ; the SFU
 # (XU) pipe issues 16 per clock per SM, so the peak interaction rate is SMs * 16 * f_max.
 XU_PER_CLK_PER_SM = 16
+# A Yukawa evaluation adds one MUFU.EX2 on the same pipe, measured at 26 per clock per SM
+# (microbenchmark): 1/16 + 1/26 clocks of the pipe per evaluation.
+XU_EX2_PER_CLK_PER_SM = 26
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 # the sweep kernel's source: its device code and the file that plans, instantiates and launches
@@ -194,9 +201,38 @@ def cpu_model() -> str:
     return "unknown"
 
 
+def oracle_measured(x, y, z, q, w, sample_batches=None, threads=None):
+    """Algorithm 1 on the host cores, measured: the setup (trees, modified charges), then the
+    evaluation of every batch; with ``sample_batches`` also the evaluation of that many batches
+    spread over the system (one per core), extrapolated by target count, and the error of that
+    estimate against the measured whole."""
+    import oracle
+    cores = threads or os.cpu_count() or 1
+    prep = oracle.Prepared(x, y, z, q, w["theta"], w["degree"], w["leaf"], w["batch"],
+                           w["kernel"], w["kappa"], threads=cores)
+    setup = prep.timings["setup"] + prep.timings["precompute"]
+    n = len(x)
+    out = {"cores": cores, "cpu_model": cpu_model(), "setup_s": setup, "n_batches": prep.n_batches}
+    if sample_batches:
+        st = oracle.Tree(x, y, z, w["batch"])
+        nl = len(st.leaves)
+        pick = np.unique(np.linspace(0, nl - 1, min(nl, sample_batches)).astype(np.int64))
+        targets = int(st.count[st.leaves[pick]].sum())
+        _, _, sec = prep.evaluate(pick, threads=cores)
+        out["estimate_s"] = setup + sec * (n / targets)
+        out["estimate_sample"] = (f"ComputePotential on {len(pick)} of {nl} batches ({targets} "
+                                  f"targets), extrapolated by target count")
+    _, _, sec = prep.evaluate(None, threads=cores)
+    out["measured_full_s"] = setup + sec
+    if sample_batches:
+        out["estimate_error"] = out["estimate_s"] / out["measured_full_s"] - 1.0
+    prep.close()
+    return out
+
+
 def oracle_sample(x, y, z, q, w, budget_batches=None, threads=None):
     """Algorithm 1 on the host cores: full trees and modified charges, ComputePotential on a
-    sample of batches; time-to-solution extrapolated by target count."""
+    sample of batches; time-to-solution extrapolated by target count (an estimate)."""
     import oracle
     cores = threads or os.cpu_count() or 1
     st = oracle.Tree(x, y, z, w["leaf"])
@@ -331,16 +367,168 @@ def run_ours(args, dist: Dist):
         out["error"] = check_errors(ctx, b, X, p, w, phi)
     if not args.no_e2e:
         out["e2e"] = run_e2e(ctx, b, x, y, z, q, p, args, dist, w)
+    if not args.no_configs:
+        out["configs"] = {}
+        for key in args.configs.split(","):
+            if key:
+                out["configs"][key] = run_config(ctx, b, key, args, dist)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cb = oracle_sample(x, y, z, q, w)
+        cb = oracle_measured(x, y, z, q, w, sample_batches=os.cpu_count() or 1)
         one = oracle_sample(x, y, z, q, w, budget_batches=1, threads=1)
-        out["cpu_baseline"] = {"value": cb["targets_per_s"], "unit": "targets/s",
-                               "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"],
-                               "cpu_model": cb["cpu_model"], "t_est_s": cb["t_est_s"], "wall_s": cb["wall_s"],
+        out["cpu_baseline"] = {"value": w["n"] / cb["measured_full_s"], "unit": "targets/s",
+                               "cores": cb["cores"], "kind": "oracle",
+                               "sample": (f"the whole {w['n']}-particle system, measured: trees and "
+                                          f"modified charges, then ComputePotential on all "
+                                          f"{cb['n_batches']} batches"),
+                               "cpu_model": cb["cpu_model"], "measured_full_s": cb["measured_full_s"],
+                               "setup_s": cb["setup_s"],
+                               "sampled_estimate": {"t_est_s": cb["estimate_s"], "sample": cb["estimate_sample"],
+                                                    "error_vs_measured": cb["estimate_error"]},
                                "single_thread": {"value": one["targets_per_s"], "cores": 1,
-                                                 "sample": one["sample"], "t_est_s": one["t_est_s"],
-                                                 "wall_s": one["wall_s"]}}
+                                                 "kind": "estimate", "sample": one["sample"],
+                                                 "t_est_s": one["t_est_s"], "wall_s": one["wall_s"]}}
     ctx.close()
+    return out
+
+
+# ---- the large configurations: sub-records of the default run ------------------------------
+
+CONFIGS = {
+    "3": dict(kind="plummer", n=8_000_000, theta=0.8, degree=8, kernel=1, kappa=0.5, seed=20031839,
+              fp32_storage=False, steps=3, warmup=1, error_targets=10_000,
+              name=("truncated Plummer sphere N=8e6 (a=1, r<=10), q in [-1,1], Yukawa kappa=0.5, "
+                    "theta=0.8, n=8, leaf=batch autotuned over {500,1000,2000,3000,4000}, mixed")),
+    "5": dict(kind="cube", n=256_000_000, theta=0.8, degree=10, kernel=0, kappa=0.0, seed=20031841,
+              fp32_storage=True, steps=2, warmup=1, error_targets=2048,
+              name=("uniform cube N=2.56e8, xyzq stored in FP32 (read as FP64), Coulomb, theta=0.8, "
+                    "n=10, leaf=batch autotuned over {500,1000,2000,3000,4000}, mixed")),
+}
+CANDIDATES = (500, 1000, 2000, 3000, 4000)
+
+
+def xu_peak(sm_count, kernel):
+    """Kernel evaluations per second the XU pipe allows at the recipe's maximum SM clock:
+    one MUFU.RSQ per evaluation (16 per clock per SM), plus one MUFU.EX2 for Yukawa (26)."""
+    per_clk = XU_PER_CLK_PER_SM if kernel == 0 else 1.0 / (1.0 / XU_PER_CLK_PER_SM +
+                                                            1.0 / XU_EX2_PER_CLK_PER_SM)
+    return sm_count * per_clk * SM_MAX_MHZ * 1e6, per_clk
+
+
+def sample_batches(leaf_counts, goal, seed):
+    """Seeded random batches, in increasing order, until they hold `goal` targets (a cluster
+    sample of targets: the error of Eq. 16 on a subset of targets, Sec. IV)."""
+    order = np.random.default_rng(seed).permutation(len(leaf_counts))
+    total, pick = 0, []
+    for i in order:
+        pick.append(int(i))
+        total += int(leaf_counts[i])
+        if total >= goal:
+            break
+    return np.sort(np.array(pick, dtype=np.int32))
+
+
+def run_config(ctx, b, key, args, dist):
+    """One large configuration: autotuned leaf/batch size, a few timed solves (inputs larger
+    than L2), kernel evaluations and the sweep's roofline, and Eq. 16 errors on sampled
+    batches: mixed and FP64 treecode against the FP64 direct sum, and mixed against FP64."""
+    import torch
+    from paper_2003_01836_gb300 import inputs
+    c = dict(CONFIGS[key])
+    if key == "5" and args.error_targets5:
+        c["error_targets"] = args.error_targets5
+    t0 = time.perf_counter()
+    host = inputs.system(c["kind"], c["n"], c["seed"] + dist.rank)
+    if c["fp32_storage"]:
+        host = [a.astype(np.float32).astype(np.float64) for a in host]
+    X = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in host]
+    del host
+    gen_s = time.perf_counter() - t0
+    p = b.params(c["degree"], c["theta"], 2000, 2000, c["kernel"], c["kappa"], b.BLTC_PRECISION_MIXED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    best, tune_ms = b.bltc_autotune(ctx.h, *X, p, leaf=CANDIDATES, repeats=1, use_cache=False)
+    tune_s = time.perf_counter() - t0
+    phi = torch.empty_like(X[0])
+    for _ in range(c["warmup"]):
+        ctx.solve(*X, best, phi)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dist.local_rank)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    step_ms, phases = [], []
+    sampler.start()
+    for _ in range(c["steps"]):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.solve(*X, best, phi)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        phases.append(b.bltc_last_timings(ctx.h))
+    clocks = sampler.stop()
+    del flush
+    ph = {k: statistics.mean(d[k] for d in phases) for k in phases[0]}
+    mean_ms = statistics.mean(step_ms)
+
+    # work counts, the sweep's roofline, and the FP64 treecode on sampled batches
+    st = b.bltc_tree_build(ctx.h, *X, best.leaf_size)
+    L = b.bltc_lists_build(ctx.h, st, st, best)
+    counts = b.bltc_stats(ctx.h, L)
+    evals = b.bltc_evaluations(ctx.h, L, best)
+    n_batches = b.bltc_lists_info(L)["n_batches"]
+    tree = b.bltc_tree_export(ctx.h, st, want=("perm", "begin", "count", "n_children"))
+    leaves = np.flatnonzero(tree["n_children"] == 0)
+    pick = sample_batches(tree["count"][leaves], c["error_targets"], c["seed"] + 1000)
+    idx = np.concatenate([tree["perm"][tree["begin"][leaves[i]]:tree["begin"][leaves[i]] +
+                                       tree["count"][leaves[i]]] for i in pick])
+    p64 = b.params(c["degree"], c["theta"], best.leaf_size, best.batch_size, c["kernel"], c["kappa"],
+                   b.BLTC_PRECISION_FP64)
+    t0 = time.perf_counter()
+    S = b.bltc_lists_select(ctx.h, L, pick)
+    b.bltc_modified_charges(ctx.h, st, S, p64)
+    phi64 = torch.empty_like(phi)
+    b.bltc_evaluate(ctx.h, S, st, st, p64, phi64)
+    torch.cuda.synchronize()
+    fp64_s = time.perf_counter() - t0
+    b.bltc_lists_destroy(S)
+    b.bltc_lists_destroy(L)
+    b.bltc_tree_destroy(st)
+    tidx = torch.from_numpy(idx).cuda()
+    T = [a.index_select(0, tidx).contiguous() for a in X[:3]]
+    ref = torch.empty_like(T[0])
+    t0 = time.perf_counter()
+    b.bltc_direct_sum(ctx.h, *T, *X[:3], X[3], p64, ref)
+    torch.cuda.synchronize()
+    direct_s = time.perf_counter() - t0
+    h = lambda t: t.detach().cpu().numpy()
+    ref_h, mx_h, d64_h = h(ref), h(phi.index_select(0, tidx)), h(phi64.index_select(0, tidx))
+    peak, per_clk = xu_peak(ctx.sm_count, c["kernel"])
+    achieved = evals / (ph["sweep"] / 1e3)
+    out = {"workload": c["name"], "n_particles": c["n"], "leaf_size": best.leaf_size,
+           "batch_size": best.batch_size, "batches": n_batches,
+           "autotune": {"seconds": tune_s, "candidates": list(CANDIDATES),
+                        "timed_ms": {str(k[0]): v for k, v in tune_ms.items() if v == v}},
+           "input_generation_s": gen_s, "steps": c["steps"], "warmup": c["warmup"],
+           "ms_per_step": mean_ms, "targets_per_s": c["n"] / (mean_ms / 1e3),
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "max": max(step_ms)},
+           "phases_ms": ph, "clocks": clocks,
+           "evaluated_interactions_per_step": counts["direct"] + counts["approx"],
+           "kernel_evaluations_per_step": evals,
+           "roofline": {"bound": "alu", "kernel": f"k_sweep_mixed<{'Coulomb' if c['kernel'] == 0 else 'Yukawa'}>",
+                        "pipe": ("XU: MUFU.RSQ at 16/clk/SM" if c["kernel"] == 0 else
+                                 "XU: MUFU.RSQ (16/clk/SM) + MUFU.EX2 (26/clk/SM) per evaluation"),
+                        "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G evaluations/s",
+                        "frac": achieved / peak, "evaluations_per_clk_per_sm_peak": per_clk,
+                        "traffic": None,
+                        "peak_basis": f"{ctx.sm_count} SMs x {per_clk:.2f}/clk x {SM_MAX_MHZ:.0f} MHz"},
+           "error": {"sample": (f"targets of {len(pick)} seeded random batches ({len(idx)} targets)"),
+                     "mixed_vs_fp64_gpu_bltc": rel_err(d64_h, mx_h),
+                     "meets_1e-6": bool(rel_err(d64_h, mx_h) <= 1e-6),
+                     "mixed_bltc_vs_fp64_direct": rel_err(ref_h, mx_h),
+                     "fp64_bltc_vs_fp64_direct": rel_err(ref_h, d64_h),
+                     "fp64_bltc_sampled_seconds": fp64_s, "fp64_direct_sampled_seconds": direct_s}}
+    del X, phi, phi64, T, ref
+    torch.cuda.empty_cache()
     return out
 
 
@@ -693,6 +881,10 @@ def run_graph(args, dist: Dist):
 # ---- reference arm: the oracle --------------------------------------------------------------
 
 def run_reference(args, dist: Dist):
+    """The oracle on the host cores, every step a bounded, measured sample of the workload:
+    Algorithm 1's evaluation (ComputePotential) of two batches per core, the batches drawn in
+    turn from a seeded permutation of all of them.  The trees and modified charges are built
+    once before the warm-up (their time is reported, not in the steps)."""
     if dist.rank != 0:
         return None
     from paper_2003_01836_gb300 import inputs
@@ -702,23 +894,45 @@ def run_reference(args, dist: Dist):
     if args.n:
         w["n"] = args.n
     x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"])
-    for _ in range(args.warmup):
-        oracle_sample(x, y, z, q, w, budget_batches=2)
-    # one sampled batch per host core, as in the cpu_baseline leg of our arm
-    runs = [oracle_sample(x, y, z, q, w) for _ in range(args.steps)]
-    t = statistics.mean(r["t_est_s"] for r in runs)
-    v = w["n"] / t
+    cores = os.cpu_count() or 1
+    prep = oracle.Prepared(x, y, z, q, w["theta"], w["degree"], w["leaf"], w["batch"],
+                           w["kernel"], w["kappa"], threads=cores)
+    setup_s = prep.timings["setup"] + prep.timings["precompute"]
+    st = oracle.Tree(x, y, z, w["batch"])
+    counts = st.count[st.leaves]
+    nl = len(counts)
+    order = np.random.default_rng(20031836).permutation(nl)
+    per_step = min(2 * cores, nl)       # two batches per core: dynamic scheduling evens them out
+
+    def batches(i):
+        return np.sort(np.take(order, np.arange(i * per_step, (i + 1) * per_step), mode="wrap"))
+
+    for i in range(args.warmup):
+        prep.evaluate(batches(i), threads=cores)
+    times, targets = [], 0
+    for i in range(args.warmup, args.warmup + args.steps):
+        pick = batches(i)
+        t0 = time.perf_counter()
+        prep.evaluate(pick, threads=cores)
+        times.append(time.perf_counter() - t0)
+        targets += int(counts[pick].sum())
+    prep.close()
+    v = targets / sum(times)
+    sample = (f"Algorithm 1's evaluation (ComputePotential) of {per_step} of the {nl} batches per step "
+              f"(two per core), drawn in turn from a seeded permutation; {targets} targets over the "
+              f"timed steps; the trees and modified charges ({setup_s:.2f} s) are built once before "
+              f"the warm-up and are not in the steps")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "targets/s",
             "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME.replace("mixed FP32 evaluation / FP64 accumulation",
                                                          "FP64 CPU oracle"),
                        "n_particles": w["n"], "theta": w["theta"], "degree": w["degree"],
                        "leaf_size": w["leaf"], "batch_size": w["batch"]},
-            "cpu_baseline": {"value": v, "unit": "targets/s", "cores": runs[0]["cores"],
-                             "cpu_model": runs[0]["cpu_model"],
-                             "kind": "oracle", "sample": runs[0]["sample"]},
+            "setup_s": setup_s,
+            "cpu_baseline": {"value": v, "unit": "targets/s", "cores": cores,
+                             "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -733,6 +947,11 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the sub-records of the 8e6 Plummer and 2.56e8 cube configurations")
+    ap.add_argument("--configs", default="3,5", help="which large configurations to add (3, 5)")
+    ap.add_argument("--error-targets5", type=int, default=0,
+                    help="targets of the 2.56e8 configuration's error sample (default 2048)")
     ap.add_argument("--serving", action="store_true",
                     help="time the serving runtime on the request stream instead")
     ap.add_argument("--variant", choices=("treecode", "cp", "cc", "hermite", "graph"), default="treecode",

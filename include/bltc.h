@@ -159,6 +159,15 @@ bltc_status bltc_tree_export(bltc_context* ctx, const bltc_tree* tree, int64_t* 
 bltc_status bltc_lists_build(bltc_context* ctx, const bltc_tree* batches,
                              const bltc_tree* sources, const bltc_params* params,
                              bltc_lists** out);
+/* The lists of some target batches only, for evaluating a sample of the targets (the
+ * error of Eq. 16 on a subset of targets, Sec. IV).  `batches` is a HOST array of
+ * n_batches batch indices (leaves of the batch tree in DFS order), strictly increasing;
+ * every other batch gets empty lists, so bltc_evaluate with the result writes phi = 0
+ * for its targets.  The result refers to the same trees as `lists` and is freed with
+ * bltc_lists_destroy.  Synchronizes.  Errors: ARG (NULL, index out of range, not
+ * increasing), OOM, CUDA. */
+bltc_status bltc_lists_select(bltc_context* ctx, const bltc_lists* lists, const int32_t* batches,
+                              int64_t n_batches, bltc_lists** out);
 void bltc_lists_destroy(bltc_lists* lists);
 bltc_status bltc_lists_info(const bltc_lists* lists, int64_t* n_batches, int64_t* n_approx,
                             int64_t* n_direct);
@@ -310,13 +319,19 @@ bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,
 
 /* ---- autotuning of the leaf and batch sizes --------------------------------------- */
 
-/* Times bltc_solve of the given system for each candidate (leaf_size, batch_size) pair
- * (leaf[i], batch[i]; batch may be NULL for batch = leaf), `repeats` times each after one
- * warm-up, and writes the fastest into *best (a copy of *params with those sizes) and the
- * fastest time of every candidate into ms[n_candidates] (may be NULL).  The choice is cached
- * in the context under (floor(log2 n), degree, kernel, precision, theta to 1e-3): a later call
- * with the same key and use_cache != 0 returns the cached choice without timing (ms untouched).
- * Device pointers as bltc_solve.  Synchronizes.  Errors: ARG, OOM, CUDA. */
+/* Chooses the leaf and batch sizes of the given system among candidate pairs (leaf[i],
+ * batch[i]; batch may be NULL for batch = leaf).  Not in the paper.  First a screen: the
+ * trees, lists and sweep plan of every candidate give its exact work in padded target slots
+ * (each batch's targets rounded up to the passes of its source groups, times the sources
+ * and proxy points it meets); candidates with the same trees count once.  Then the
+ * contenders, at most 3 distinct candidates within 10% of the smallest work, are timed with
+ * bltc_solve (one warm-up, then `repeats` runs, the fastest counts) and the fastest wins;
+ * a single contender wins untimed.  Writes the choice into *best (a copy of *params with
+ * those sizes) and every candidate's fastest time into ms[n_candidates] (may be NULL; NaN
+ * for a candidate not timed).  The choice is cached in the context under (floor(log2 n),
+ * degree, kernel, precision, theta to 1e-3, mean batch size of the first candidate in
+ * quarter octaves): a later call with the same key and use_cache != 0 returns it after the
+ * screen, untimed.  Device pointers as bltc_solve.  Synchronizes.  Errors: ARG, OOM, CUDA. */
 bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, const double* z,
                           const double* q, int64_t n, const bltc_params* params,
                           const int32_t* leaf, const int32_t* batch, int32_t n_candidates,

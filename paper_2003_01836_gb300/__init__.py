@@ -108,6 +108,7 @@ _SIGNATURES = {
     "bltc_tree_info": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "bltc_tree_export": ([_vp] * 13, ctypes.c_int),
     "bltc_lists_build": ([_vp, _vp, _vp, _P, _pp], ctypes.c_int),
+    "bltc_lists_select": ([_vp, _vp, _vp, _i64, _pp], ctypes.c_int),
     "bltc_lists_destroy": ([_vp], None),
     "bltc_lists_info": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "bltc_lists_export": ([_vp] * 6, ctypes.c_int),
@@ -295,17 +296,23 @@ def bltc_tree_info(tree):
             "n_levels": v[3].value}
 
 
-def bltc_tree_export(ctx, tree):
+_TREE_FIELDS = ("perm", "begin", "count", "parent", "level", "n_children", "children", "lo", "hi",
+                "center", "radius")
+
+
+def bltc_tree_export(ctx, tree, want=_TREE_FIELDS):
+    """The tree's arrays on the host (those named in `want`)."""
     info = bltc_tree_info(tree)
     n, m = info["n_particles"], info["n_nodes"]
-    out = {"perm": np.empty(n, np.int64), "begin": np.empty(m, np.int64),
-           "count": np.empty(m, np.int64), "parent": np.empty(m, np.int32),
-           "level": np.empty(m, np.int32), "n_children": np.empty(m, np.int32),
-           "children": np.empty((m, 8), np.int32), "lo": np.empty((m, 3)),
-           "hi": np.empty((m, 3)), "center": np.empty((m, 3)), "radius": np.empty(m)}
-    keys = ["perm", "begin", "count", "parent", "level", "n_children", "children", "lo", "hi",
-            "center", "radius"]
-    _check(ctx, lib().bltc_tree_export(ctx, tree, *[out[k].ctypes.data for k in keys]))
+    make = {"perm": lambda: np.empty(n, np.int64), "begin": lambda: np.empty(m, np.int64),
+            "count": lambda: np.empty(m, np.int64), "parent": lambda: np.empty(m, np.int32),
+            "level": lambda: np.empty(m, np.int32), "n_children": lambda: np.empty(m, np.int32),
+            "children": lambda: np.empty((m, 8), np.int32), "lo": lambda: np.empty((m, 3)),
+            "hi": lambda: np.empty((m, 3)), "center": lambda: np.empty((m, 3)),
+            "radius": lambda: np.empty(m)}
+    out = {k: make[k]() for k in _TREE_FIELDS if k in want}
+    _check(ctx, lib().bltc_tree_export(ctx, tree, *[out[k].ctypes.data if k in out else None
+                                                    for k in _TREE_FIELDS]))
     return out
 
 
@@ -313,6 +320,14 @@ def bltc_lists_build(ctx, batches, sources, p: bltc_params):
     _stream(ctx)
     h = ctypes.c_void_p()
     _check(ctx, lib().bltc_lists_build(ctx, batches, sources, ctypes.byref(p), ctypes.byref(h)))
+    return h.value
+
+
+def bltc_lists_select(ctx, lists, batches):
+    """The lists of the given batches only (others empty: their targets get phi = 0)."""
+    sel = np.ascontiguousarray(batches, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(ctx, lib().bltc_lists_select(ctx, lists, sel.ctypes.data, sel.shape[0], ctypes.byref(h)))
     return h.value
 
 

@@ -1,19 +1,23 @@
 // api.cu -- the extern "C" boundary declared in include/bltc.h: argument checks, status
 // codes, the context (device, stream, allocator, Chebyshev tables) and the composition of
 // the steps into Algorithm 1 (bltc_solve).
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <new>
 #include <tuple>
+#include <vector>
 
 #include "internal.cuh"
 
 struct bltc_context {
     bltc::Context c;
-    // autotuner cache: (log2 n, degree, kernel, precision, theta * 1000) -> (leaf, batch)
-    std::map<std::tuple<int, int, int, int, int>, std::pair<int32_t, int32_t>> tuned;
+    // autotuner cache: (log2 n, degree, kernel, precision, theta * 1000, distribution shape)
+    // -> (leaf, batch)
+    std::map<std::tuple<int, int, int, int, int, int>, std::pair<int32_t, int32_t>> tuned;
 };
 struct bltc_tree {
     bltc::Tree t;
@@ -390,6 +394,17 @@ bltc_status bltc_lists_build(bltc_context* ctx, const bltc_tree* batches, const 
     });
 }
 
+bltc_status bltc_lists_select(bltc_context* ctx, const bltc_lists* lists, const int32_t* batches,
+                              int64_t n_batches, bltc_lists** out) {
+    if (!ctx || !lists || !out) return BLTC_ERR_ARG;
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        std::unique_ptr<bltc_lists> l(new bltc_lists());
+        select_lists(&ctx->c, &lists->l, batches, n_batches, &l->l);
+        *out = l.release();
+    });
+}
+
 void bltc_lists_destroy(bltc_lists* lists) {
     if (!lists) return;
     if (lists->l.ctx) cudaSetDevice(lists->l.ctx->device);
@@ -616,10 +631,52 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
         require(leaf && n_candidates >= 1 && repeats >= 1, "autotune: need candidates and repeats");
         for (int i = 0; i < n_candidates; ++i)
             require(leaf[i] >= 1 && (!batch || batch[i] >= 1), "autotune: sizes must be >= 1");
+        Context* c = &ctx->c;
+        if (ms)
+            for (int i = 0; i < n_candidates; ++i) ms[i] = std::nanf("");
+        // Screen: the exact work of every candidate from its trees, lists and the sweep's
+        // plan (no charges, no sweep).  Candidates whose trees are the same are one candidate.
+        struct Cand {
+            int64_t s_nodes = 0, b_nodes = 0, b_leaves = 0, cost = 0;
+            int same = -1;
+        };
+        std::vector<Cand> cs(static_cast<size_t>(n_candidates));
+        for (int i = 0; i < n_candidates; ++i) {
+            bltc_params p = *params;
+            p.leaf_size = leaf[i];
+            p.batch_size = batch ? batch[i] : leaf[i];
+            Tree st;
+            build_tree(c, x, y, z, q, n, p.leaf_size, &st);
+            std::unique_ptr<Tree> btp;
+            const Tree* bt = &st;
+            if (p.batch_size != p.leaf_size) {
+                btp.reset(new Tree());
+                build_tree(c, x, y, z, nullptr, n, p.batch_size, btp.get());
+                bt = btp.get();
+            }
+            Lists L;
+            build_lists(c, bt, &st, p.theta, p.degree, &L);
+            Cand& k = cs[static_cast<size_t>(i)];
+            k.s_nodes = st.n_nodes;
+            k.b_nodes = bt->n_nodes;
+            k.b_leaves = bt->n_leaves;
+            k.cost = plan_slot_cost(c, &L, p.degree, p.precision);
+            for (int j = 0; j < i; ++j) {
+                const Cand& o = cs[static_cast<size_t>(j)];
+                if (o.same < 0 && o.s_nodes == k.s_nodes && o.b_nodes == k.b_nodes && o.cost == k.cost) {
+                    k.same = j;
+                    break;
+                }
+            }
+        }
+        // The distribution enters the cache key as the mean batch size of the first candidate
+        // (quarter octaves): a uniform cube and a Plummer sphere of the same size differ there.
         int lg = 0;
         while ((int64_t(1) << (lg + 1)) <= n) ++lg;
+        const int shape = static_cast<int>(std::lround(4.0 * std::log2(static_cast<double>(n) /
+                                                                           static_cast<double>(cs[0].b_leaves))));
         const auto key = std::make_tuple(lg, params->degree, params->kernel, params->precision,
-                                         static_cast<int>(std::lround(params->theta * 1000.0)));
+                                         static_cast<int>(std::lround(params->theta * 1000.0)), shape);
         *best = *params;
         if (use_cache) {
             auto it = ctx->tuned.find(key);
@@ -629,42 +686,64 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
                 return;
             }
         }
-        Context* c = &ctx->c;
-        DBuf<double> phi(c, n);
-        cudaEvent_t e0, e1;
-        BLTC_CUDA(cudaEventCreate(&e0));
-        BLTC_CUDA(cudaEventCreate(&e1));
-        float best_ms = 3.0e38f;
-        try {
-            for (int i = 0; i < n_candidates; ++i) {
-                bltc_params p = *params;
-                p.leaf_size = leaf[i];
-                p.batch_size = batch ? batch[i] : leaf[i];
-                solve_device(c, x, y, z, q, n, p, phi.p);     // warm-up
-                float t_min = 3.0e38f;
-                for (int r = 0; r < repeats; ++r) {
-                    BLTC_CUDA(cudaEventRecord(e0, c->stream));
-                    solve_device(c, x, y, z, q, n, p, phi.p);
-                    BLTC_CUDA(cudaEventRecord(e1, c->stream));
-                    BLTC_CUDA(cudaEventSynchronize(e1));
-                    float t = 0.f;
-                    BLTC_CUDA(cudaEventElapsedTime(&t, e0, e1));
-                    t_min = std::min(t_min, t);
+        // Time only the contenders: distinct candidates within kBand of the smallest cost.
+        constexpr double kBand = 0.10;
+        constexpr int kMaxTimed = 3;
+        int64_t min_cost = INT64_MAX;
+        for (const Cand& k : cs)
+            if (k.same < 0) min_cost = std::min(min_cost, k.cost);
+        std::vector<int> cont;
+        for (int i = 0; i < n_candidates; ++i) {
+            const Cand& k = cs[static_cast<size_t>(i)];
+            if (k.same < 0 && static_cast<double>(k.cost) <= (1.0 + kBand) * static_cast<double>(min_cost))
+                cont.push_back(i);
+        }
+        std::stable_sort(cont.begin(), cont.end(), [&](int u, int v) {
+            return cs[static_cast<size_t>(u)].cost < cs[static_cast<size_t>(v)].cost;
+        });
+        if (static_cast<int>(cont.size()) > kMaxTimed) cont.resize(kMaxTimed);
+        int win = cont[0];
+        if (cont.size() > 1) {
+            DBuf<double> phi(c, n);
+            cudaEvent_t e0, e1;
+            BLTC_CUDA(cudaEventCreate(&e0));
+            BLTC_CUDA(cudaEventCreate(&e1));
+            float best_ms = 3.0e38f;
+            try {
+                for (int i : cont) {
+                    bltc_params p = *params;
+                    p.leaf_size = leaf[i];
+                    p.batch_size = batch ? batch[i] : leaf[i];
+                    solve_device(c, x, y, z, q, n, p, phi.p);     // warm-up
+                    float t_min = 3.0e38f;
+                    for (int r = 0; r < repeats; ++r) {
+                        BLTC_CUDA(cudaEventRecord(e0, c->stream));
+                        solve_device(c, x, y, z, q, n, p, phi.p);
+                        BLTC_CUDA(cudaEventRecord(e1, c->stream));
+                        BLTC_CUDA(cudaEventSynchronize(e1));
+                        float t = 0.f;
+                        BLTC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                        t_min = std::min(t_min, t);
+                    }
+                    if (ms) ms[i] = t_min;
+                    if (t_min < best_ms) {
+                        best_ms = t_min;
+                        win = i;
+                    }
                 }
-                if (ms) ms[i] = t_min;
-                if (t_min < best_ms) {
-                    best_ms = t_min;
-                    best->leaf_size = p.leaf_size;
-                    best->batch_size = p.batch_size;
-                }
+            } catch (...) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                throw;
             }
-        } catch (...) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            throw;
+            if (ms)
+                for (int i = 0; i < n_candidates; ++i)
+                    if (cs[static_cast<size_t>(i)].same >= 0) ms[i] = ms[cs[static_cast<size_t>(i)].same];
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        best->leaf_size = leaf[win];
+        best->batch_size = batch ? batch[win] : leaf[win];
         ctx->tuned[key] = {best->leaf_size, best->batch_size};
     });
 }

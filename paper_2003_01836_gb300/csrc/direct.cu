@@ -5,8 +5,8 @@
 // Grid: (target tiles of 256*T targets) x (source splits).  Each block stages its sources
 // in shared-memory tiles and streams them against the targets held in registers, writing
 // one partial per (split, target) into a scratch buffer; a second kernel sums the splits
-// in order, so the result does not depend on scheduling.  MIXED evaluates in FP32 on the
-// coordinates rounded once from FP64, sums each staged tile in FP32 and tiles in FP64.
+// in order, so the result does not depend on scheduling.  MIXED evaluates in FP32 with every
+// coordinate an FP32 (hi, lo) pair, sums blocks of sources in FP32 and tiles in FP64.
 #include <algorithm>
 #include <mutex>
 
@@ -16,7 +16,7 @@ namespace bltc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTile32 = 2048;
+constexpr int kTileM = 512;      // sources per staged tile of the MIXED kernel (64 B each)
 constexpr int kTile64 = 1024;
 constexpr int kBlock = 32;       // FP32 block folded into a TwoSum accumulator
 
@@ -49,52 +49,93 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
     lo = __fadd_rn(lo, e);
 }
 
+// An FP64 value as an FP32 pair hi + lo (hi = fp32(v), lo = fp32(v - hi)): about 48 bits.
+__device__ __forceinline__ float2 split_pair(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - static_cast<double>(h)));
+}
+
+// MIXED: every coordinate enters as an FP32 pair, and x_j - x_i = (hi_j - hi_i) + (lo_j - lo_i).
+// For a close pair the two highs are within a factor of two of each other, so their
+// difference is exact (Sterbenz) and the distance keeps FP32's relative precision however
+// close the particles are; with coordinates rounded once to FP32, a pair at distance r would
+// carry a relative error of about 2^-24 |x| / r.  Two targets per packed FP32x2 operation;
+// the FP32 sums over blocks of kBlock sources are folded by TwoSum, tiles are added in FP64.
 template <int KER, int T>
 __global__ void __launch_bounds__(kThreads, 2) k_direct_mixed(DirectArgs a) {
-    __shared__ __align__(16) float4 sm[kTile32];
+    static_assert(T % 2 == 0, "targets are processed in packed pairs");
+    constexpr int H = T / 2;
+    // per source: (xh, xh, yh, yh), (zh, zh, q, q), (xl, xl, yl, yl), (zl, zl, 0, 0)
+    __shared__ __align__(16) float4 sm[4 * kTileM];
     const int64_t t0 = static_cast<int64_t>(blockIdx.x) * kThreads * T;
     const int64_t s0 = static_cast<int64_t>(blockIdx.y) * a.per_split;
     const int64_t s1 = std::min<int64_t>(a.ns, s0 + a.per_split);
-    float xt[T], yt[T], zt[T];
+    float2 nxh[H], nyh[H], nzh[H], nxl[H], nyl[H], nzl[H];   // targets, negated
     double acc[T];
 #pragma unroll
     for (int u = 0; u < T; ++u) {
         const int64_t t = std::min<int64_t>(t0 + threadIdx.x + kThreads * u, a.nt - 1);
-        xt[u] = __double2float_rn(a.tx[t]);
-        yt[u] = __double2float_rn(a.ty[t]);
-        zt[u] = __double2float_rn(a.tz[t]);
+        const float2 px = split_pair(a.tx[t]), py = split_pair(a.ty[t]), pz = split_pair(a.tz[t]);
+        if (u & 1) {
+            nxh[u / 2].y = -px.x; nxl[u / 2].y = -px.y;
+            nyh[u / 2].y = -py.x; nyl[u / 2].y = -py.y;
+            nzh[u / 2].y = -pz.x; nzl[u / 2].y = -pz.y;
+        } else {
+            nxh[u / 2].x = -px.x; nxl[u / 2].x = -px.y;
+            nyh[u / 2].x = -py.x; nyl[u / 2].x = -py.y;
+            nzh[u / 2].x = -pz.x; nzl[u / 2].x = -pz.y;
+        }
         acc[u] = 0.0;
     }
-    for (int64_t j0 = s0; j0 < s1; j0 += kTile32) {
-        const int m = static_cast<int>(std::min<int64_t>(kTile32, s1 - j0));
+    const float2 nkl2e = make_float2(a.neg_kappa_log2e, a.neg_kappa_log2e);
+    for (int64_t j0 = s0; j0 < s1; j0 += kTileM) {
+        const int m = static_cast<int>(std::min<int64_t>(kTileM, s1 - j0));
         __syncthreads();
-        for (int j = threadIdx.x; j < m; j += kThreads)
-            sm[j] = make_float4(__double2float_rn(a.sx[j0 + j]), __double2float_rn(a.sy[j0 + j]),
-                                __double2float_rn(a.sz[j0 + j]), __double2float_rn(a.sq[j0 + j]));
+        for (int j = threadIdx.x; j < m; j += kThreads) {
+            const float2 px = split_pair(a.sx[j0 + j]), py = split_pair(a.sy[j0 + j]);
+            const float2 pz = split_pair(a.sz[j0 + j]);
+            const float q = __double2float_rn(a.sq[j0 + j]);
+            sm[4 * j] = make_float4(px.x, px.x, py.x, py.x);
+            sm[4 * j + 1] = make_float4(pz.x, pz.x, q, q);
+            sm[4 * j + 2] = make_float4(px.y, px.y, py.y, py.y);
+            sm[4 * j + 3] = make_float4(pz.y, pz.y, 0.f, 0.f);
+        }
         __syncthreads();
         float hi[T], lo[T];
 #pragma unroll
         for (int u = 0; u < T; ++u) hi[u] = lo[u] = 0.f;
         for (int jb = 0; jb < m; jb += kBlock) {
             const int je = min(jb + kBlock, m);
-            float f[T];
+            float2 f[H];
 #pragma unroll
-            for (int u = 0; u < T; ++u) f[u] = 0.f;
+            for (int v = 0; v < H; ++v) f[v] = make_float2(0.f, 0.f);
 #pragma unroll 2
             for (int j = jb; j < je; ++j) {
-                const float4 s = sm[j];
+                const float4 h0 = sm[4 * j], h1 = sm[4 * j + 1], l0 = sm[4 * j + 2], l1 = sm[4 * j + 3];
+                const float2 sxh = make_float2(h0.x, h0.y), syh = make_float2(h0.z, h0.w);
+                const float2 szh = make_float2(h1.x, h1.y), sq = make_float2(h1.z, h1.w);
+                const float2 sxl = make_float2(l0.x, l0.y), syl = make_float2(l0.z, l0.w);
+                const float2 szl = make_float2(l1.x, l1.y);
 #pragma unroll
-                for (int u = 0; u < T; ++u) {
-                    const float dx = s.x - xt[u], dy = s.y - yt[u], dz = s.z - zt[u];
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float ri = rsqrt_approx(r2);
-                    ri = r2 > 0.f ? ri : 0.f;
-                    if (KER == BLTC_KERNEL_YUKAWA) ri *= ex2_approx(a.neg_kappa_log2e * (r2 * ri));
-                    f[u] = fmaf(s.w, ri, f[u]);
+                for (int v = 0; v < H; ++v) {
+                    const float2 dx = __fadd2_rn(__fadd2_rn(sxh, nxh[v]), __fadd2_rn(sxl, nxl[v]));
+                    const float2 dy = __fadd2_rn(__fadd2_rn(syh, nyh[v]), __fadd2_rn(syl, nyl[v]));
+                    const float2 dz = __fadd2_rn(__fadd2_rn(szh, nzh[v]), __fadd2_rn(szl, nzl[v]));
+                    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                    float2 ri = make_float2(r2.x > 0.f ? rsqrt_approx(r2.x) : 0.f,
+                                            r2.y > 0.f ? rsqrt_approx(r2.y) : 0.f);
+                    if (KER == BLTC_KERNEL_YUKAWA) {
+                        const float2 e = __fmul2_rn(nkl2e, __fmul2_rn(r2, ri));
+                        ri = __fmul2_rn(ri, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+                    }
+                    f[v] = __ffma2_rn(sq, ri, f[v]);
                 }
             }
 #pragma unroll
-            for (int u = 0; u < T; ++u) two_sum_add(hi[u], lo[u], f[u]);
+            for (int v = 0; v < H; ++v) {
+                two_sum_add(hi[2 * v], lo[2 * v], f[v].x);
+                two_sum_add(hi[2 * v + 1], lo[2 * v + 1], f[v].y);
+            }
         }
 #pragma unroll
         for (int u = 0; u < T; ++u) acc[u] += static_cast<double>(hi[u]) + static_cast<double>(lo[u]);
@@ -193,10 +234,10 @@ void direct_sum(Context* ctx, const double* tx, const double* ty, const double* 
     require(tx && ty && tz && sx && sy && sz && sq && phi, "direct: NULL pointer");
     cudaStream_t s = ctx->stream;
     const bool mixed = p.precision == BLTC_PRECISION_MIXED;
-    const int T = mixed ? 8 : 4;
+    const int T = 4;
     const int64_t tiles = ceil_div(nt, static_cast<int64_t>(kThreads) * T);
     const int64_t want = 4 * static_cast<int64_t>(std::max(1, ctx->sm_count));
-    const int64_t tile_src = mixed ? kTile32 : kTile64;
+    const int64_t tile_src = mixed ? kTileM : kTile64;
     int64_t splits = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, tiles), ceil_div(ns, tile_src)));
     splits = std::min<int64_t>(splits, 65535);
     const int64_t per = ceil_div(ceil_div(ns, splits), tile_src) * tile_src;
@@ -209,10 +250,10 @@ void direct_sum(Context* ctx, const double* tx, const double* ty, const double* 
     const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(splits));
     if (mixed) {
         if (p.kernel == BLTC_KERNEL_YUKAWA) {
-            k_direct_mixed<BLTC_KERNEL_YUKAWA, 8><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+            k_direct_mixed<BLTC_KERNEL_YUKAWA, 4><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
         }
         else {
-            k_direct_mixed<BLTC_KERNEL_COULOMB, 8><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
+            k_direct_mixed<BLTC_KERNEL_COULOMB, 4><<<grid, kThreads, 0, s>>>(a); ++ctx->launches;
         }
     } else {
         if (p.kernel == BLTC_KERNEL_YUKAWA) {
@@ -237,10 +278,10 @@ void direct_sum_noalloc(Context* ctx, const double* tx, const double* ty, const 
     double* scratch = direct_scratch_address(ctx->device);
     cudaStream_t s = ctx->stream;
     const bool mixed = p.precision == BLTC_PRECISION_MIXED;
-    const int T = mixed ? 8 : 4;
+    const int T = 4;
     const int64_t tiles = ceil_div(nt, static_cast<int64_t>(kThreads) * T);
     const int64_t want = 4 * static_cast<int64_t>(std::max(1, ctx->sm_count));
-    const int64_t tile_src = mixed ? kTile32 : kTile64;
+    const int64_t tile_src = mixed ? kTileM : kTile64;
     // as many source splits as the fixed scratch holds (splits * nt partial sums)
     int64_t splits = std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, tiles), ceil_div(ns, tile_src)));
     splits = std::min<int64_t>({splits, int64_t(65535), kNoAllocScratchDoubles / nt});
@@ -253,9 +294,9 @@ void direct_sum_noalloc(Context* ctx, const double* tx, const double* ty, const 
     const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(splits));
     if (mixed) {
         if (p.kernel == BLTC_KERNEL_YUKAWA)
-            k_direct_mixed<BLTC_KERNEL_YUKAWA, 8><<<grid, kThreads, 0, s>>>(a);
+            k_direct_mixed<BLTC_KERNEL_YUKAWA, 4><<<grid, kThreads, 0, s>>>(a);
         else
-            k_direct_mixed<BLTC_KERNEL_COULOMB, 8><<<grid, kThreads, 0, s>>>(a);
+            k_direct_mixed<BLTC_KERNEL_COULOMB, 4><<<grid, kThreads, 0, s>>>(a);
     } else {
         if (p.kernel == BLTC_KERNEL_YUKAWA)
             k_direct_fp64<BLTC_KERNEL_YUKAWA, 4><<<grid, kThreads, 0, s>>>(a);

@@ -191,6 +191,9 @@ void build_tree(Context* ctx, const double* x, const double* y, const double* z,
                 const double* q, int64_t n, int32_t max_leaf, Tree* out);
 void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int degree,
                  Lists* out);
+// The lists of the selected batches only (strictly increasing batch indices); the other
+// batches get empty lists.
+void select_lists(Context* ctx, const Lists* L, const int32_t* sel, int64_t n_sel, Lists* out);
 void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int degree,
                               int precision);
 // The upward pass in two parts: prepare_upward marks the clusters, allocates the modified
@@ -233,6 +236,9 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual);
 void prepare_plan(Context* ctx, Lists* L, int degree, int precision);
 // Kernel evaluations the sweep performs for that plan (mutual pairs counted once).
 int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision);
+// The sweep's cost model for that plan: evaluations with every batch padded to the target
+// slots its source groups run (the autotuner's screen).
+int64_t plan_slot_cost(Context* ctx, Lists* L, int degree, int precision);
 // The Hermite treecode's sweep (sweep.cu) and the whole solve (hermite.cu).
 void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
                       const double* qh64, const float* qh32, const int32_t* qslot, double* phi);

@@ -10,6 +10,9 @@
 // A first pass counts, a scan makes CSR offsets, a second pass fills the ids.  The MAC is
 // FP64 with IEEE-rounded intrinsics (no fused multiply-add; also --fmad=false), so the
 // lists are bit-identical to any other implementation of the same arithmetic.
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace bltc {
@@ -125,6 +128,18 @@ __global__ void k_append_total(int32_t* off, int64_t n, const int32_t* total) {
     off[n] = *total;
 }
 
+// Copies the list entries of the selected batches (one block per batch) to their places in
+// the new CSR arrays.
+__global__ void k_gather_lists(const int32_t* __restrict__ sel, int64_t n_sel,
+                               const int32_t* __restrict__ off_old, const int32_t* __restrict__ ids_old,
+                               const int32_t* __restrict__ off_new, int32_t* __restrict__ ids_new) {
+    for (int64_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
+        const int b = sel[i];
+        const int a0 = off_old[b], len = off_old[b + 1] - a0, o = off_new[b];
+        for (int k = threadIdx.x; k < len; k += blockDim.x) ids_new[o + k] = ids_old[a0 + k];
+    }
+}
+
 }  // namespace
 
 void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int degree,
@@ -184,6 +199,58 @@ void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int
     a.dir_ids = out->dir_ids.p;
     k_lists<true><<<grid_for(32 * nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("lists fill");
+}
+
+// The lists of some batches only: every other batch keeps an empty list (its targets get
+// phi = 0 from an evaluation).  Batches are listed in increasing order.
+void select_lists(Context* ctx, const Lists* L, const int32_t* sel, int64_t n_sel, Lists* out) {
+    const int64_t nb = L->n_batches;
+    require(n_sel >= 0 && (n_sel == 0 || sel != nullptr), "select: batches is NULL");
+    for (int64_t i = 0; i < n_sel; ++i) {
+        require(sel[i] >= 0 && sel[i] < nb, "select: batch index out of range");
+        require(i == 0 || sel[i] > sel[i - 1], "select: batches must be strictly increasing");
+    }
+    cudaStream_t s = ctx->stream;
+    std::vector<int32_t> ha(nb + 1), hd(nb + 1), na(nb + 1, 0), nd(nb + 1, 0);
+    BLTC_CUDA(cudaMemcpyAsync(ha.data(), L->app_off.p, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost, s));
+    BLTC_CUDA(cudaMemcpyAsync(hd.data(), L->dir_off.p, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost, s));
+    BLTC_CUDA(cudaStreamSynchronize(s));
+    std::vector<char> on(nb, 0);
+    for (int64_t i = 0; i < n_sel; ++i) on[sel[i]] = 1;
+    for (int64_t b = 0; b < nb; ++b) {
+        na[b + 1] = na[b] + (on[b] ? ha[b + 1] - ha[b] : 0);
+        nd[b + 1] = nd[b] + (on[b] ? hd[b + 1] - hd[b] : 0);
+    }
+    out->ctx = ctx;
+    out->serial = ctx->next_serial++;
+    out->bt = L->bt;
+    out->st = L->st;
+    out->theta = L->theta;
+    out->degree = L->degree;
+    out->n_batches = nb;
+    out->n_app = na[nb];
+    out->n_dir = nd[nb];
+    out->app_off = DBuf<int32_t>(ctx, nb + 1);
+    out->dir_off = DBuf<int32_t>(ctx, nb + 1);
+    out->app_ids = DBuf<int32_t>(ctx, out->n_app);
+    out->dir_ids = DBuf<int32_t>(ctx, out->n_dir);
+    DBuf<int32_t> dsel(ctx, n_sel);
+    BLTC_CUDA(cudaMemcpyAsync(out->app_off.p, na.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+    BLTC_CUDA(cudaMemcpyAsync(out->dir_off.p, nd.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+    if (n_sel > 0) {
+        BLTC_CUDA(cudaMemcpyAsync(dsel.p, sel, sizeof(int32_t) * n_sel, cudaMemcpyHostToDevice, s));
+        const unsigned g = static_cast<unsigned>(std::min<int64_t>(n_sel, 65535));
+        k_gather_lists<<<g, 256, 0, s>>>(dsel.p, n_sel, L->app_off.p, L->app_ids.p, out->app_off.p,
+                                         out->app_ids.p);
+        ++ctx->launches;
+        BLTC_LAUNCH_CHECK("select approximation lists");
+        k_gather_lists<<<g, 256, 0, s>>>(dsel.p, n_sel, L->dir_off.p, L->dir_ids.p, out->dir_off.p,
+                                         out->dir_ids.p);
+        ++ctx->launches;
+        BLTC_LAUNCH_CHECK("select direct lists");
+    }
+    // the host arrays above are read by the copies: wait for them before they go
+    BLTC_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace bltc

@@ -364,20 +364,32 @@ __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* 
     }
 }
 
+// out[0]: direct interactions, out[1]: approximation interactions, out[2]: direct kernel
+// evaluations (skipped mutual entries excluded), out[3]: the sweep's cost in target slots
+// (each batch's targets padded to its groups' passes, groups_for) times sources, a mutual
+// owner's entry weighted 5/4 for its second accumulation.
 __global__ void k_counts(const int32_t* b_leaves, const int32_t* b_count, const int32_t* s_count,
                          const int32_t* app_off, const int32_t* dir_off, const int32_t* dir_ids,
                          const uint8_t* dir_sel, int64_t n_batches, int64_t P, unsigned long long* out) {
     const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (b >= n_batches) return;
     const int64_t nb = b_count[b_leaves[b]];
-    int64_t d = 0, de = 0;
+    int64_t d = 0, de = 0, dw = 0;
     for (int e = dir_off[b]; e < dir_off[b + 1]; ++e) {
-        d += s_count[dir_ids[e]];
-        if (!dir_sel || !(dir_sel[e] & kSelSkip)) de += s_count[dir_ids[e]];
+        const int64_t c = s_count[dir_ids[e]];
+        d += c;
+        if (!dir_sel || !(dir_sel[e] & kSelSkip)) {
+            de += c;
+            dw += (dir_sel && (dir_sel[e] & kSelMutual)) ? c + c / 4 : c;
+        }
     }
+    const int64_t app = static_cast<int64_t>(app_off[b + 1] - app_off[b]) * P;
+    const int w = kThreads / groups_for(static_cast<int>(nb)) * kT;
+    const int64_t slots = (nb + w - 1) / w * w;
     atomicAdd(&out[0], static_cast<unsigned long long>(d * nb));
-    atomicAdd(&out[1], static_cast<unsigned long long>(static_cast<int64_t>(app_off[b + 1] - app_off[b]) * P * nb));
+    atomicAdd(&out[1], static_cast<unsigned long long>(app * nb));
     atomicAdd(&out[2], static_cast<unsigned long long>(de * nb));
+    atomicAdd(&out[3], static_cast<unsigned long long>((app + dw) * slots));
 }
 
 }  // namespace
@@ -747,20 +759,20 @@ void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
     }
 }
 
-static void counts(Context* ctx, const Lists* L, const uint8_t* dir_sel, int64_t* out3) {
-    DBuf<int64_t> w(ctx, 3);
-    BLTC_CUDA(cudaMemsetAsync(w.p, 0, 3 * sizeof(int64_t), ctx->stream));
+static void counts(Context* ctx, const Lists* L, const uint8_t* dir_sel, int64_t* out4) {
+    DBuf<int64_t> w(ctx, 4);
+    BLTC_CUDA(cudaMemsetAsync(w.p, 0, 4 * sizeof(int64_t), ctx->stream));
     const int64_t np1 = L->degree + 1;
     k_counts<<<grid_for(L->n_batches, 128), 128, 0, ctx->stream>>>(
         L->bt->leaves.p, L->bt->count.p, L->st->count.p, L->app_off.p, L->dir_off.p,
         L->dir_ids.p, dir_sel, L->n_batches, np1 * np1 * np1, reinterpret_cast<unsigned long long*>(w.p)); ++ctx->launches;
     BLTC_LAUNCH_CHECK("counts");
-    const int64_t* r = ctx->read_words(w.p, 3);
-    for (int i = 0; i < 3; ++i) out3[i] = r[i];
+    const int64_t* r = ctx->read_words(w.p, 4);
+    for (int i = 0; i < 4; ++i) out4[i] = r[i];
 }
 
 void interaction_counts(Context* ctx, const Lists* L, int64_t* n_dir, int64_t* n_app) {
-    int64_t r[3];
+    int64_t r[4];
     counts(ctx, L, nullptr, r);
     if (n_dir) *n_dir = r[0];
     if (n_app) *n_app = r[1];
@@ -769,9 +781,17 @@ void interaction_counts(Context* ctx, const Lists* L, int64_t* n_dir, int64_t* n
 int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision) {
     require(degree == L->degree, "evaluations: the lists were built for another degree");
     prepare_plan(ctx, L, degree, precision);
-    int64_t r[3];
+    int64_t r[4];
     counts(ctx, L, L->plan.dir_sel.p, r);
     return r[1] + r[2];
+}
+
+int64_t plan_slot_cost(Context* ctx, Lists* L, int degree, int precision) {
+    require(degree == L->degree, "cost: the lists were built for another degree");
+    prepare_plan(ctx, L, degree, precision);
+    int64_t r[4];
+    counts(ctx, L, L->plan.dir_sel.p, r);
+    return r[3];
 }
 
 }  // namespace bltc

@@ -167,13 +167,25 @@ struct Targets {
 };
 
 // Source groups.  A block is 256 threads x kT targets.  A batch of nb targets uses G groups
-// of 256/G threads (G = 1, 2, 4, 8 as nb shrinks below 256*kT, 128*kT, 64*kT): every group covers
-// all targets of the batch and takes every G-th block of work of each cluster (blocks of
-// kBlock sources in the near field, (k1, k2) rows of the proxy grid in the far field).  Each
-// group keeps its own partial potentials; they are added in group order at the end of the
-// item, so the result is fixed by the batch alone.
+// of 256/G threads (G = 1, 2, 4 or 8): every group covers all targets of the batch, in passes
+// of 2048/G targets, and takes every G-th block of work of each cluster (blocks of kBlock
+// sources in the near field, (k1, k2) rows of the proxy grid in the far field).  Each group
+// keeps its own partial potentials; they are added in group order at the end of the item, so
+// the result is fixed by the batch alone.  The last pass runs its padding slots like targets,
+// so G is the one with the fewest target slots, ceil(nb / (2048/G)) * 2048/G, the smallest G
+// on a tie: a batch of 1100 targets runs 1280 slots with G = 8 instead of 2048 with G = 1.
 __device__ __forceinline__ int groups_for(int nb) {
-    return nb > 128 * kT ? 1 : (nb > 64 * kT ? 2 : (nb > 32 * kT ? 4 : 8));
+    int best = 1, best_slots = (nb + kThreads * kT - 1) / (kThreads * kT) * (kThreads * kT);
+#pragma unroll
+    for (int G = 2; G <= 8; G *= 2) {
+        const int w = kThreads / G * kT;
+        const int slots = (nb + w - 1) / w * w;
+        if (slots < best_slots) {
+            best = G;
+            best_slots = slots;
+        }
+    }
+    return best;
 }
 
 // Close-pair screening per block of kBlock staged sources.  A source farther than tau from the

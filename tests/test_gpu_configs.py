@@ -44,7 +44,9 @@ def test_plummer_8e6_yukawa_autotuned(gpu):
     p = b.params(8, 0.8, 2000, 2000, b.BLTC_KERNEL_YUKAWA, 0.5, b.BLTC_PRECISION_MIXED)
     best, ms = b.bltc_autotune(gpu.h, *X, p, leaf=(500, 1000, 2000, 3000, 4000), repeats=1)
     assert best.leaf_size in (500, 1000, 2000, 3000, 4000) and best.batch_size == best.leaf_size
-    assert ms[(best.leaf_size, best.batch_size)] == min(ms.values())
+    timed = {k: v for k, v in ms.items() if v == v}      # the screen's contenders
+    if timed:
+        assert ms[(best.leaf_size, best.batch_size)] == min(timed.values())
     again, _ = b.bltc_autotune(gpu.h, *X, p)          # cached: no timing
     assert again.leaf_size == best.leaf_size
     leaf = best.leaf_size

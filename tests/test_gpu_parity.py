@@ -223,6 +223,8 @@ CASES = [
     ("plummer", 40000, 400, 400, 0.8, 6, 1, 0.5),     # uneven tree
     ("cube", 50000, 3000, 3000, 0.7, 2, 0, 0.0),      # > 2048 targets and sources per tile
     ("cube", 3001, 64, 64, 0.9, 1, 0, 0.0),           # degree 1
+    ("cube", 10000, 1500, 1500, 0.7, 5, 0, 0.0),      # batches of 1100-1500: several passes of
+    ("plummer", 20000, 1500, 1500, 0.8, 4, 1, 0.3),   # 256 or 512 targets (4 or 8 source groups)
     ("cube", 7, 2, 2, 0.5, 3, 0, 0.0),                # tiny
     ("cube", 1, 1, 1, 0.7, 4, 1, 0.5),                # a single particle: phi = 0
 ]
@@ -331,6 +333,79 @@ def test_step_api_matches_solve_and_stats(gpu):
     b.bltc_tree_destroy(st)
 
 
+def test_selected_batches(gpu):
+    # The lists of some batches only (the error of Eq. 16 on a sample of targets, Sec. IV):
+    # FP64 gives bit for bit the full solve's potentials there and 0 elsewhere, and matches
+    # the oracle's Algorithm 1 on the same batches; mixed stays within the mixed bar.
+    import torch
+    x, y, z, q = system("cube", 30000, 12)
+    X = dev(x, y, z, q)
+    st = b.bltc_tree_build(gpu.h, *X, 1000)
+    ot = oracle.Tree(x, y, z, 1000)
+    pick = np.array([0, 5, len(ot.leaves) // 2, len(ot.leaves) - 1])
+    idx = batch_targets(ot, pick)
+    rest = np.setdiff1d(np.arange(len(x)), idx)
+    want, want_abs = _oracle(x, y, z, q, b.params(6, 0.7, 1000, precision=0), pick)
+    try:
+        for prec in (b.BLTC_PRECISION_FP64, b.BLTC_PRECISION_MIXED):
+            p = b.params(6, 0.7, 1000, precision=prec)
+            L = b.bltc_lists_build(gpu.h, st, st, p)
+            S = b.bltc_lists_select(gpu.h, L, pick)
+            info = b.bltc_lists_info(S)
+            lw = oracle.lists(ot, ot, 0.7, 6)
+            assert info["n_approx"] == sum(lw["approx_off"][i + 1] - lw["approx_off"][i] for i in pick)
+            b.bltc_modified_charges(gpu.h, st, S, p)
+            phi = torch.empty_like(X[0])
+            b.bltc_evaluate(gpu.h, S, st, st, p, phi)
+            torch.cuda.synchronize()
+            got, full = host(phi), gpu_solve(gpu, x, y, z, q, p)
+            assert not np.any(got[rest])
+            if prec == b.BLTC_PRECISION_FP64:
+                assert np.array_equal(got[idx], full[idx])
+                assert_close_abs(want[idx], got[idx], want_abs[idx], FP64_REL2, FP64_ELEM, "selected fp64")
+            else:
+                assert_close_abs(full[idx], got[idx], want_abs[idx], MIXED_REL2, MIXED_ELEM, "selected mixed")
+            for bad in ([3, 2], [0, len(ot.leaves)], [-1]):
+                with pytest.raises(b.BltcError) as e:
+                    b.bltc_lists_select(gpu.h, L, bad)
+                assert e.value.status == b.BLTC_ERR_ARG
+            b.bltc_lists_destroy(S)
+            b.bltc_lists_destroy(L)
+    finally:
+        b.bltc_tree_destroy(st)
+
+
+def test_autotune_screen_and_never_slower(gpu):
+    # The autotuner's screen counts every candidate's padded work; duplicates (the same trees)
+    # are one candidate; the choice is never slower than the default N_L = N_B = 2000.
+    import torch
+    x, y, z, q = system("plummer", 400000, 20031905)
+    X = dev(x, y, z, q)
+    p = b.params(6, 0.8, 2000, 2000, b.BLTC_KERNEL_COULOMB, 0.0, b.BLTC_PRECISION_MIXED)
+    cands = (250, 500, 1000, 2000, 2000, 4000)
+    best, ms = b.bltc_autotune(gpu.h, *X, p, leaf=cands, repeats=2, use_cache=False)
+    assert best.leaf_size in cands and best.batch_size == best.leaf_size
+    phi = torch.empty_like(X[0])
+
+    def fastest(pp):
+        ts = []
+        for _ in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.bltc_solve(gpu.h, *X, pp, phi)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts[1:])
+    t_best, t_default = fastest(best), fastest(p)
+    assert t_best <= 1.1 * t_default, (best.leaf_size, t_best, t_default, ms)
+    # its potentials are the solve's at that size, within the bars against FP64
+    got = gpu_solve(gpu, x, y, z, q, best)
+    ref = gpu_solve(gpu, x, y, z, q, b.params(6, 0.8, best.leaf_size, best.batch_size,
+                                              b.BLTC_KERNEL_COULOMB, 0.0, b.BLTC_PRECISION_FP64))
+    assert oracle.rel_err(ref, got) <= MIXED_REL2
+
+
 def test_solve_host_matches_device(gpu):
     x, y, z, q = system("cube", 20000, 6)
     p = b.params(6, 0.7, 1000)
@@ -353,7 +428,8 @@ def test_invalid_parameters_rejected(gpu, bad):
 
 # ---- direct sum (the GPU baseline) --------------------------------------------------------
 
-@pytest.mark.parametrize("nt,ns,ker", [(3000, 3000, 0), (2047, 5001, 1), (1, 17, 0), (40000, 40000, 0)])
+@pytest.mark.parametrize("nt,ns,ker", [(3000, 3000, 0), (2047, 5001, 1), (1, 17, 0), (40000, 40000, 0),
+                                      (200000, 200000, 0), (100000, 100000, 1)])
 def test_direct_sum(gpu, nt, ns, ker):
     import torch
     xs = system("cube", max(nt, ns), nt + ns)
@@ -366,11 +442,35 @@ def test_direct_sum(gpu, nt, ns, ker):
     else:
         pick = np.arange(nt)
     ref, ref_abs = oracle.direct_sum(np.stack(t)[:, pick], np.stack(s), q, ker, 0.5, with_abs=True)
-    for prec, r2, el in ((0, 1e-14, 1e-14), (1, 1e-6, 1e-5)):
+    # FP64: summation order and rsqrt() against 1/sqrt only, the treecode's FP64 bar; MIXED:
+    # the mixed bar (FP32 coordinate pairs keep every distance to FP32 precision)
+    for prec, r2, el in ((0, FP64_REL2, FP64_ELEM), (1, MIXED_REL2, MIXED_ELEM)):
         phi = torch.empty_like(T[0])
         b.bltc_direct_sum(gpu.h, *T, *S, Q, b.params(4, 0.5, 10, kernel=ker, kappa=0.5, precision=prec), phi)
         got = host(phi)[pick]
         assert_close_abs(ref, got, ref_abs, r2, el, f"direct prec={prec}")
+
+
+def test_direct_sum_close_pairs_mixed(gpu):
+    # Near-duplicates 1e-9..1e-5 apart: the FP32 coordinate pairs keep their distance to
+    # FP32 precision (the highs of a close pair subtract exactly), so the mixed direct sum
+    # stays within the mixed bar where single FP32 coordinates would lose every digit.
+    import torch
+    rng = np.random.default_rng(20031907)
+    x, y, z, q = system("cube", 100000, 20031907)
+    k = 3000
+    pick = rng.choice(len(x), k, replace=False)
+    d = rng.normal(size=(3, k))
+    d *= (10 ** rng.uniform(-9, -5, k)) / np.linalg.norm(d, axis=0)
+    X = [np.concatenate([x, x[pick] + d[0]]), np.concatenate([y, y[pick] + d[1]]),
+         np.concatenate([z, z[pick] + d[2]])]
+    Q = np.concatenate([q, rng.uniform(-1, 1, k)])
+    sel = np.concatenate([pick[:500], len(x) + np.arange(500), np.arange(0, len(x), 211)])
+    ref, ref_abs = oracle.direct_sum(np.stack(X)[:, sel], np.stack(X), Q, with_abs=True)
+    D = dev(*X, Q)
+    phi = torch.empty_like(D[0])
+    b.bltc_direct_sum(gpu.h, *D[:3], *D[:3], D[3], b.params(4, 0.5, 10, precision=1), phi)
+    assert_close_abs(ref, host(phi)[sel], ref_abs, MIXED_REL2, MIXED_ELEM, "direct close pairs")
 
 
 # ---- the full-size workload, sampled ------------------------------------------------------
