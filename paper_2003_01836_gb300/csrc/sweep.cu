@@ -24,6 +24,7 @@
 // A pair with r^2 == 0 (a target meeting itself) is skipped; for the far field theta < 1
 // keeps every proxy point away from every target, so no test is needed there.
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "internal.cuh"
@@ -40,18 +41,23 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_mixed(SweepArgs 
 }
 
 // Several requests' sweeps in one persistent launch (the serving engine).  `order` lists
-// (request, item) pairs longest first; each block copies the request's arguments to shared
-// memory when the request changes.  An item computes exactly what it computes in a
-// single-request launch, so every request's potentials are the same bits alone or in a mix.
+// (request, item) pairs longest first.  The requests' arguments travel in the kernel's
+// parameter space (a __grid_constant__ array read through the constant cache), as a single
+// request's do.  An item computes exactly what it computes in a single-request launch, so
+// every request's potentials are the same bits alone or in a mix.
+constexpr int kMultiMax = 64;      // requests per launch: 64 argument sets fit the 32 KB parameter space
+struct MultiArgs {
+    SweepArgs r[kMultiMax];
+};
+static_assert(sizeof(MultiArgs) + 64 <= 32764, "the multi-request arguments must fit the kernel parameter space");
+
 template <int KER>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_multi(const SweepArgs* __restrict__ reqs,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_multi(const __grid_constant__ MultiArgs m,
                                                              const int2* __restrict__ order,
                                                              int total, unsigned int* counter) {
     extern __shared__ __align__(16) float4 sm_dyn[];
     float4* sm = sm_dyn;
-    __shared__ __align__(16) SweepArgs s_a;
     __shared__ int s_item;
-    int cur = -1;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(counter, 1u));
@@ -59,14 +65,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_multi(const Swee
         const int i = s_item;
         if (i >= total) return;
         const int2 o = order[i];
-        if (o.x != cur) {
-            const int* src = reinterpret_cast<const int*>(reqs + o.x);
-            int* dst = reinterpret_cast<int*>(&s_a);
-            for (int w = threadIdx.x; w < static_cast<int>(sizeof(SweepArgs) / sizeof(int)); w += kThreads) dst[w] = src[w];
-            cur = o.x;
-            __syncthreads();
-        }
-        item_mixed<KER>(s_a, s_a.items[o.y], sm);
+        const SweepArgs& a = m.r[o.x];
+        item_mixed<KER>(a, a.items[o.y], sm);
     }
 }
 
@@ -690,14 +690,10 @@ void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
     cudaStream_t s = ctx->stream;
     const int R = static_cast<int>(jobs.size());
     std::vector<DBuf<double>> partials, mparts;
-    std::vector<SweepArgs> args;
     partials.reserve(jobs.size());
     mparts.reserve(jobs.size());
-    args.reserve(jobs.size());
     DBuf<unsigned int> counter(ctx, 1);
     BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
-    // global longest-first order over all requests' items
-    std::vector<std::pair<int64_t, int2>> all;
     for (int r = 0; r < R; ++r) {
         const SweepJob& j = jobs[static_cast<size_t>(r)];
         require(j.p.precision == BLTC_PRECISION_MIXED, "serving runs the mixed-precision sweep");
@@ -708,44 +704,54 @@ void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
         const Plan& pl = j.L->plan;
         partials.emplace_back(ctx, pl.partial_len);
         mparts.emplace_back(ctx, pl.mutual ? pl.mpart_len : 0);
-        args.push_back(make_args(ctx, j.L, j.bt, j.st, j.p, partials.back().p, counter.p));
-        args.back().mpart = pl.mutual ? mparts.back().p : nullptr;
-        for (int64_t i = 0; i < pl.n_items; ++i)
-            all.push_back({pl.h_cost[static_cast<size_t>(i)], make_int2(r, static_cast<int>(i))});
     }
-    std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int2>& x,
-                                                const std::pair<int64_t, int2>& y) { return x.first > y.first; });
-    // one persistent launch per kernel type present (each instantiation keeps its registers)
-    std::vector<int2> order[2];
-    for (const auto& pr : all) order[jobs[static_cast<size_t>(pr.second.x)].p.kernel == BLTC_KERNEL_YUKAWA].push_back(pr.second);
-    DBuf<SweepArgs> d_args(ctx, R);
-    DBuf<int2> d_order(ctx, static_cast<int64_t>(all.size()));
-    DBuf<unsigned int> counter2(ctx, 1);
-    BLTC_CUDA(cudaMemsetAsync(counter2.p, 0, sizeof(unsigned int), s));
-    BLTC_CUDA(cudaMemcpyAsync(d_args.p, args.data(), sizeof(SweepArgs) * R, cudaMemcpyHostToDevice, s));
-    if (!order[0].empty())
-        BLTC_CUDA(cudaMemcpyAsync(d_order.p, order[0].data(), sizeof(int2) * order[0].size(), cudaMemcpyHostToDevice, s));
-    if (!order[1].empty())
-        BLTC_CUDA(cudaMemcpyAsync(d_order.p + order[0].size(), order[1].data(), sizeof(int2) * order[1].size(),
-                                  cudaMemcpyHostToDevice, s));
-    // the host vectors must outlive the asynchronous copies
-    BLTC_CUDA(cudaStreamSynchronize(s));
     const int64_t cap = kMinBlocks * static_cast<int64_t>(std::max(1, ctx->sm_count));
-    if (!order[0].empty()) {
-        const int total = static_cast<int>(order[0].size());
-        BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_COULOMB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
-        k_sweep_multi<BLTC_KERNEL_COULOMB><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, kMixedSmem, s>>>(
-            d_args.p, d_order.p, total, counter.p); ++ctx->launches;
-        BLTC_LAUNCH_CHECK("sweep multi coulomb");
-    }
-    if (!order[1].empty()) {
-        const int total = static_cast<int>(order[1].size());
-        BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_YUKAWA>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
-        k_sweep_multi<BLTC_KERNEL_YUKAWA><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, kMixedSmem, s>>>(
-            d_args.p, d_order.p + order[0].size(), total, counter2.p); ++ctx->launches;
-        BLTC_LAUNCH_CHECK("sweep multi yukawa");
+    // up to kMultiMax requests per launch; within a launch, items longest first over all of
+    // its requests, one persistent launch per kernel type present
+    for (int r0 = 0; r0 < R; r0 += kMultiMax) {
+        const int r1 = std::min(R, r0 + kMultiMax);
+        std::unique_ptr<MultiArgs> m(new MultiArgs());
+        std::vector<std::pair<int64_t, int2>> all;
+        for (int r = r0; r < r1; ++r) {
+            const SweepJob& j = jobs[static_cast<size_t>(r)];
+            const Plan& pl = j.L->plan;
+            SweepArgs& sa = m->r[r - r0];
+            sa = make_args(ctx, j.L, j.bt, j.st, j.p, partials[static_cast<size_t>(r)].p, counter.p);
+            sa.mpart = pl.mutual ? mparts[static_cast<size_t>(r)].p : nullptr;
+            for (int64_t i = 0; i < pl.n_items; ++i)
+                all.push_back({pl.h_cost[static_cast<size_t>(i)], make_int2(r - r0, static_cast<int>(i))});
+        }
+        std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int2>& x,
+                                                    const std::pair<int64_t, int2>& y) { return x.first > y.first; });
+        std::vector<int2> order[2];
+        for (const auto& pr : all)
+            order[jobs[static_cast<size_t>(r0 + pr.second.x)].p.kernel == BLTC_KERNEL_YUKAWA].push_back(pr.second);
+        DBuf<int2> d_order(ctx, static_cast<int64_t>(all.size()));
+        DBuf<unsigned int> counters(ctx, 2);
+        BLTC_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned int), s));
+        if (!order[0].empty())
+            BLTC_CUDA(cudaMemcpyAsync(d_order.p, order[0].data(), sizeof(int2) * order[0].size(), cudaMemcpyHostToDevice, s));
+        if (!order[1].empty())
+            BLTC_CUDA(cudaMemcpyAsync(d_order.p + order[0].size(), order[1].data(), sizeof(int2) * order[1].size(),
+                                      cudaMemcpyHostToDevice, s));
+        if (!order[0].empty()) {
+            const int total = static_cast<int>(order[0].size());
+            BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_COULOMB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+            k_sweep_multi<BLTC_KERNEL_COULOMB><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, kMixedSmem, s>>>(
+                *m, d_order.p, total, counters.p); ++ctx->launches;
+            BLTC_LAUNCH_CHECK("sweep multi coulomb");
+        }
+        if (!order[1].empty()) {
+            const int total = static_cast<int>(order[1].size());
+            BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_YUKAWA>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+            k_sweep_multi<BLTC_KERNEL_YUKAWA><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, kMixedSmem, s>>>(
+                *m, d_order.p + order[0].size(), total, counters.p + 1); ++ctx->launches;
+            BLTC_LAUNCH_CHECK("sweep multi yukawa");
+        }
+        // the host order vectors must outlive the asynchronous copies
+        BLTC_CUDA(cudaStreamSynchronize(s));
     }
     for (int r = 0; r < R; ++r) {
         const SweepJob& j = jobs[static_cast<size_t>(r)];

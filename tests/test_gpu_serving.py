@@ -49,6 +49,22 @@ def test_served_results_equal_solo(gpu):
         srv.close()
 
 
+def test_more_requests_in_a_sweep_than_one_launch_holds(gpu):
+    # 80 small requests ready together with max_batch 100: the merged sweep runs them in
+    # launches of at most 64 argument sets, and every result is still its solo solve's bits
+    reqs = _requests(80, 5, nmax_exp=3.3)
+    solo = [gpu_solve(gpu, *r) for r in reqs]
+    srv = b.Server(0, setup_workers=4, max_batch=100, linger_us=2_000_000)
+    try:
+        tickets = [srv.submit(*r) for r in reqs]
+        for i, (t, ref) in enumerate(zip(tickets, solo)):
+            st, phi, _ = srv.wait(t)
+            assert st == b.BLTC_OK and np.array_equal(phi, ref), i
+        assert srv.stats()["max_batch"] > 64
+    finally:
+        srv.close()
+
+
 def test_served_small_requests_match_oracle(gpu):
     reqs = [r for r in _requests(10, 2, nmax_exp=3.7)][:6]
     srv = b.Server(0, setup_workers=2, max_batch=8)
