@@ -41,6 +41,15 @@ WORKLOAD = dict(kind="cube", n=1_000_000, theta=0.7, degree=8, leaf=2000, batch=
                 kernel=0, kappa=0.0, seed=20031838)
 WORKLOAD_NAME = ("uniform cube N=1e6 (q in [-1,1]), Coulomb, theta=0.7, n=8, N_L=N_B=2000, "
                  "mixed FP32 evaluation / FP64 accumulation")
+
+
+def workload_name(w):
+    """The workload's description, with any size or theta override spelled out."""
+    if w["n"] == WORKLOAD["n"] and w["theta"] == WORKLOAD["theta"]:
+        return WORKLOAD_NAME
+    return (f"uniform cube N={w['n']} (q in [-1,1]), Coulomb, theta={w['theta']}, n={w['degree']}, "
+            f"N_L=N_B={w['leaf']}, mixed FP32 evaluation / FP64 accumulation (override of the "
+            f"1e6 workload)")
 # Roofline of the sweep: one interaction of the Coulomb kernel costs one MUFU.RSQ; the SFU
 # (XU) pipe issues 16 per clock per SM, so the peak interaction rate is SMs * 16 * f_max.
 XU_PER_CLK_PER_SM = 16
@@ -283,6 +292,8 @@ def run_ours(args, dist: Dist):
     w = dict(WORKLOAD)
     if args.n:
         w["n"] = args.n
+    if args.theta >= 0:
+        w["theta"] = args.theta
     x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"] + dist.rank)
     X = [torch.from_numpy(a).to(f"cuda:{dev}") for a in (x, y, z, q)]
     phi = torch.empty_like(X[0])
@@ -348,7 +359,7 @@ def run_ours(args, dist: Dist):
            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": agg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 (f64 accumulation)", "data": "synthetic",
-           "config": {"workload": WORKLOAD_NAME, "n_particles": w["n"], "theta": w["theta"],
+           "config": {"workload": workload_name(w), "n_particles": w["n"], "theta": w["theta"],
                       "degree": w["degree"], "leaf_size": w["leaf"], "batch_size": w["batch"],
                       "kernel": "coulomb", "precision": "mixed", "batches": n_batches,
                       "parallelism": f"replicas x{dist.world}",
@@ -367,6 +378,12 @@ def run_ours(args, dist: Dist):
         out["error"] = check_errors(ctx, b, X, p, w, phi)
     if not args.no_e2e:
         out["e2e"] = run_e2e(ctx, b, x, y, z, q, p, args, dist, w)
+    if not args.no_serving:
+        sv = serve_measure(args.serve_record_requests, (0.5,), args.serve_workers, dist,
+                           args.serve_slice_us)
+        out["serving"] = {"requests": sv["config"]["requests"], "total_targets": sv["config"]["total_targets"],
+                          "mix": sv["config"]["mix"], "slice_us": sv["config"]["slice_us"], "levels": sv["levels"], "solo": sv["solo"],
+                          "served_vs_solo": sv["served_vs_solo"]}
     if not args.no_configs:
         out["configs"] = {}
         for key in args.configs.split(","):
@@ -653,13 +670,22 @@ def serve_solo_time(reqs, data, dist):
 
 
 def run_serving(args, dist: Dist):
+    from paper_2003_01836_gb300 import build
+    build.build()
+    return serve_measure(args.serve_requests, (0.5, 0.8, 1.0), args.serve_workers, dist,
+                         args.serve_slice_us)
+
+
+def serve_measure(count, fractions, workers, dist, slice_us=10000):
+    """The serving runtime on the first `count` requests of the stream: all at once
+    (saturated), then Poisson arrivals at each fraction of that rate; every request is also
+    solved alone for the comparison."""
     import concurrent.futures as cf
     import threading
 
     import paper_2003_01836_gb300 as b
-    from paper_2003_01836_gb300 import build, inputs
-    build.build()
-    reqs = serve_requests(args.serve_requests)
+    from paper_2003_01836_gb300 import inputs
+    reqs = serve_requests(count)
 
     def make(r):
         kind, n, sd, _ = r
@@ -668,7 +694,7 @@ def run_serving(args, dist: Dist):
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         data = list(ex.map(make, reqs))
     total_targets = sum(r[1] for r in reqs)
-    srv = b.Server(dist.local_rank, setup_workers=args.serve_workers, max_batch=64)
+    srv = b.Server(dist.local_rank, setup_workers=workers, max_batch=64, slice_us=slice_us)
     try:
         # warm-up: a few requests
         for i in range(min(8, len(reqs))):
@@ -706,7 +732,7 @@ def run_serving(args, dist: Dist):
         wall, lat = run_load(None)
         x_req = len(reqs) / wall
         runs = [("saturated (all submitted at t=0)", None, wall, lat)]
-        for frac in (0.5, 0.8, 1.0):
+        for frac in fractions:
             wall_f, lat_f = run_load(frac * x_req)
             runs.append((f"Poisson at {frac:.1f} x saturated rate", frac * x_req, wall_f, lat_f))
         stats = srv.stats()
@@ -730,7 +756,7 @@ def run_serving(args, dist: Dist):
                        "total_targets": total_targets,
                        "mix": "N log-uniform [1e3,1e6]; cube|Plummer; Coulomb|Yukawa kappa U[0.1,1]; "
                               "theta U[0.5,0.8]; n in {4,6,8,10}; N_L=N_B=2000; mixed",
-                       "setup_workers": args.serve_workers, "max_batch": 64},
+                       "setup_workers": workers, "max_batch": 64, "slice_us": slice_us},
             "levels": levels,
             "solo": {"seconds": solo, "targets_per_s": total_targets / solo,
                      "p50_ms": float(np.percentile(solo_each, 50) * 1e3),
@@ -764,6 +790,8 @@ def run_variant(args, dist: Dist):
     w = dict(WORKLOAD)
     if args.n:
         w["n"] = args.n
+    if args.theta >= 0:
+        w["theta"] = args.theta
     x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"] + dist.rank)
     X = [torch.from_numpy(a).to(f"cuda:{dev}") for a in (x, y, z, q)]
     phi = torch.empty_like(X[0])
@@ -807,7 +835,7 @@ def run_variant(args, dist: Dist):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 (f64 accumulation and interpolation)", "data": "synthetic",
-           "config": {"workload": f"{name} variant on " + WORKLOAD_NAME, "n_particles": w["n"],
+           "config": {"workload": f"{name} variant on " + workload_name(w), "n_particles": w["n"],
                       "theta": w["theta"], "degree": w["degree"], "leaf_size": w["leaf"],
                       "batch_size": w["batch"], "kernel": "coulomb", "precision": "mixed",
                       "l2": "flushed before every timed step (256 MiB device write)"},
@@ -854,6 +882,8 @@ def run_graph(args, dist: Dist):
     w = dict(WORKLOAD)
     if args.n:
         w["n"] = args.n
+    if args.theta >= 0:
+        w["theta"] = args.theta
     x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"] + dist.rank)
     X = [torch.from_numpy(a).to(f"cuda:{dev}") for a in (x, y, z, q)]
     charges = [X[3].clone(), torch.from_numpy(np.random.default_rng(20031836 + dist.rank)
@@ -897,7 +927,7 @@ def run_graph(args, dist: Dist):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 (f64 accumulation)", "data": "synthetic",
-           "config": {"workload": "solve replayed as one CUDA graph on " + WORKLOAD_NAME, "n_particles": w["n"],
+           "config": {"workload": "solve replayed as one CUDA graph on " + workload_name(w), "n_particles": w["n"],
                       "theta": w["theta"], "degree": w["degree"], "leaf_size": w["leaf"],
                       "batch_size": w["batch"], "kernel": "coulomb", "precision": "mixed",
                       "l2": "flushed before every timed step (256 MiB device write)"},
@@ -930,6 +960,8 @@ def run_reference(args, dist: Dist):
     w = dict(WORKLOAD)
     if args.n:
         w["n"] = args.n
+    if args.theta >= 0:
+        w["theta"] = args.theta
     x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"])
     cores = os.cpu_count() or 1
     prep = oracle.Prepared(x, y, z, q, w["theta"], w["degree"], w["leaf"], w["batch"],
@@ -963,7 +995,7 @@ def run_reference(args, dist: Dist):
             "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME.replace("mixed FP32 evaluation / FP64 accumulation",
+            "config": {"workload": workload_name(w).replace("mixed FP32 evaluation / FP64 accumulation",
                                                          "FP64 CPU oracle"),
                        "n_particles": w["n"], "theta": w["theta"], "degree": w["degree"],
                        "leaf_size": w["leaf"], "batch_size": w["batch"]},
@@ -981,6 +1013,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=0, help="override the particle count (smoke runs)")
+    ap.add_argument("--theta", type=float, default=-1.0,
+                    help="override theta of the main workload (profiling: 0 makes the sweep all near field)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -996,6 +1030,12 @@ def main(argv=None):
                          "barycentric Hermite (n = 4) variant on the same workload instead; "
                          "graph: replays with fixed positions and new charges")
     ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-slice-us", type=int, default=10000,
+                    help="serving engine slice length in microseconds (0: all ready work at once)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving sub-record of the default run")
+    ap.add_argument("--serve-record-requests", type=int, default=1024,
+                    help="requests of the default run's serving sub-record")
     ap.add_argument("--serve-workers", type=int, default=3)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":

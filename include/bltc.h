@@ -396,9 +396,10 @@ bltc_status bltc_direct_sum_noalloc(bltc_context* ctx, const double* tx, const d
  * of Algorithm 1 in mixed precision (targets = sources).  Requests are admitted in
  * arrival order while their estimated device memory fits the HBM budget; setup workers
  * (host threads with their own streams) build each admitted request's tree, lists,
- * modified charges and work plan; one engine merges the far/near sweeps of all prepared
- * requests into one persistent launch (work items of all requests, longest first), then
- * finalizes each request and copies its potentials out.  Setup of later requests overlaps
+ * modified charges and work plan; one engine merges the far/near sweeps of the prepared
+ * requests into persistent launches (work items of all their requests, longest first), in
+ * slices of about slice_us microseconds that favour the requests with the least remaining
+ * work, then finalizes each request and copies its potentials out.  Setup of later requests overlaps
  * the running sweep.  A request's potentials are bit-identical to bltc_solve of that
  * request alone, whatever else is in flight. */
 
@@ -407,17 +408,22 @@ typedef struct bltc_server bltc_server;
 typedef struct bltc_server_config {
     int32_t device;           /* CUDA device */
     int32_t setup_workers;    /* host threads preparing requests, 1..64 */
-    int32_t max_batch;        /* most requests merged into one sweep launch, >= 1 */
+    int32_t max_batch;        /* most requests one slice takes work from, >= 1 */
     int32_t linger_us;        /* batching window, >= 0: with fewer than max_batch requests
                                * ready while others are still being prepared, the engine
                                * waits up to this many microseconds for them before it
                                * launches (0: launch at once) */
     int64_t hbm_budget_bytes; /* device bytes admitted requests may reserve; 0 = 80% of free */
+    int32_t slice_us;         /* >= 0: the engine runs the ready work in slices of about this
+                               * many microseconds, the requests with the least remaining work
+                               * first, so a request that arrives during a large sweep starts
+                               * at the next slice; 0: all ready work in one slice */
+    int32_t reserved;         /* must be 0 */
 } bltc_server_config;
 
 typedef struct bltc_request_info {
     int32_t status;           /* bltc_status of the request */
-    int32_t batch;            /* requests in the sweep launch it ran in */
+    int32_t batch;            /* requests in the last slice it ran in */
     int64_t bytes_reserved;   /* device bytes reserved for it at admission */
     double t_submit, t_admit, t_ready, t_done;   /* host monotonic clock, seconds */
 } bltc_request_info;

@@ -63,7 +63,8 @@ def params(degree=8, theta=0.7, leaf_size=2000, batch_size=None, kernel=BLTC_KER
 class bltc_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("setup_workers", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("linger_us", ctypes.c_int32),
-                ("hbm_budget_bytes", ctypes.c_int64)]
+                ("hbm_budget_bytes", ctypes.c_int64), ("slice_us", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class bltc_request_info(ctypes.Structure):
@@ -513,9 +514,10 @@ def bltc_autotune(ctx, x, y, z, q, p: bltc_params, leaf=(500, 1000, 2000, 3000, 
 
 # ---- serving -------------------------------------------------------------------------
 
-def bltc_server_create(device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0, linger_us=0):
+def bltc_server_create(device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0, linger_us=0,
+                       slice_us=10000):
     cfg = bltc_server_config(int(device), int(setup_workers), int(max_batch), int(linger_us),
-                             int(hbm_budget_bytes))
+                             int(hbm_budget_bytes), int(slice_us), 0)
     h = ctypes.c_void_p()
     st = lib().bltc_server_create(ctypes.byref(cfg), ctypes.byref(h))
     if st != BLTC_OK:
@@ -568,8 +570,10 @@ def bltc_server_destroy(server):
 class Server:
     """Owns a serving runtime; keeps each request's host arrays alive until it is waited."""
 
-    def __init__(self, device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0, linger_us=0):
-        self.h = bltc_server_create(device, setup_workers, max_batch, hbm_budget_bytes, linger_us)
+    def __init__(self, device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0, linger_us=0,
+                 slice_us=10000):
+        self.h = bltc_server_create(device, setup_workers, max_batch, hbm_budget_bytes, linger_us,
+                                    slice_us)
         self._keep = {}
 
     def submit(self, x, y, z, q, p, phi=None):

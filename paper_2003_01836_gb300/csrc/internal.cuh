@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -223,7 +224,8 @@ void evaluate(Context* ctx, Lists* lists, const Tree* bt, const Tree* st,
 // evaluate in parts: the work plan (prepare_plan), the sweep's scratch, and the launches
 // alone (run_sweep: no allocation, no synchronisation), for capture in a graph.
 struct SweepBuffers {
-    DBuf<double> partials, mpart;
+    DBuf<double> partials;
+    DBuf<float> mpart;
     DBuf<unsigned int> counter;
 };
 void alloc_sweep_buffers(Context* ctx, const Lists* lists, SweepBuffers* b);
@@ -268,9 +270,35 @@ struct SweepJob {
     bltc_params p;
     double* phi;
 };
-// Mixed-precision sweep of several prepared requests in one persistent launch, then each
-// request's finalize; results are identical to evaluate() of each request alone.
-void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs);
+// Mixed-precision sweeps of several prepared requests, in slices (the serving engine).  A
+// request is added when it is ready; run_slice launches work items worth about `budget`
+// interactions (all of them when budget <= 0), taken from the requests with the least
+// remaining work first, at most max_requests of them, as persistent launches of at most 64
+// requests each, then the finalize of every request whose items have all run, and returns
+// those requests' tags.  An item computes the same bits in any launch, so every request's
+// potentials equal evaluate() of that request alone.
+class MultiSweep {
+public:
+    explicit MultiSweep(Context* ctx);
+    ~MultiSweep();
+    MultiSweep(const MultiSweep&) = delete;
+    MultiSweep& operator=(const MultiSweep&) = delete;
+    void add(const SweepJob& job, void* tag);      // checks the job, allocates its partials
+    bool idle() const { return jobs_.empty(); }
+    std::vector<void*> tags() const;                // requests with work still to run
+    void clear();                                   // drops every request (after a failure)
+    // returns the number of requests the slice took items from
+    int run_slice(int64_t budget, int max_requests, std::vector<void*>* finished);
+
+private:
+    struct Job;
+    struct Slot;
+    Context* ctx_;
+    std::vector<std::unique_ptr<Job>> jobs_;
+    std::vector<std::unique_ptr<Slot>> slots_;      // staging of the item order, two in flight
+    int next_slot_ = 0;
+    uint64_t seq_ = 0;
+};
 void direct_sum(Context* ctx, const double* tx, const double* ty, const double* tz,
                 int64_t nt, const double* sx, const double* sy, const double* sz,
                 const double* sq, int64_t ns, const bltc_params& p, double* phi);

@@ -5,15 +5,19 @@
 // the HBM budget.  Admitted requests are prepared by setup workers -- host threads, each with
 // its own stream -- which copy the inputs in and build the tree, the interaction lists, the
 // modified charges and the work plan (steps A0-A2 and the plan).  The sweep engine thread
-// takes every request that is ready (up to max_batch) and runs their far- and near-field
-// sweeps together in one persistent launch, items of all requests ordered longest first,
-// followed by each request's finalize.  A completer thread waits for the launch, copies each
-// potential back to the caller's buffer, frees the request's device memory and returns its
-// budget.  While one merged sweep runs, the workers prepare the next requests on their own
-// streams, so setup and sweeps of different requests overlap on the device.
+// takes every request that is ready and runs the far- and near-field sweeps of the requests
+// in its hands in slices: each slice takes the work items worth about slice_us microseconds
+// from the requests with the least remaining work first (at most max_batch requests), runs
+// them as persistent launches (items longest first), then finalizes every request whose
+// items have all run.  A request that becomes ready while a large one is being swept joins
+// at the next slice instead of waiting for the whole large sweep; slice_us = 0 runs all the
+// ready work in one slice.  A completer thread waits for the finalize, copies each potential
+// back to the caller's buffer, frees the request's device memory and returns its budget.
+// While slices run, the workers prepare the next requests on their own streams, so setup and
+// sweeps of different requests overlap on the device.
 //
 // A request's work items depend only on the request, and an item computes the same bits in
-// a merged launch as alone, so every potential equals bltc_solve of that request alone.
+// any launch, so every potential equals bltc_solve of that request alone.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -80,6 +84,7 @@ struct Server {
     uint64_t next_ticket = 1;
     int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_cancelled = 0, n_launches = 0;
     int64_t max_batch_seen = 0;
+    bool engine_failed = false;      // the engine could not start: requests fail at submission
     int64_t preparing = 0;          // admitted, not yet ready or failed
     std::string last_err;           // message of the most recent failed request
     bool stop = false;
@@ -236,16 +241,32 @@ static void worker_loop(Server* s, Context* c) {
     }
 }
 
+// Interactions the sweep runs per microsecond, about (1e6 cube, Coulomb): converts the slice
+// duration asked for into a work budget.
+constexpr double kInteractionsPerUs = 3.5e6;
+
 static void engine_loop(Server* s) {
     Context* c = s->engine_ctx.get();
     cudaSetDevice(s->cfg.device);
+    const int64_t budget = s->cfg.slice_us > 0
+                               ? static_cast<int64_t>(kInteractionsPerUs * s->cfg.slice_us) : 0;
+    std::unique_ptr<MultiSweep> ms;
+    try {
+        ms.reset(new MultiSweep(c));
+    } catch (const std::exception& e) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->last_err = e.what();
+        s->engine_failed = true;
+        s->cv.notify_all();
+        return;
+    }
     for (;;) {
-        std::vector<ServerRequest*> batch;
+        std::vector<ServerRequest*> add;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv.wait(lk, [&] { return s->stop || !s->ready.empty(); });
-            if (s->stop && s->ready.empty()) return;
-            if (s->cfg.linger_us > 0) {
+            s->cv.wait(lk, [&] { return s->stop || !s->ready.empty() || !ms->idle(); });
+            if (s->stop && s->ready.empty() && ms->idle()) return;
+            if (ms->idle() && s->cfg.linger_us > 0) {
                 // batching window: wait for requests still in preparation (or queued)
                 const auto until = std::chrono::steady_clock::now() +
                                    std::chrono::microseconds(s->cfg.linger_us);
@@ -254,25 +275,21 @@ static void engine_loop(Server* s) {
                            (s->preparing == 0 && s->queued.empty());
                 });
             }
-            while (!s->ready.empty() && static_cast<int>(batch.size()) < s->cfg.max_batch) {
-                batch.push_back(s->ready.front());
+            while (!s->ready.empty()) {
+                add.push_back(s->ready.front());
                 s->ready.pop_front();
             }
         }
-        std::vector<SweepJob> jobs;
-        for (ServerRequest* r : batch) {
-            cudaStreamWaitEvent(c->stream, r->ready_ev, 0);
-            jobs.push_back(SweepJob{r->L.get(), r->bt ? r->bt.get() : r->st.get(), r->st.get(), r->p,
-                                    r->phi.p});
-            r->batch = static_cast<int>(batch.size());
-        }
-        cudaEvent_t done = nullptr;
+        std::vector<void*> fin;
+        int took = 0;
         bltc_status st = BLTC_OK;
         std::string err;
         try {
-            evaluate_multi(c, jobs);
-            BLTC_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
-            BLTC_CUDA(cudaEventRecord(done, c->stream));
+            for (ServerRequest* r : add) {
+                BLTC_CUDA(cudaStreamWaitEvent(c->stream, r->ready_ev, 0));
+                ms->add(SweepJob{r->L.get(), r->bt ? r->bt.get() : r->st.get(), r->st.get(), r->p, r->phi.p}, r);
+            }
+            took = ms->run_slice(budget, s->cfg.max_batch, &fin);
         } catch (const Error& e) {
             st = e.status;
             err = e.what();
@@ -280,19 +297,46 @@ static void engine_loop(Server* s) {
             st = BLTC_ERR_CUDA;
             err = e.what();
         }
-        std::lock_guard<std::mutex> lk(s->mu);
-        ++s->n_launches;
-        s->max_batch_seen = std::max<int64_t>(s->max_batch_seen, static_cast<int64_t>(batch.size()));
         if (st != BLTC_OK) {
-            cudaStreamSynchronize(c->stream);
-            for (ServerRequest* r : batch) {
+            // every request with work in the engine fails
+            std::vector<void*> tags = ms->tags();
+            for (ServerRequest* r : add)
+                if (std::find(tags.begin(), tags.end(), static_cast<void*>(r)) == tags.end() &&
+                    std::find(fin.begin(), fin.end(), static_cast<void*>(r)) == fin.end())
+                    tags.push_back(r);
+            for (void* t : fin) tags.push_back(t);
+            ms->clear();
+            std::lock_guard<std::mutex> lk(s->mu);
+            ++s->n_launches;
+            for (void* t : tags) {
+                ServerRequest* r = static_cast<ServerRequest*>(t);
                 drop_device_state(r);
                 finish(s, r, st, err);
             }
             continue;
         }
-        s->inflight.emplace_back(std::move(batch), done);
-        s->cv.notify_all();
+        cudaEvent_t done = nullptr;
+        if (!fin.empty()) {
+            if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(done, c->stream) != cudaSuccess) {
+                cudaStreamSynchronize(c->stream);
+                if (done) cudaEventDestroy(done);
+                done = nullptr;
+            }
+        }
+        std::lock_guard<std::mutex> lk(s->mu);
+        ++s->n_launches;
+        s->max_batch_seen = std::max<int64_t>(s->max_batch_seen, static_cast<int64_t>(took));
+        if (!fin.empty()) {
+            std::vector<ServerRequest*> batch;
+            for (void* t : fin) {
+                ServerRequest* r = static_cast<ServerRequest*>(t);
+                r->batch = took;
+                batch.push_back(r);
+            }
+            s->inflight.emplace_back(std::move(batch), done);
+            s->cv.notify_all();
+        }
     }
 }
 
@@ -311,8 +355,10 @@ static void completer_loop(Server* s) {
             job = std::move(s->inflight.front());
             s->inflight.pop_front();
         }
-        cudaEventSynchronize(job.second);
-        cudaEventDestroy(job.second);
+        if (job.second) {
+            cudaEventSynchronize(job.second);
+            cudaEventDestroy(job.second);
+        }
         for (ServerRequest* r : job.first) {
             cudaError_t e = cudaMemcpyAsync(r->hphi, r->phi.p, sizeof(double) * static_cast<size_t>(r->n),
                                             cudaMemcpyDeviceToHost, c->stream);
@@ -339,7 +385,7 @@ bltc_status bltc_server_create(const bltc_server_config* cfg, bltc_server** out)
     if (!cfg || !out) return BLTC_ERR_ARG;
     *out = nullptr;
     if (cfg->setup_workers < 1 || cfg->setup_workers > 64 || cfg->max_batch < 1 || cfg->hbm_budget_bytes < 0 ||
-        cfg->linger_us < 0)
+        cfg->linger_us < 0 || cfg->slice_us < 0 || cfg->reserved != 0)
         return BLTC_ERR_ARG;
     std::unique_ptr<bltc_server> h(new bltc_server());
     Server& s = h->s;
@@ -400,7 +446,7 @@ bltc_status bltc_server_submit(bltc_server* h, const double* x, const double* y,
     r->bytes = estimate_bytes(n, *p);
     r->t_submit = now_s();
     std::lock_guard<std::mutex> lk(s.mu);
-    if (s.stop) return BLTC_ERR_STATE;
+    if (s.stop || s.engine_failed) return BLTC_ERR_STATE;
     if (r->bytes > s.budget) return BLTC_ERR_OOM;
     r->ticket = s.next_ticket++;
     *ticket = r->ticket;

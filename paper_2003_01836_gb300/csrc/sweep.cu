@@ -276,20 +276,51 @@ __global__ void k_item_costs(PlanArgs a, const int4* __restrict__ items, int64_t
     cost[i] = c;
 }
 
-// Per target: its items' partials in item order, then (mutual pairs) the rows that partner
-// batches wrote for it, in list order; scattered to the caller's order.  Each thread keeps 8
-// targets so that every row is read with 8 independent, coalesced loads in flight.
+// Adds rows [r, n) of s_row, read as T, to this thread's U targets; kAhead rows are loaded
+// before they are added, so every thread keeps several independent loads in flight.
+template <typename T, int U, int kAhead>
+__device__ __forceinline__ void add_rows(const void* const* s_row, int r, int n, int t0, int nb,
+                                         double (&s)[U]) {
+    for (; r + kAhead <= n; r += kAhead) {
+        double v[kAhead][U];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            const T* row = static_cast<const T*>(s_row[r + k]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
+                v[k][u] = t < nb ? static_cast<double>(row[t]) : 0.0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k)
+#pragma unroll
+            for (int u = 0; u < U; ++u) s[u] += v[k][u];
+    }
+    for (; r < n; ++r) {
+        const T* row = static_cast<const T*>(s_row[r]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
+            if (t < nb) s[u] += static_cast<double>(row[t]);
+        }
+    }
+}
+
+// Per target: its items' partials (FP64) in item order, then (mutual pairs) the FP32 rows that
+// partner batches wrote for it, in list order; scattered to the caller's order.  Each thread
+// keeps 8 targets so that every row is read with 8 independent, coalesced loads in flight.
 __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* __restrict__ b_begin,
                            const int32_t* __restrict__ b_count, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ n_chunks, const int64_t* __restrict__ part_off,
                            const double* __restrict__ partials, const int32_t* __restrict__ dir_off,
                            const uint8_t* __restrict__ dir_sel, const int64_t* __restrict__ dir_moff,
-                           const double* __restrict__ mpart, double* __restrict__ phi) {
+                           const float* __restrict__ mpart, double* __restrict__ phi) {
     constexpr int U = 8;          // targets per thread
     constexpr int kRows = 256;    // row pointers gathered per round
     constexpr int kAhead = 4;     // rows loaded before they are added
-    __shared__ const double* s_row[kRows];
-    __shared__ int s_n;
+    __shared__ const void* s_row[kRows];
+    __shared__ int s_n, s_nd;
     __shared__ bool s_more;
     const int b = blockIdx.x;
     const int B = b_leaves[b];
@@ -303,7 +334,8 @@ __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* 
         for (int u = 0; u < U; ++u) s[u] = 0.0;
         // The rows are added in a fixed order: the item partials, then (mutual pairs) the partner
         // rows of the skipped entries in list order.  Warp 0 gathers their addresses in rounds
-        // (its own progress in r0 and e); every thread then loads kAhead rows before adding them.
+        // (its own progress in r0 and e), the item rows of a round first; every thread then adds
+        // the round's rows.
         int r0 = 0, e = dir_off[b];
         for (;;) {
             __syncthreads();
@@ -311,6 +343,7 @@ __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* 
                 int n = 0;
                 for (; r0 < K && n < kRows; ++r0, ++n)
                     if (lane == 0) s_row[n] = p + static_cast<int64_t>(r0) * nb;
+                const int nd = n;
                 if (mpart && r0 >= K) {
                     while (e < e1 && n <= kRows - 32) {
                         const int ee = e + lane;
@@ -323,37 +356,15 @@ __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* 
                 }
                 if (lane == 0) {
                     s_n = n;
+                    s_nd = nd;
                     s_more = r0 < K || (mpart != nullptr && e < e1);
                 }
             }
             __syncthreads();
-            const int n = s_n;
+            const int n = s_n, nd = s_nd;
             const bool more = s_more;
-            int r = 0;
-            for (; r + kAhead <= n; r += kAhead) {
-                double v[kAhead][U];
-#pragma unroll
-                for (int k = 0; k < kAhead; ++k) {
-                    const double* row = s_row[r + k];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
-                        v[k][u] = t < nb ? row[t] : 0.0;
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < kAhead; ++k)
-#pragma unroll
-                    for (int u = 0; u < U; ++u) s[u] += v[k][u];
-            }
-            for (; r < n; ++r) {
-                const double* row = s_row[r];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int t = t0 + static_cast<int>(threadIdx.x) + u * static_cast<int>(blockDim.x);
-                    if (t < nb) s[u] += row[t];
-                }
-            }
+            add_rows<double, U, kAhead>(s_row, 0, nd, t0, nb, s);
+            add_rows<float, U, kAhead>(s_row, nd, n, t0, nb, s);
             if (!more) break;
         }
 #pragma unroll
@@ -584,7 +595,7 @@ void evaluate(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc
 void alloc_sweep_buffers(Context* ctx, const Lists* L, SweepBuffers* b) {
     const Plan& pl = L->plan;
     b->partials = DBuf<double>(ctx, pl.partial_len);
-    b->mpart = DBuf<double>(ctx, pl.mutual ? pl.mpart_len : 0);
+    b->mpart = DBuf<float>(ctx, pl.mutual ? pl.mpart_len : 0);
     b->counter = DBuf<unsigned int>(ctx, 1);
 }
 
@@ -648,7 +659,7 @@ void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, co
     prepare_plan(ctx, L, L->degree, p.precision);
     Plan& pl = L->plan;
     DBuf<double> partials(ctx, pl.partial_len);
-    DBuf<double> mpart(ctx, pl.mutual ? pl.mpart_len : 0);
+    DBuf<float> mpart(ctx, pl.mutual ? pl.mpart_len : 0);
     DBuf<unsigned int> counter(ctx, 1);
     BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
     SweepArgs a = make_args(ctx, L, bt, st, p, partials.p, counter.p);
@@ -685,84 +696,186 @@ void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, co
     ctx->mark(Context::kEnd);
 }
 
-void evaluate_multi(Context* ctx, const std::vector<SweepJob>& jobs) {
-    if (jobs.empty()) return;
-    cudaStream_t s = ctx->stream;
-    const int R = static_cast<int>(jobs.size());
-    std::vector<DBuf<double>> partials, mparts;
-    partials.reserve(jobs.size());
-    mparts.reserve(jobs.size());
-    DBuf<unsigned int> counter(ctx, 1);
-    BLTC_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned int), s));
-    for (int r = 0; r < R; ++r) {
-        const SweepJob& j = jobs[static_cast<size_t>(r)];
-        require(j.p.precision == BLTC_PRECISION_MIXED, "serving runs the mixed-precision sweep");
-        check_eval(j.L, j.bt, j.st, j.p, j.phi);
-        if (!j.L->plan.valid || j.L->plan.degree != j.p.degree ||
-            j.L->plan.mutual != (j.L->bt == j.L->st && j.L->n_dir > 0))
-            throw Error(BLTC_ERR_STATE, "evaluate_multi: request has no work plan");
-        const Plan& pl = j.L->plan;
-        partials.emplace_back(ctx, pl.partial_len);
-        mparts.emplace_back(ctx, pl.mutual ? pl.mpart_len : 0);
+struct MultiSweep::Job {
+    SweepJob j;
+    void* tag = nullptr;
+    uint64_t seq = 0;
+    DBuf<double> partials;
+    DBuf<float> mpart;
+    int64_t next = 0;                 // first item (in the plan's longest-first order) not run
+    int64_t remaining = 0;            // weighted cost of the items not run
+};
+
+// Pinned host and device staging of one slice's item order, reused once its event completed.
+struct MultiSweep::Slot {
+    int2* host = nullptr;
+    int64_t cap = 0;
+    DBuf<int2> dev;
+    DBuf<unsigned int> counters;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+MultiSweep::MultiSweep(Context* ctx) : ctx_(ctx) {
+    for (int i = 0; i < 2; ++i) {
+        slots_.emplace_back(new Slot());
+        BLTC_CUDA(cudaEventCreateWithFlags(&slots_.back()->done, cudaEventDisableTiming));
     }
-    const int64_t cap = kMinBlocks * static_cast<int64_t>(std::max(1, ctx->sm_count));
-    // up to kMultiMax requests per launch; within a launch, items longest first over all of
-    // its requests, one persistent launch per kernel type present
-    for (int r0 = 0; r0 < R; r0 += kMultiMax) {
-        const int r1 = std::min(R, r0 + kMultiMax);
+}
+
+MultiSweep::~MultiSweep() {
+    for (auto& sl : slots_) {
+        if (sl->done) {
+            cudaEventSynchronize(sl->done);
+            cudaEventDestroy(sl->done);
+        }
+        if (sl->host) cudaFreeHost(sl->host);
+    }
+}
+
+// A Yukawa evaluation costs about 1.5 times a Coulomb one (one MUFU.EX2 beside the RSQ).
+static int64_t weighted_cost(int64_t cost, const bltc_params& p) {
+    return p.kernel == BLTC_KERNEL_YUKAWA ? cost + cost / 2 : cost;
+}
+
+void MultiSweep::add(const SweepJob& job, void* tag) {
+    require(job.p.precision == BLTC_PRECISION_MIXED, "serving runs the mixed-precision sweep");
+    check_eval(job.L, job.bt, job.st, job.p, job.phi);
+    if (!job.L->plan.valid || job.L->plan.degree != job.p.degree ||
+        job.L->plan.mutual != (job.L->bt == job.L->st && job.L->n_dir > 0))
+        throw Error(BLTC_ERR_STATE, "multi sweep: request has no work plan");
+    const Plan& pl = job.L->plan;
+    std::unique_ptr<Job> jb(new Job());
+    jb->j = job;
+    jb->tag = tag;
+    jb->seq = seq_++;
+    jb->partials = DBuf<double>(ctx_, pl.partial_len);
+    jb->mpart = DBuf<float>(ctx_, pl.mutual ? pl.mpart_len : 0);
+    for (int64_t c : pl.h_cost) jb->remaining += weighted_cost(c, job.p);
+    jobs_.push_back(std::move(jb));
+}
+
+std::vector<void*> MultiSweep::tags() const {
+    std::vector<void*> t;
+    for (const auto& jb : jobs_) t.push_back(jb->tag);
+    return t;
+}
+
+void MultiSweep::clear() {
+    cudaStreamSynchronize(ctx_->stream);
+    jobs_.clear();
+}
+
+int MultiSweep::run_slice(int64_t budget, int max_requests, std::vector<void*>* finished) {
+    if (jobs_.empty()) return 0;
+    cudaStream_t s = ctx_->stream;
+    // the requests with the least remaining work first (arrival order on ties)
+    std::vector<Job*> byrem;
+    for (auto& jb : jobs_) byrem.push_back(jb.get());
+    std::stable_sort(byrem.begin(), byrem.end(), [](const Job* x, const Job* y) {
+        return x->remaining != y->remaining ? x->remaining < y->remaining : x->seq < y->seq;
+    });
+    // items of this slice: (job, first item, end item), whole requests first, the last one in part
+    struct Take {
+        Job* jb;
+        int64_t i0, i1;
+    };
+    std::vector<Take> take;
+    int64_t got = 0;
+    for (Job* jb : byrem) {
+        if (static_cast<int>(take.size()) >= std::max(1, max_requests)) break;
+        if (budget > 0 && got >= budget) break;
+        const Plan& pl = jb->j.L->plan;
+        int64_t i = jb->next;
+        while (i < pl.n_items && (budget <= 0 || got < budget)) {
+            const int64_t c = weighted_cost(pl.h_cost[static_cast<size_t>(i)], jb->j.p);
+            got += c;
+            jb->remaining -= c;
+            ++i;
+        }
+        if (i > jb->next) take.push_back(Take{jb, jb->next, i});
+        jb->next = i;
+    }
+    const int64_t cap = kMinBlocks * static_cast<int64_t>(std::max(1, ctx_->sm_count));
+    BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_COULOMB>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+    BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_YUKAWA>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
+    for (size_t t0 = 0; t0 < take.size(); t0 += kMultiMax) {
+        const size_t t1 = std::min(take.size(), t0 + kMultiMax);
         std::unique_ptr<MultiArgs> m(new MultiArgs());
         std::vector<std::pair<int64_t, int2>> all;
-        for (int r = r0; r < r1; ++r) {
-            const SweepJob& j = jobs[static_cast<size_t>(r)];
-            const Plan& pl = j.L->plan;
-            SweepArgs& sa = m->r[r - r0];
-            sa = make_args(ctx, j.L, j.bt, j.st, j.p, partials[static_cast<size_t>(r)].p, counter.p);
-            sa.mpart = pl.mutual ? mparts[static_cast<size_t>(r)].p : nullptr;
-            for (int64_t i = 0; i < pl.n_items; ++i)
-                all.push_back({pl.h_cost[static_cast<size_t>(i)], make_int2(r - r0, static_cast<int>(i))});
+        for (size_t t = t0; t < t1; ++t) {
+            Job* jb = take[t].jb;
+            const Plan& pl = jb->j.L->plan;
+            SweepArgs& sa = m->r[t - t0];
+            sa = make_args(ctx_, jb->j.L, jb->j.bt, jb->j.st, jb->j.p, jb->partials.p, nullptr);
+            sa.mpart = pl.mutual ? jb->mpart.p : nullptr;
+            for (int64_t i = take[t].i0; i < take[t].i1; ++i)
+                all.push_back({pl.h_cost[static_cast<size_t>(i)], make_int2(static_cast<int>(t - t0), static_cast<int>(i))});
         }
+        // longest first within the launch, one persistent launch per kernel type present
         std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int2>& x,
                                                     const std::pair<int64_t, int2>& y) { return x.first > y.first; });
-        std::vector<int2> order[2];
+        Slot& sl = *slots_[static_cast<size_t>(next_slot_)];
+        next_slot_ ^= 1;
+        if (sl.used) BLTC_CUDA(cudaEventSynchronize(sl.done));     // its previous slice has run
+        const int64_t total = static_cast<int64_t>(all.size());
+        if (total > sl.cap) {
+            if (sl.host) cudaFreeHost(sl.host);
+            sl.host = nullptr;
+            sl.cap = std::max<int64_t>(total, 2 * sl.cap);
+            BLTC_CUDA(cudaMallocHost(&sl.host, sizeof(int2) * sl.cap));
+        }
+        if (!sl.dev.p || sl.dev.n < total) sl.dev = DBuf<int2>(ctx_, sl.cap);
+        if (!sl.counters.p) sl.counters = DBuf<unsigned int>(ctx_, 2);
+        int64_t nc = 0;
         for (const auto& pr : all)
-            order[jobs[static_cast<size_t>(r0 + pr.second.x)].p.kernel == BLTC_KERNEL_YUKAWA].push_back(pr.second);
-        DBuf<int2> d_order(ctx, static_cast<int64_t>(all.size()));
-        DBuf<unsigned int> counters(ctx, 2);
-        BLTC_CUDA(cudaMemsetAsync(counters.p, 0, 2 * sizeof(unsigned int), s));
-        if (!order[0].empty())
-            BLTC_CUDA(cudaMemcpyAsync(d_order.p, order[0].data(), sizeof(int2) * order[0].size(), cudaMemcpyHostToDevice, s));
-        if (!order[1].empty())
-            BLTC_CUDA(cudaMemcpyAsync(d_order.p + order[0].size(), order[1].data(), sizeof(int2) * order[1].size(),
-                                      cudaMemcpyHostToDevice, s));
-        if (!order[0].empty()) {
-            const int total = static_cast<int>(order[0].size());
-            BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_COULOMB>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
-            k_sweep_multi<BLTC_KERNEL_COULOMB><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, kMixedSmem, s>>>(
-                *m, d_order.p, total, counters.p); ++ctx->launches;
+            if (take[t0 + pr.second.x].jb->j.p.kernel != BLTC_KERNEL_YUKAWA) sl.host[nc++] = pr.second;
+        int64_t ny = nc;
+        for (const auto& pr : all)
+            if (take[t0 + pr.second.x].jb->j.p.kernel == BLTC_KERNEL_YUKAWA) sl.host[ny++] = pr.second;
+        BLTC_CUDA(cudaMemsetAsync(sl.counters.p, 0, 2 * sizeof(unsigned int), s));
+        BLTC_CUDA(cudaMemcpyAsync(sl.dev.p, sl.host, sizeof(int2) * total, cudaMemcpyHostToDevice, s));
+        if (nc > 0) {
+            k_sweep_multi<BLTC_KERNEL_COULOMB><<<static_cast<unsigned>(std::min<int64_t>(nc, cap)), kThreads, kMixedSmem, s>>>(
+                *m, sl.dev.p, static_cast<int>(nc), sl.counters.p); ++ctx_->launches;
             BLTC_LAUNCH_CHECK("sweep multi coulomb");
         }
-        if (!order[1].empty()) {
-            const int total = static_cast<int>(order[1].size());
-            BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_YUKAWA>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
-            k_sweep_multi<BLTC_KERNEL_YUKAWA><<<static_cast<unsigned>(std::min<int64_t>(total, cap)), kThreads, kMixedSmem, s>>>(
-                *m, d_order.p + order[0].size(), total, counters.p + 1); ++ctx->launches;
+        if (total > nc) {
+            k_sweep_multi<BLTC_KERNEL_YUKAWA><<<static_cast<unsigned>(std::min<int64_t>(total - nc, cap)), kThreads, kMixedSmem, s>>>(
+                *m, sl.dev.p + nc, static_cast<int>(total - nc), sl.counters.p + 1); ++ctx_->launches;
             BLTC_LAUNCH_CHECK("sweep multi yukawa");
         }
-        // the host order vectors must outlive the asynchronous copies
-        BLTC_CUDA(cudaStreamSynchronize(s));
+        BLTC_CUDA(cudaEventRecord(sl.done, s));
+        sl.used = true;
     }
-    for (int r = 0; r < R; ++r) {
-        const SweepJob& j = jobs[static_cast<size_t>(r)];
-        const Plan& pl = j.L->plan;
-        k_finalize<<<static_cast<unsigned>(j.L->n_batches), 256, 0, s>>>(
-            j.bt->leaves.p, j.bt->begin.p, j.bt->count.p, j.bt->perm.p, pl.n_chunks.p, pl.part_off.p,
-            partials[static_cast<size_t>(r)].p, j.L->dir_off.p, pl.dir_sel.p,
-            pl.mutual ? pl.dir_moff.p : nullptr, pl.mutual ? mparts[static_cast<size_t>(r)].p : nullptr,
-            j.phi); ++ctx->launches;
+    // finalize the requests whose items have all run; their buffers are freed in stream order
+    for (size_t k = 0; k < jobs_.size();) {
+        Job* jb = jobs_[k].get();
+        const Plan& pl = jb->j.L->plan;
+        if (jb->next < pl.n_items) {
+            ++k;
+            continue;
+        }
+        k_finalize<<<static_cast<unsigned>(jb->j.L->n_batches), 256, 0, s>>>(
+            jb->j.bt->leaves.p, jb->j.bt->begin.p, jb->j.bt->count.p, jb->j.bt->perm.p, pl.n_chunks.p,
+            pl.part_off.p, jb->partials.p, jb->j.L->dir_off.p, pl.dir_sel.p,
+            pl.mutual ? pl.dir_moff.p : nullptr, pl.mutual ? jb->mpart.p : nullptr, jb->j.phi);
+        ++ctx_->launches;
         BLTC_LAUNCH_CHECK("finalize multi");
+        finished->push_back(jb->tag);
+        jobs_.erase(jobs_.begin() + static_cast<std::ptrdiff_t>(k));
     }
+    if (jobs_.empty()) {
+        // idle: the device staging goes back to the allocator (freed after its last use in
+        // stream order); the pinned host staging stays for the next request
+        for (auto& sl : slots_) {
+            sl->dev.reset();
+            sl->counters.reset();
+        }
+    }
+    return static_cast<int>(take.size());
 }
 
 static void counts(Context* ctx, const Lists* L, const uint8_t* dir_sel, int64_t* out4) {

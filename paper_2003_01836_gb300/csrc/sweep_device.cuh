@@ -49,7 +49,7 @@ struct SweepArgs {
     const uint8_t* dir_sel;    // per direct entry: bit 0 = r^2 == 0 possible, bit 1 = close pairs possible
     const float* dir_tau2;     // per direct entry: pairs closer than this (r^2) are redone in FP64
     const int64_t* dir_moff;   // per direct entry: offset of its mutual row in mpart, or -1
-    double* mpart;             // mutual rows: potentials a batch's particles induce on a partner's
+    float* mpart;              // mutual rows (FP32): potentials a batch's particles induce on a partner's
     const int4* items;
     const int64_t* part_off;
     double* partials;
@@ -421,10 +421,10 @@ __device__ __forceinline__ void near_mutual_block(const SweepArgs& a, const floa
 // own batch, whose list entry for B is skipped).  The second sum runs over B's targets,
 // which sit in different lanes: per source, each lane adds its 8 targets' q_i G in FP32, the
 // warp adds its lanes (warp_sum8), and after the tile the group's warps are added in warp
-// order into C's mutual row (FP64), so the result does not depend on scheduling.
+// order into C's mutual row (FP32), so the result does not depend on scheduling.
 template <int KER, bool SEL, bool CHECK>
 __device__ void near_mutual(const SweepArgs& a, int C, int B, float tau2, const double cb[3], const Targets& tg,
-                            double* acc, float4* sm, float* sbuf, double* mrow, int g, int G, int tb,
+                            double* acc, float4* sm, float* sbuf, float* mrow, int g, int G, int tb,
                             int nb, int t0, int l, int tpg) {
     constexpr int kTile = kNearTile;
     constexpr bool SCREEN = CHECK && kCloseBlockScreen;
@@ -507,7 +507,7 @@ __device__ void near_mutual(const SweepArgs& a, int C, int B, float tau2, const 
             const int w0 = ((j / kBlock) % G) * wpg;
             float hs = 0.f, ls = 0.f;       // TwoSum pair: about twice the FP32 precision
             for (int w = w0; w < w0 + wpg; ++w) two_sum_add(hs, ls, sbuf[w * kTile + j]);
-            const double sum = static_cast<double>(hs) + static_cast<double>(ls);
+            const float sum = hs + ls;
             if (t0 == 0) mrow[j0 + j] = sum; else mrow[j0 + j] += sum;
         }
     }
@@ -726,7 +726,7 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
             if (sel & kSelSkip) continue;            // evaluated by the partner's mutual entry
             if (sel & kSelMutual) {
                 float* sbuf = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + kSmemBytes + kAccBytes);
-                double* mrow = a.mpart + a.dir_moff[de];
+                float* mrow = a.mpart + a.dir_moff[de];
                 switch (sel & (kSelZero | kSelClose)) {
                     case 0: near_mutual<KER, false, false>(a, C, B, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;
                     case kSelClose: near_mutual<KER, false, true>(a, C, B, tau2, cb, tg, acc, sm, sbuf, mrow, g, G, tb, nb, t0, l, tpg); break;

@@ -6,8 +6,9 @@
   mixed against FP64 over all targets, and both against the direct sum on seeded targets
   (the error is sampled at a random subset of targets for large N, Sec. IV).
 * 2.56e8 uniform particles, Coulomb, theta 0.8, n 10: the mixed treecode against the oracle's
-  own direct sum on 64 seeded targets and against the GPU FP64 direct sum on 2048, plus
-  determinism of a repeated solve.
+  own direct sum on 64 seeded targets and against the GPU FP64 direct sum on 2048; tree and
+  lists bit-exact with the oracle at full size; mixed against the FP64 treecode on six
+  sampled batches; and determinism of a repeated solve.
 """
 import numpy as np
 import pytest
@@ -111,6 +112,43 @@ def test_uniform_2_56e8_sampled(gpu):
     assert oracle.rel_err(ref_cpu, ref_gpu[pos]) < 1e-12
     e_gpu = oracle.rel_err(ref_gpu, phi[t2k])
     assert e_cpu < 1e-5 and e_gpu < 1e-5, (e_cpu, e_gpu)
+    # tree and lists bit-exact with the oracle at full size, and the mixed treecode within
+    # the mixed bar of the FP64 treecode on sampled batches (the FP64 solve of the whole system
+    # would take minutes at this size)
+    st = b.bltc_tree_build(gpu.h, *X, 2000)
+    try:
+        ot = oracle.Tree(x, y, z, 2000)
+        gt = b.bltc_tree_export(gpu.h, st)
+        for k in ("perm", "begin", "count", "parent", "n_children", "children"):
+            assert np.array_equal(getattr(ot, k), gt[k].astype(getattr(ot, k).dtype)), k
+        for k in ("lo", "hi", "center", "radius"):
+            assert np.array_equal(getattr(ot, k).view(np.int64), gt[k].view(np.int64)), k
+        del gt
+        p64 = b.params(10, 0.8, 2000, 2000, precision=b.BLTC_PRECISION_FP64)
+        L = b.bltc_lists_build(gpu.h, st, st, p64)
+        got = b.bltc_lists_export(gpu.h, L)
+        want = oracle.lists(ot, ot, 0.8, 10)
+        for k in want:
+            assert np.array_equal(want[k], got[k]), k
+        del got, want
+        nl = len(ot.leaves)
+        pick = np.sort(np.random.default_rng(20031843).choice(nl, 6, replace=False)).astype(np.int32)
+        S = b.bltc_lists_select(gpu.h, L, pick)
+        b.bltc_modified_charges(gpu.h, st, S, p64)
+        phi64 = torch.empty_like(X[0])
+        b.bltc_evaluate(gpu.h, S, st, st, p64, phi64)
+        torch.cuda.synchronize()
+        b.bltc_lists_destroy(S)
+        b.bltc_lists_destroy(L)
+        idx = batch_targets(ot, pick)
+        got64 = host(phi64)[idx]
+        assert oracle.rel_err(got64, phi[idx]) <= MIXED_REL2
+        # against the oracle's direct sum on 32 of those targets: the treecode's own error
+        sub = idx[::max(1, len(idx) // 32)][:32]
+        ref_sub = oracle.direct_sum([x[sub], y[sub], z[sub]], [x, y, z], q)
+        assert oracle.rel_err(ref_sub, host(phi64)[sub]) < 1e-5
+    finally:
+        b.bltc_tree_destroy(st)
     # determinism of a repeated solve
     del X
     torch.cuda.empty_cache()

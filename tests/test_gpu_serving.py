@@ -54,13 +54,36 @@ def test_more_requests_in_a_sweep_than_one_launch_holds(gpu):
     # launches of at most 64 argument sets, and every result is still its solo solve's bits
     reqs = _requests(80, 5, nmax_exp=3.3)
     solo = [gpu_solve(gpu, *r) for r in reqs]
-    srv = b.Server(0, setup_workers=4, max_batch=100, linger_us=2_000_000)
+    srv = b.Server(0, setup_workers=4, max_batch=100, linger_us=2_000_000, slice_us=0)
     try:
         tickets = [srv.submit(*r) for r in reqs]
         for i, (t, ref) in enumerate(zip(tickets, solo)):
             st, phi, _ = srv.wait(t)
             assert st == b.BLTC_OK and np.array_equal(phi, ref), i
         assert srv.stats()["max_batch"] > 64
+    finally:
+        srv.close()
+
+
+def test_sliced_sweeps_let_small_requests_pass_a_large_one(gpu):
+    # With slices of 2 ms, small requests that become ready while a large sweep runs are
+    # swept at the next slice (least remaining work first) and finish before the large one;
+    # every result is still its solo solve's bits.
+    big = system("cube", 600000, 20031911) + (b.params(10, 0.5, 2000),)
+    small = [system("plummer", 3000, 20031912 + i) + (b.params(6, 0.7, 500),) for i in range(6)]
+    solo = [gpu_solve(gpu, *r) for r in [big] + small]
+    srv = b.Server(0, setup_workers=2, max_batch=16, slice_us=2000)
+    try:
+        tb = srv.submit(*big)
+        import time
+        time.sleep(0.02)                 # the large request is being prepared or swept
+        ts = [srv.submit(*r) for r in small]
+        outs = [srv.wait(t) for t in [tb] + ts]
+        for (st, phi, _), ref in zip(outs, solo):
+            assert st == b.BLTC_OK and np.array_equal(phi, ref)
+        t_big = outs[0][2]["t_done"]
+        assert all(o[2]["t_done"] < t_big for o in outs[1:]), [o[2]["t_done"] - t_big for o in outs]
+        assert srv.stats()["sweep_launches"] > 2
     finally:
         srv.close()
 
