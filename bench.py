@@ -593,7 +593,20 @@ def check_errors(ctx, b, X, p, w, phi_mixed):
             "mixed_bltc_vs_direct_sampled": rel_err(h(ref), h(phi_mx.index_select(0, idx))),
             "fp64_gpu_bltc_seconds": t64, "direct_sample_targets": int(idx.numel()),
             "gpu_direct_sum_mixed_seconds": e0.elapsed_time(e1) * 1e-3,
+            # the mixed direct sum is bound by the FMA pipe: 13 FP32 operations per evaluation
+            # (three per coordinate difference from FP32 pairs, three for r^2, one accumulation)
+            # against 128 per clock per SM
+            "gpu_direct_sum_mixed_roofline": direct_roofline(ctx, w["n"], e0.elapsed_time(e1) * 1e-3),
             "gpu_direct_sum_mixed_vs_fp64_sampled": rel_err(h(ref), h(dmx.index_select(0, idx)))}
+
+
+def direct_roofline(ctx, n, seconds):
+    """The mixed direct sum's evaluations per second against its FMA-pipe bound."""
+    evals = n * (n - 1)
+    peak = ctx.sm_count * 128.0 / 13.0 * SM_MAX_MHZ * 1e6
+    return {"bound": "alu", "pipe": "FMA (13 FP32 operations per evaluation)",
+            "achieved": evals / seconds / 1e9, "peak": peak / 1e9, "unit": "G evaluations/s",
+            "frac": evals / seconds / peak}
 
 
 def run_e2e(ctx, b, x, y, z, q, p, args, dist, w):
