@@ -12,7 +12,7 @@ Prints one JSON line (rank 0).  Under torchrun each rank solves its own independ
 on its own GPU (replicas: the treecode of one system needs no exchange); the value is the
 whole job's targets per second over the slowest rank.  ``--impl reference`` times the FP64
 CPU oracle (Algorithm 1 as written, on the host cores) on a bounded sample of the same
-workload in every step: the evaluation of two batches per core.
+workload in every step: the evaluation of eight batches per core.
 
 The default run adds sub-records for the 8e6 Plummer (Yukawa) and 2.56e8 uniform (n = 10)
 configurations under "configs", and the oracle's measured time for the whole 1e6 system under
@@ -962,7 +962,7 @@ def run_graph(args, dist: Dist):
 
 def run_reference(args, dist: Dist):
     """The oracle on the host cores, every step a bounded, measured sample of the workload:
-    Algorithm 1's evaluation (ComputePotential) of two batches per core, the batches drawn in
+    Algorithm 1's evaluation (ComputePotential) of eight batches per core, the batches drawn in
     turn from a seeded permutation of all of them.  The trees and modified charges are built
     once before the warm-up (their time is reported, not in the steps)."""
     if dist.rank != 0:
@@ -984,7 +984,10 @@ def run_reference(args, dist: Dist):
     counts = st.count[st.leaves]
     nl = len(counts)
     order = np.random.default_rng(20031836).permutation(nl)
-    per_step = min(2 * cores, nl)       # two batches per core: dynamic scheduling evens them out
+    # eight batches per core: the batches' costs differ by up to 8x (leaves of ~1953 and ~250
+    # targets), and with two per core the slowest core paced each step at 61% of the whole
+    # solve's rate; the oracle schedules batches dynamically over its threads
+    per_step = min(8 * cores, nl)
 
     def batches(i):
         return np.sort(np.take(order, np.arange(i * per_step, (i + 1) * per_step), mode="wrap"))
@@ -1001,7 +1004,7 @@ def run_reference(args, dist: Dist):
     prep.close()
     v = targets / sum(times)
     sample = (f"Algorithm 1's evaluation (ComputePotential) of {per_step} of the {nl} batches per step "
-              f"(two per core), drawn in turn from a seeded permutation; {targets} targets over the "
+              f"(eight per core), drawn in turn from a seeded permutation; {targets} targets over the "
               f"timed steps; the trees and modified charges ({setup_s:.2f} s) are built once before "
               f"the warm-up and are not in the steps")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "targets/s",

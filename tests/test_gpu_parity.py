@@ -369,6 +369,14 @@ def test_selected_batches(gpu):
                 with pytest.raises(b.BltcError) as e:
                     b.bltc_lists_select(gpu.h, L, bad)
                 assert e.value.status == b.BLTC_ERR_ARG
+            # no batch at all: every list is empty and every potential 0
+            E = b.bltc_lists_select(gpu.h, L, [])
+            assert b.bltc_lists_info(E) == {"n_batches": len(ot.leaves), "n_approx": 0, "n_direct": 0}
+            b.bltc_modified_charges(gpu.h, st, E, p)
+            b.bltc_evaluate(gpu.h, E, st, st, p, phi)
+            torch.cuda.synchronize()
+            assert not np.any(host(phi))
+            b.bltc_lists_destroy(E)
             b.bltc_lists_destroy(S)
             b.bltc_lists_destroy(L)
     finally:
