@@ -378,13 +378,15 @@ def run_ours(args, dist: Dist):
         out["error"] = check_errors(ctx, b, X, p, w, phi)
     if not args.no_e2e:
         out["e2e"] = run_e2e(ctx, b, x, y, z, q, p, args, dist, w)
-    if not args.no_serving:
+    # the sub-records run on one GPU only: under torchrun every rank is a replica of the main
+    # workload, and N copies of the 2.56e8 system or the request stream would crowd the host
+    if dist.world == 1 and not args.no_serving:
         sv = serve_measure(args.serve_record_requests, (0.5,), args.serve_workers, dist,
                            args.serve_slice_us)
         out["serving"] = {"requests": sv["config"]["requests"], "total_targets": sv["config"]["total_targets"],
                           "mix": sv["config"]["mix"], "slice_us": sv["config"]["slice_us"], "levels": sv["levels"], "solo": sv["solo"],
                           "served_vs_solo": sv["served_vs_solo"]}
-    if not args.no_configs:
+    if dist.world == 1 and not args.no_configs:
         out["configs"] = {}
         for key in args.configs.split(","):
             if key:
