@@ -330,8 +330,8 @@ bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,
  * those sizes) and every candidate's fastest time into ms[n_candidates] (may be NULL; NaN
  * for a candidate not timed).  The choice is cached in the context under (floor(log2 n),
  * degree, kernel, precision, theta to 1e-3, mean batch size of the first candidate in
- * quarter octaves): a later call with the same key and use_cache != 0 returns it after the
- * screen, untimed.  Device pointers as bltc_solve.  Synchronizes.  Errors: ARG, OOM, CUDA. */
+ * quarter octaves): a later call with the same key and use_cache != 0 returns it untimed,
+ * after screening the first candidate only, if it is among that call's candidates.  Device pointers as bltc_solve.  Synchronizes.  Errors: ARG, OOM, CUDA. */
 bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, const double* z,
                           const double* q, int64_t n, const bltc_params* params,
                           const int32_t* leaf, const int32_t* batch, int32_t n_candidates,

@@ -641,7 +641,7 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
             int same = -1;
         };
         std::vector<Cand> cs(static_cast<size_t>(n_candidates));
-        for (int i = 0; i < n_candidates; ++i) {
+        auto screen = [&](int i) {
             bltc_params p = *params;
             p.leaf_size = leaf[i];
             p.batch_size = batch ? batch[i] : leaf[i];
@@ -668,9 +668,11 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
                     break;
                 }
             }
-        }
+        };
+        screen(0);
         // The distribution enters the cache key as the mean batch size of the first candidate
         // (quarter octaves): a uniform cube and a Plummer sphere of the same size differ there.
+        // A cached choice is taken only if it is among this call's candidates.
         int lg = 0;
         while ((int64_t(1) << (lg + 1)) <= n) ++lg;
         const int shape = static_cast<int>(std::lround(4.0 * std::log2(static_cast<double>(n) /
@@ -681,11 +683,16 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
         if (use_cache) {
             auto it = ctx->tuned.find(key);
             if (it != ctx->tuned.end()) {
-                best->leaf_size = it->second.first;
-                best->batch_size = it->second.second;
-                return;
+                for (int i = 0; i < n_candidates; ++i) {
+                    if (leaf[i] == it->second.first && (batch ? batch[i] : leaf[i]) == it->second.second) {
+                        best->leaf_size = it->second.first;
+                        best->batch_size = it->second.second;
+                        return;
+                    }
+                }
             }
         }
+        for (int i = 1; i < n_candidates; ++i) screen(i);
         // Time only the contenders: distinct candidates within kBand of the smallest cost.
         constexpr double kBand = 0.10;
         constexpr int kMaxTimed = 3;
