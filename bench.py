@@ -14,8 +14,8 @@ whole job's targets per second over the slowest rank.  ``--impl reference`` time
 CPU oracle (Algorithm 1 as written, on the host cores) on a bounded sample of the same
 workload in every step: the evaluation of eight batches per core.
 
-The default run adds sub-records for the 8e6 Plummer (Yukawa) and 2.56e8 uniform (n = 10)
-configurations under "configs", and the oracle's measured time for the whole 1e6 system under
+The default run adds sub-records for the 1e4 cube (errors over all targets), the 8e6 Plummer
+(Yukawa) and the 2.56e8 uniform (n = 10) configurations under "configs", and the oracle's measured time for the whole 1e6 system under
 "cpu_baseline".
 """
 from __future__ import annotations
@@ -389,7 +389,9 @@ def run_ours(args, dist: Dist):
     if dist.world == 1 and not args.no_configs:
         out["configs"] = {}
         for key in args.configs.split(","):
-            if key:
+            if key == "1":
+                out["configs"][key] = run_config1(ctx, b, dist)
+            elif key:
                 out["configs"][key] = run_config(ctx, b, key, args, dist)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cb = oracle_measured(x, y, z, q, w, sample_batches=os.cpu_count() or 1)
@@ -548,6 +550,51 @@ def run_config(ctx, b, key, args, dist):
                      "fp64_bltc_sampled_seconds": fp64_s, "fp64_direct_sampled_seconds": direct_s}}
     del X, phi, phi64, T, ref
     torch.cuda.empty_cache()
+    return out
+
+
+CONFIG1 = dict(kind="cube", n=10_000, theta=0.7, degree=4, leaf=500, kernel=0, kappa=0.0,
+               seed=20031837, steps=20, warmup=3,
+               name=("uniform cube N=1e4 (q in [-1,1]), Coulomb, theta=0.7, n=4, N_L=N_B=500: "
+                     "FP64 and mixed GPU treecode against the FP64 GPU direct sum on all targets"))
+
+
+def run_config1(ctx, b, dist):
+    """The small configuration: every target's potential by the FP64 and the mixed treecode,
+    each against the FP64 direct sum of Eq. 1 over all targets (Eq. 16 on the whole system),
+    beside the time of each solve."""
+    import torch
+    from paper_2003_01836_gb300 import inputs
+    c = CONFIG1
+    X = [torch.from_numpy(a).cuda() for a in inputs.system(c["kind"], c["n"], c["seed"] + dist.rank)]
+    out = {"workload": c["name"], "n_particles": c["n"], "steps": c["steps"], "warmup": c["warmup"]}
+    phis = {}
+    for name, prec in (("fp64", b.BLTC_PRECISION_FP64), ("mixed", b.BLTC_PRECISION_MIXED)):
+        p = b.params(c["degree"], c["theta"], c["leaf"], c["leaf"], c["kernel"], c["kappa"], prec)
+        phi = torch.empty_like(X[0])
+        for _ in range(c["warmup"]):
+            ctx.solve(*X, p, phi)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(c["steps"]):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.solve(*X, p, phi)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        phis[name] = phi.cpu().numpy()
+        out[f"{name}_ms_per_solve"] = statistics.median(ms)
+    p64 = b.params(c["degree"], c["theta"], c["leaf"], c["leaf"], c["kernel"], c["kappa"],
+                   b.BLTC_PRECISION_FP64)
+    ref = torch.empty_like(X[0])
+    b.bltc_direct_sum(ctx.h, *X[:3], *X[:3], X[3], p64, ref)
+    ref_h = ref.cpu().numpy()
+    out["error"] = {"sample": "all targets",
+                    "fp64_bltc_vs_fp64_direct": rel_err(ref_h, phis["fp64"]),
+                    "mixed_bltc_vs_fp64_direct": rel_err(ref_h, phis["mixed"]),
+                    "mixed_vs_fp64_gpu_bltc": rel_err(phis["fp64"], phis["mixed"]),
+                    "meets_1e-6": bool(rel_err(phis["fp64"], phis["mixed"]) <= 1e-6)}
     return out
 
 
@@ -1038,7 +1085,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the sub-records of the 8e6 Plummer and 2.56e8 cube configurations")
-    ap.add_argument("--configs", default="3,5", help="which large configurations to add (3, 5)")
+    ap.add_argument("--configs", default="1,3,5", help="which other configurations to add (1, 3, 5)")
     ap.add_argument("--error-targets5", type=int, default=0,
                     help="targets of the 2.56e8 configuration's error sample (default 2048)")
     ap.add_argument("--serving", action="store_true",
