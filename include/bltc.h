@@ -311,6 +311,34 @@ bltc_status bltc_graph_launch(bltc_context* ctx, bltc_graph* graph);
 int64_t bltc_graph_kernels(const bltc_graph* graph);
 void bltc_graph_destroy(bltc_graph* graph);
 
+/* A solve for NEW positions at every launch, as one CUDA graph: the whole of Algorithm 1
+ * (tree and batches, Sec. II-D; lists, Eq. 13; modified charges, Eq. 12; far and near field,
+ * Eq. 11 and 9; the fixed-order finalize), with no host synchronisation between the tree and
+ * the finalize.  The host-driven bltc_solve reads counts back at every step to size the next;
+ * here every buffer has a capacity and every count stays in device memory.
+ *
+ * bltc_graph_create_positions solves once with x, y, z, q into phi (as bltc_solve), sets the
+ * capacities to that solve's counts (tree nodes and levels, list entries, clusters with
+ * modified charges, work items, partial and mutual-row lengths) times `headroom` (0 selects
+ * 1.25; else 1 <= headroom <= 16) plus a margin, and captures the sized solve.  x, y, z, q and
+ * phi (device, n, caller order) are BOUND: each bltc_graph_launch reads the positions and
+ * charges currently in them and overwrites phi.  A launch is one cudaGraphLaunch followed by a
+ * read of a 4-byte flag, so it SYNCHRONIZES.  Results are the bits bltc_solve gives for the same
+ * inputs.  If the positions need more than a capacity (or are not finite), the sized solve raises
+ * the flag without writing past any buffer; the launch then solves again on the host-driven path
+ * (which reports non-finite input as ARG) and rebuilds the graph for the new sizes, so phi is
+ * always correct.  Parameters as bltc_solve (built-in or registered kernels, FP64 or mixed, leaf
+ * and batch sizes may differ).  Memory: the graph holds every buffer of one solve at its capacity
+ * (about the footprint of a bltc_solve times the headroom).  Errors: as bltc_graph_create.
+ *
+ * bltc_graph_info writes {kernels per launch, launches, launches redone on the host path,
+ * captures} of either kind of graph to out[4]; ARG for NULL. */
+bltc_status bltc_graph_create_positions(bltc_context* ctx, const double* x, const double* y,
+                                        const double* z, const double* q, int64_t n,
+                                        const bltc_params* params, double* phi, double headroom,
+                                        bltc_graph** out);
+bltc_status bltc_graph_info(const bltc_graph* graph, int64_t* out);
+
 /* bltc_solve for HOST buffers x, y, z, q, phi (pinned memory recommended): copies the
  * inputs to the device, solves, copies phi back.  Synchronizes.  Errors: as bltc_solve. */
 bltc_status bltc_solve_host(bltc_context* ctx, const double* x, const double* y,

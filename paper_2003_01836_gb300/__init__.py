@@ -127,6 +127,9 @@ _SIGNATURES = {
     "bltc_graph_launch": ([_vp, _vp], ctypes.c_int),
     "bltc_graph_kernels": ([_vp], _i64),
     "bltc_graph_destroy": ([_vp], None),
+    "bltc_graph_create_positions": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, ctypes.c_double, _pp],
+                                    ctypes.c_int),
+    "bltc_graph_info": ([_vp, _vp], ctypes.c_int),
     "bltc_dual_lists": ([_vp, _vp, _vp, _P, _vp, _vp, _vp], ctypes.c_int),
     "bltc_solve_targets": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                            ctypes.c_int),
@@ -452,6 +455,25 @@ def bltc_graph_create(ctx, x, y, z, q, p: bltc_params, phi):
     return h.value
 
 
+def bltc_graph_create_positions(ctx, x, y, z, q, p: bltc_params, phi, headroom=0.0):
+    """Capture the whole solve sized on the device; x, y, z, q and phi (device tensors) are bound
+    to the graph and read (written) at every launch."""
+    _stream(ctx)
+    h = ctypes.c_void_p()
+    _check(ctx, lib().bltc_graph_create_positions(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.numel(),
+                                                  ctypes.byref(p), _ptr(phi), float(headroom),
+                                                  ctypes.byref(h)))
+    return h.value
+
+
+def bltc_graph_info(graph):
+    """{kernels, launches, redone, captures} of a graph."""
+    out = (ctypes.c_int64 * 4)()
+    if lib().bltc_graph_info(graph, out) != BLTC_OK:
+        raise BltcError(BLTC_ERR_ARG, "graph_info: NULL graph")
+    return {"kernels": out[0], "launches": out[1], "redone": out[2], "captures": out[3]}
+
+
 def bltc_graph_launch(ctx, graph):
     """Replay: reads the charges now in the bound q, overwrites the bound phi."""
     _stream(ctx)
@@ -629,16 +651,25 @@ class Graph:
     tensor ``q`` and the output ``phi`` are bound: write new charges into ``q`` (in place), call
     ``launch()``, read ``phi``."""
 
-    def __init__(self, ctx, x, y, z, q, p, phi=None):
+    def __init__(self, ctx, x, y, z, q, p, phi=None, positions=False, headroom=0.0):
+        """``positions=True``: the whole solve sized on the device, so the positions tensors
+        ``x, y, z`` are bound too and may change (in place) between launches."""
         import torch
         self.ctx = ctx
-        self.q = q
+        self.x, self.y, self.z, self.q = x, y, z, q
         self.phi = torch.empty_like(x) if phi is None else phi
-        self.h = bltc_graph_create(ctx.h, x, y, z, q, p, self.phi)
+        if positions:
+            self.h = bltc_graph_create_positions(ctx.h, x, y, z, q, p, self.phi, headroom)
+        else:
+            self.h = bltc_graph_create(ctx.h, x, y, z, q, p, self.phi)
 
     @property
     def kernels(self):
         return bltc_graph_kernels(self.h)
+
+    @property
+    def info(self):
+        return bltc_graph_info(self.h)
 
     def launch(self):
         bltc_graph_launch(self.ctx.h, self.h)

@@ -34,7 +34,15 @@ namespace bltc {
 
 void* Context::dalloc(size_t bytes) {
     void* p = nullptr;
+    if (arena.base) {
+        const size_t b = Arena::footprint(bytes);
+        if (arena.used + b > arena.size) throw Error(BLTC_ERR_STATE, "graph arena exhausted");
+        p = arena.base + arena.used;
+        arena.used += b;
+        return p;
+    }
     if (capturing) throw Error(BLTC_ERR_STATE, "device allocation inside a graph capture");
+    if (arena.measure) arena.measured += Arena::footprint(bytes);
     if (alloc_fn) {
         p = alloc_fn(bytes, stream, alloc_user);
         if (!p) throw Error(BLTC_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
@@ -162,8 +170,8 @@ static void upward_beside_plan(Context* c, Tree* st, Lists* L, const bltc_params
     c->join();
 }
 
-static void solve_device(Context* c, const double* x, const double* y, const double* z,
-                         const double* q, int64_t n, const bltc_params& p, double* phi) {
+void solve_device(Context* c, const double* x, const double* y, const double* z,
+                  const double* q, int64_t n, const bltc_params& p, double* phi) {
     c->mark(Context::kStart);
     Tree st;
     build_tree(c, x, y, z, q, n, p.leaf_size, &st);
@@ -587,6 +595,28 @@ bltc_status bltc_graph_launch(bltc_context* ctx, bltc_graph* graph) {
         if (graph->ctx != ctx) throw Error(BLTC_ERR_STATE, "graph_launch: the graph belongs to another context");
         graph_launch(&ctx->c, graph->g);
     });
+}
+
+bltc_status bltc_graph_create_positions(bltc_context* ctx, const double* x, const double* y,
+                                        const double* z, const double* q, int64_t n,
+                                        const bltc_params* params, double* phi, double headroom,
+                                        bltc_graph** out) {
+    if (!ctx || !out) return BLTC_ERR_ARG;
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(x && y && z && q && phi, "graph_create_positions: NULL pointer");
+        std::unique_ptr<bltc_graph> h(new bltc_graph());
+        h->g = graph_create_positions(&ctx->c, x, y, z, q, n, *params, phi, headroom);
+        h->ctx = ctx;
+        *out = h.release();
+    });
+}
+
+bltc_status bltc_graph_info(const bltc_graph* graph, int64_t* out) {
+    if (!graph || !graph->g || !out) return BLTC_ERR_ARG;
+    graph_info(graph->g, out);
+    return BLTC_OK;
 }
 
 int64_t bltc_graph_kernels(const bltc_graph* graph) {

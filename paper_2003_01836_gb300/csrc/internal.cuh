@@ -73,6 +73,19 @@ struct Context {
         if (cudaEventRecord(events[m], stream) == cudaSuccess) marked |= 1u << m;
     }
 
+    // A bump arena that serves every allocation while it is set (the capture of a solve sized
+    // on the device, which allocates nothing while captured): blocks are never freed one by
+    // one, the arena's owner frees it whole.  With `measure` set, allocations are served as
+    // usual and their arena footprint is summed in `measured`.
+    struct Arena {
+        char* base = nullptr;
+        size_t size = 0, used = 0;
+        bool measure = false;
+        size_t measured = 0;
+        static size_t footprint(size_t bytes) { return (bytes + 255) & ~static_cast<size_t>(255); }
+    };
+    Arena arena;
+    bool in_arena() const { return arena.base != nullptr; }
     void* dalloc(size_t bytes);
     void dfree(void* p, size_t bytes);
     // Every allocation is rounded up to 16 bytes so small counters can be read as words.
@@ -109,7 +122,8 @@ struct DBuf {
     T* p = nullptr;
     int64_t n = 0;
     DBuf() = default;
-    DBuf(Context* c, int64_t count) : ctx(c), p(c->alloc<T>(count)), n(count) {}
+    // memory from the context's arena is not freed by the buffer (ctx stays null)
+    DBuf(Context* c, int64_t count) : ctx(c->in_arena() ? nullptr : c), p(c->alloc<T>(count)), n(count) {}
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
     DBuf(DBuf&& o) noexcept : ctx(o.ctx), p(o.p), n(o.n) { o.p = nullptr; }
@@ -135,14 +149,38 @@ struct DBuf {
     }
 };
 
+// Capacities of a setup sized on the device (a solve for new positions captured as one CUDA
+// graph).  The host-driven setup reads each count back before it allocates and launches the
+// next step.  Sized on the device, every buffer is allocated once at its capacity, every count
+// stays in device memory, kernels launch over the capacity and skip what lies beyond the
+// count, and a solve that would exceed a capacity raises `flag` (device memory, 0 = all held)
+// instead of writing past it.  Entries beyond a count are inert: nodes with level -1, no
+// particles and no children; batches with leaf id -1; list counts of 0.
+struct Caps {
+    int32_t nodes = 0;                // tree nodes
+    int32_t levels = 0;               // level iterations of the tree build
+    int32_t level_nodes = 0;          // nodes of one level
+    int64_t chunks = 0;               // particle chunks of one level
+    int64_t app = 0, dir = 0;         // list entries
+    int32_t slots = 0;                // clusters with modified charges
+    int32_t up_items = 0;             // leaf-sum items of the upward pass
+    int32_t m2m = 0;                  // marked internal nodes of one level
+    int64_t items = 0;                // sweep work items
+    int64_t partial_len = 0;          // item partials (doubles)
+    int64_t mpart_len = 0;            // mutual rows (floats)
+    int32_t* flag = nullptr;          // device overflow flag
+};
+
 // A built tree (nodes in DFS pre-order; particles in tree order).
 struct Tree {
     Context* ctx = nullptr;
     int64_t n = 0;
     int32_t max_leaf = 0;
-    int64_t n_nodes = 0, n_leaves = 0;
+    int64_t n_nodes = 0, n_leaves = 0;  // sized on the device: the capacities
     int32_t n_levels = 0;
     bool has_q = false;
+    const Caps* caps = nullptr;       // non-null: sized on the device
+    DBuf<int32_t> dcount;             // sized on the device: {nodes, leaves} in device memory
     DBuf<double> px, py, pz, pq;      // particles in tree order
     DBuf<int32_t> perm;               // perm[i] = original index
     DBuf<int32_t> begin, count, parent, level, nch, child;  // child: 8 per node
@@ -173,6 +211,10 @@ struct Plan {
                                       // check, bit 2 mutual owner, bit 3 mutual partner (skip)
     DBuf<float> dir_tau2;             // per direct entry: r^2 below which pairs are redone in FP64
     std::vector<int64_t> h_cost;      // host copy of the items' interaction counts (queue order)
+    // sized on the device: the plan's totals ({cost, items, partial length, mutual length}) and
+    // the sweep's first item (the sorted items fill the end of the capacity)
+    DBuf<int64_t> dwords;
+    DBuf<int32_t> dstart;
 };
 
 struct Lists {
@@ -182,16 +224,19 @@ struct Lists {
     const Tree* st = nullptr;
     double theta = 0.0;
     int degree = 0;
-    int64_t n_batches = 0, n_app = 0, n_dir = 0;
+    int64_t n_batches = 0, n_app = 0, n_dir = 0;   // sized on the device: the capacities
     DBuf<int32_t> app_off, app_ids, dir_off, dir_ids;
+    const Caps* caps = nullptr;       // non-null: sized on the device
+    DBuf<int32_t> dcount;             // sized on the device: {approximation, direct} entries
     Plan plan;
 };
 
 // ---- steps (implemented in tree.cu, lists.cu, upward.cu, sweep.cu, direct.cu) -------
 void build_tree(Context* ctx, const double* x, const double* y, const double* z,
-                const double* q, int64_t n, int32_t max_leaf, Tree* out);
+                const double* q, int64_t n, int32_t max_leaf, Tree* out,
+                const Caps* caps = nullptr);
 void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int degree,
-                 Lists* out);
+                 Lists* out, const Caps* caps = nullptr);
 // The lists of the selected batches only (strictly increasing batch indices); the other
 // batches get empty lists.
 void select_lists(Context* ctx, const Lists* L, const int32_t* sel, int64_t n_sel, Lists* out);
@@ -202,6 +247,9 @@ void compute_modified_charges(Context* ctx, Tree* st, const Lists* lists, int de
 // launches kernels (no allocation, no synchronisation), so it can be captured in a graph.
 struct UpwardPlan {
     int degree = 0, precision = 0;
+    const Caps* caps = nullptr;      // non-null: sized on the device (counts below are capacities)
+    DBuf<int32_t> dcount;            // {slots, items} in device memory
+    DBuf<int32_t> lev;               // sized on the device: per level count, offset, cursor
     int32_t n_slots = 0, n_items = 0, chunk = 1;
     DBuf<int32_t> slot_node, item0, list;
     DBuf<int4> items;
@@ -212,10 +260,23 @@ void prepare_upward(Context* ctx, Tree* st, const Lists* lists, int degree, int 
                     UpwardPlan* up);
 void run_upward(Context* ctx, Tree* st, const UpwardPlan& up);
 
-// A solve with fixed positions captured as one CUDA graph (graph.cu).
+// The whole of Algorithm 1 (api.cu): trees, lists, upward pass beside the plan, sweep.
+void solve_device(Context* c, const double* x, const double* y, const double* z,
+                  const double* q, int64_t n, const bltc_params& p, double* phi);
+// Capacities of a tree from its node arrays (tree.cu): nodes, levels, the widest level, the
+// most particle chunks of a level.  Reads the tree back to the host.
+void tree_counts(Context* ctx, const Tree& t, Caps* caps);
+
+// A solve captured as one CUDA graph (graph.cu): with fixed positions (only the charges are
+// read at a launch) or, sized on the device, for new positions at every launch.
 struct GraphSolve;
 GraphSolve* graph_create(Context* c, const double* x, const double* y, const double* z, const double* q,
                          int64_t n, const bltc_params& p, double* phi);
+GraphSolve* graph_create_positions(Context* c, const double* x, const double* y, const double* z,
+                                   const double* q, int64_t n, const bltc_params& p, double* phi,
+                                   double headroom);
+// {kernels per launch, launches, launches redone on the host path, captures}
+void graph_info(const GraphSolve* g, int64_t out[4]);
 void graph_launch(Context* c, GraphSolve* g);
 int64_t graph_kernels(const GraphSolve* g);
 void graph_destroy(GraphSolve* g);

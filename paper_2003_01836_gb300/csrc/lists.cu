@@ -82,6 +82,14 @@ __global__ void k_lists(ListArgs a) {
     const int64_t b = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     if (b >= a.n_batches) return;
     const int32_t B = a.b_leaves[b];
+    if (B < 0) {                       // no batch (beyond the count of a tree sized on the device)
+        if (!kFill && lane == 0) a.app_cnt[b] = a.dir_cnt[b] = 0;
+        return;
+    }
+    // entries beyond the batch's range are not written (sized on the device, the offsets are
+    // clamped to the capacities, so a batch may get fewer slots than it has entries)
+    const int32_t app_end = kFill ? a.app_off[b + 1] - a.app_off[b] : 0;
+    const int32_t dir_end = kFill ? a.dir_off[b + 1] - a.dir_off[b] : 0;
     const double cbx = a.b_center[3 * B], cby = a.b_center[3 * B + 1], cbz = a.b_center[3 * B + 2];
     const double rB = a.b_radius[B];
     int2* st = reinterpret_cast<int2*>(a.stack) + b * a.stack_cap;
@@ -96,10 +104,10 @@ __global__ void k_lists(ListArgs a) {
     while (sp > 0) {
         const int2 top = st[--sp];
         if (top.y == kApprox) {
-            if (kFill && lane == 0) app[na] = top.x;
+            if (kFill && lane == 0 && na < app_end) app[na] = top.x;
             ++na;
         } else if (top.y == kDirect) {
-            if (kFill && lane == 0) dir[nd] = top.x;
+            if (kFill && lane == 0 && nd < dir_end) dir[nd] = top.x;
             ++nd;
         } else {
             const int k = a.s_nch[top.x];
@@ -128,6 +136,21 @@ __global__ void k_append_total(int32_t* off, int64_t n, const int32_t* total) {
     off[n] = *total;
 }
 
+__global__ void k_raise_if(const int32_t* src, int32_t* flag) {
+    if (*src) atomicOr(flag, 1);
+}
+
+// Sized on the device: offsets clamped to the capacity, so that every batch's range lies in
+// the id array; a total beyond it raises the flag.
+__global__ void k_clamp_offsets(int32_t* off, int64_t n, int64_t cap, int32_t* cap_flag) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    if (off[i] > cap) {
+        off[i] = static_cast<int32_t>(cap);
+        if (i == n) atomicOr(cap_flag, 1);
+    }
+}
+
 // Copies the list entries of the selected batches (one block per batch) to their places in
 // the new CSR arrays.
 __global__ void k_gather_lists(const int32_t* __restrict__ sel, int64_t n_sel,
@@ -143,7 +166,7 @@ __global__ void k_gather_lists(const int32_t* __restrict__ sel, int64_t n_sel,
 }  // namespace
 
 void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int degree,
-                 Lists* out) {
+                 Lists* out, const Caps* caps) {
     require(degree >= 1 && degree <= BLTC_MAX_DEGREE, "lists: degree out of range");
     require(theta >= 0.0 && theta < 1.0, "lists: theta must satisfy 0 <= theta < 1");
     cudaStream_t s = ctx->stream;
@@ -179,6 +202,7 @@ void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int
     a.app_cnt = cnt.p;
     a.dir_cnt = cnt.p + nb;
     a.overflow = flags.p + 2;
+    if (caps) require(st->caps == caps && bt->caps != nullptr, "lists: trees not sized on the device");
     BLTC_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int32_t), s));
     k_lists<false><<<grid_for(32 * nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("lists count");
@@ -186,6 +210,25 @@ void build_lists(Context* ctx, const Tree* bt, const Tree* st, double theta, int
     exclusive_scan_i32(ctx, a.dir_cnt, out->dir_off.p, nb, flags.p + 1);
     k_append_total<<<1, 1, 0, s>>>(out->app_off.p, nb, flags.p); ++ctx->launches;
     k_append_total<<<1, 1, 0, s>>>(out->dir_off.p, nb, flags.p + 1); ++ctx->launches;
+    if (caps) {
+        // entry counts stay in device memory; the fill writes only batches that fit
+        out->caps = caps;
+        out->n_app = caps->app;
+        out->n_dir = caps->dir;
+        out->app_ids = DBuf<int32_t>(ctx, caps->app);
+        out->dir_ids = DBuf<int32_t>(ctx, caps->dir);
+        k_raise_if<<<1, 1, 0, s>>>(flags.p + 2, caps->flag); ++ctx->launches;   // stack overflow
+        out->dcount = std::move(flags);
+        k_clamp_offsets<<<grid_for(nb + 1, 256), 256, 0, s>>>(out->app_off.p, nb, caps->app, caps->flag); ++ctx->launches;
+        k_clamp_offsets<<<grid_for(nb + 1, 256), 256, 0, s>>>(out->dir_off.p, nb, caps->dir, caps->flag); ++ctx->launches;
+        a.app_off = out->app_off.p;
+        a.dir_off = out->dir_off.p;
+        a.app_ids = out->app_ids.p;
+        a.dir_ids = out->dir_ids.p;
+        k_lists<true><<<grid_for(32 * nb, kThreads), kThreads, 0, s>>>(a); ++ctx->launches;
+        BLTC_LAUNCH_CHECK("lists fill");
+        return;
+    }
     const int32_t* w = reinterpret_cast<const int32_t*>(ctx->read_words(flags.p, 2));
     const int32_t n_app = w[0], n_dir = w[1], overflow = w[2];
     if (overflow) throw Error(BLTC_ERR_CUDA, "lists: traversal stack overflow");

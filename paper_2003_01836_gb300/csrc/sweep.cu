@@ -118,7 +118,18 @@ struct PlanArgs {
     int64_t* mlen;               // per direct entry: mutual row length (owners only)
     const int64_t* moff_e;       // per direct entry: exclusive scan of mlen
     int64_t* dir_moff;
+    // sized on the device (else null / unbounded): the direct entry count, the total cost from
+    // which the item cut is derived, the item capacity and the overflow flag
+    const int32_t* n_dir_dev;
+    const unsigned long long* total_dev;
+    int64_t cut_div;
+    int64_t item_cap;
+    int32_t* cap_flag;
 };
+
+__device__ __forceinline__ int64_t dir_count(const PlanArgs& a, int64_t n_dir) {
+    return a.n_dir_dev && *a.n_dir_dev < n_dir ? *a.n_dir_dev : n_dir;
+}
 
 // The batch owning direct entry e: the last b with dir_off[b] <= e.
 __device__ __forceinline__ int64_t batch_of_entry(const PlanArgs& a, int64_t e) {
@@ -149,7 +160,7 @@ __device__ __forceinline__ int64_t dir_cost(const PlanArgs& a, int64_t e, int64_
 // the test.
 __global__ void k_dir_flags(PlanArgs a, int64_t n_dir) {
     const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= n_dir) return;
+    if (e >= dir_count(a, n_dir)) return;
     const int B = a.b_leaves[batch_of_entry(a, e)];
     const int C = a.dir_ids[e];
     bool separated = false;
@@ -183,24 +194,25 @@ __global__ void k_dir_flags(PlanArgs a, int64_t n_dir) {
 // in DFS order, i.e. sorted by node id, so the partner entry is found by binary search.
 __global__ void k_leaf_index(PlanArgs a, int32_t* lidx) {
     const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (b < a.n_batches) lidx[a.b_leaves[b]] = static_cast<int32_t>(b);
+    if (b < a.n_batches && a.b_leaves[b] >= 0) lidx[a.b_leaves[b]] = static_cast<int32_t>(b);
 }
 
 __global__ void k_mutual_mark(PlanArgs a, int64_t n_dir) {
     const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= n_dir) return;
+    if (e >= dir_count(a, n_dir)) return;
     const int64_t b = batch_of_entry(a, e);
     const int A = a.b_leaves[b], C = a.dir_ids[e];
     int32_t partner = -1;
     int64_t len = 0;
     const int b2 = C != A && a.s_nch[C] == 0 ? a.lidx[C] : -1;
     if (b2 >= 0) {
-        int lo = a.dir_off[b2], hi = a.dir_off[b2 + 1];       // search A in [lo, hi)
+        const int end = a.dir_off[b2 + 1];
+        int lo = a.dir_off[b2], hi = end;                     // search A in [lo, hi)
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (a.dir_ids[mid] < A) lo = mid + 1; else hi = mid;
         }
-        if (lo < a.dir_off[b2 + 1] && a.dir_ids[lo] == A) {
+        if (lo < end && a.dir_ids[lo] == A) {
             partner = lo;
             if (b < b2) {
                 a.dir_sel[e] |= kSelMutual;
@@ -216,7 +228,7 @@ __global__ void k_mutual_mark(PlanArgs a, int64_t n_dir) {
 
 __global__ void k_mutual_moff(PlanArgs a, int64_t n_dir) {
     const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= n_dir) return;
+    if (e >= dir_count(a, n_dir)) return;
     const uint8_t sel = a.dir_sel[e];
     a.dir_moff[e] = (sel & kSelMutual) ? a.moff_e[e] : ((sel & kSelSkip) ? a.moff_e[a.partner[e]] : -1);
 }
@@ -224,6 +236,10 @@ __global__ void k_mutual_moff(PlanArgs a, int64_t n_dir) {
 __global__ void k_batch_cost(PlanArgs a) {
     const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (b >= a.n_batches) return;
+    if (a.b_leaves[b] < 0) {
+        a.cost[b] = 0;
+        return;
+    }
     const int64_t nb = a.b_count[a.b_leaves[b]];
     int64_t c = static_cast<int64_t>(a.app_off[b + 1] - a.app_off[b]) * a.P * nb;
     for (int e = a.dir_off[b]; e < a.dir_off[b + 1]; ++e) c += dir_cost(a, e, nb);
@@ -237,6 +253,21 @@ template <bool kFill>
 __global__ void k_chunks(PlanArgs a) {
     const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (b >= a.n_batches) return;
+    if (a.b_leaves[b] < 0) {
+        if (!kFill) {
+            a.n_chunks[b] = 0;
+            a.part_len[b] = 0;
+        }
+        return;
+    }
+    if (kFill && a.item_off[b] + a.n_chunks[b] > a.item_cap) {
+        atomicOr(a.cap_flag, 1);
+        return;
+    }
+    if (a.total_dev) {
+        const int64_t t = static_cast<int64_t>(*a.total_dev) / a.cut_div;
+        a.cut = t > (int64_t(1) << 20) ? t : (int64_t(1) << 20);
+    }
     const int64_t nb = a.b_count[a.b_leaves[b]];
     const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0;
     const int d0 = a.dir_off[b], nd = a.dir_off[b + 1] - d0;
@@ -264,7 +295,12 @@ __global__ void k_chunks(PlanArgs a) {
 
 // Interaction count of each item (for longest-first ordering).
 __global__ void k_item_costs(PlanArgs a, const int4* __restrict__ items, int64_t n_items,
-                             int64_t* cost) {
+                             int64_t* cost, const int32_t* n_items_dev) {
+    if (n_items_dev) {
+        // sized on the device: unwritten items follow an exceeded capacity (nothing runs then)
+        if (*a.cap_flag) return;
+        if (*n_items_dev < n_items) n_items = *n_items_dev;
+    }
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n_items) return;
     const int4 it = items[i];
@@ -315,7 +351,8 @@ __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* 
                            const int32_t* __restrict__ n_chunks, const int64_t* __restrict__ part_off,
                            const double* __restrict__ partials, const int32_t* __restrict__ dir_off,
                            const uint8_t* __restrict__ dir_sel, const int64_t* __restrict__ dir_moff,
-                           const float* __restrict__ mpart, double* __restrict__ phi) {
+                           const float* __restrict__ mpart, double* __restrict__ phi,
+                           const int32_t* __restrict__ stop) {
     constexpr int U = 8;          // targets per thread
     constexpr int kRows = 256;    // row pointers gathered per round
     constexpr int kAhead = 4;     // rows loaded before they are added
@@ -324,6 +361,8 @@ __global__ void k_finalize(const int32_t* __restrict__ b_leaves, const int32_t* 
     __shared__ bool s_more;
     const int b = blockIdx.x;
     const int B = b_leaves[b];
+    // sized on the device: no batch here, or a capacity was exceeded (the solve is redone)
+    if (B < 0 || (stop && *stop)) return;
     const int tb = b_begin[B], nb = b_count[B], K = n_chunks[b];
     const double* p = partials + part_off[b];
     const int e1 = dir_off[b + 1];
@@ -403,12 +442,108 @@ __global__ void k_counts(const int32_t* b_leaves, const int32_t* b_count, const 
     atomicAdd(&out[3], static_cast<unsigned long long>((app + dw) * slots));
 }
 
+// ---- the plan sized on the device --------------------------------------------------------
+//
+// Items are placed longest first by a bucket sort on the device: a key per item from its cost
+// (four buckets per octave, larger costs first), a histogram, offsets, and a scatter whose order
+// within a bucket follows the atomics.  As on the host, the order changes no result (each item
+// writes its own partials and rows), only how the persistent sweep's blocks share the work.
+// The sorted items occupy the end of the item array, [cap - n, cap), so that the sweep, whose
+// queue ends at the capacity, starts its counter at cap - n (cap when a capacity was exceeded:
+// no item runs) and stays the same kernel as the host-driven path launches.
+constexpr int kBuckets = 256;
+
+__device__ __forceinline__ int cost_bucket(int64_t c) {
+    if (c <= 0) return kBuckets - 1;
+    const int e = 63 - __clzll(static_cast<unsigned long long>(c));
+    const int f = e >= 2 ? static_cast<int>((static_cast<unsigned long long>(c) >> (e - 2)) & 3) : 0;
+    const int level = 4 * e + f;              // 0 .. 255, increasing with the cost
+    return kBuckets - 1 - level;              // longest first
+}
+
+__global__ void k_bucket_hist(const int64_t* __restrict__ cost, const int32_t* __restrict__ n_dev,
+                              int64_t cap, int32_t* hist) {
+    const int64_t n = min(static_cast<int64_t>(*n_dev), cap);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(&hist[cost_bucket(cost[i])], 1);
+}
+
+// One warp: bucket offsets from cap - n, zero cursors, the sweep's first item, and the checks
+// of the plan's totals against their capacities.
+__global__ void k_bucket_offsets(int32_t* hist, const int64_t* __restrict__ words, int64_t item_cap,
+                                 int64_t partial_cap, int64_t mpart_cap, int32_t* start, int32_t* cap_flag) {
+    const int32_t n = reinterpret_cast<const int32_t*>(words + 1)[0];
+    const bool over = n > item_cap || words[2] > partial_cap || words[3] > mpart_cap;
+    if (threadIdx.x == 0) {
+        if (over) atomicOr(cap_flag, 1);
+        int64_t o = item_cap - min(static_cast<int64_t>(n), item_cap);
+        for (int k = 0; k < kBuckets; ++k) {
+            const int32_t h = hist[k];
+            hist[kBuckets + k] = static_cast<int32_t>(o);
+            hist[2 * kBuckets + k] = 0;
+            o += h;
+        }
+        *start = static_cast<int32_t>(item_cap - min(static_cast<int64_t>(n), item_cap));
+    }
+}
+
+__global__ void k_bucket_scatter(const int4* __restrict__ raw, const int64_t* __restrict__ cost,
+                                 const int32_t* __restrict__ n_dev, int64_t cap, int32_t* hist,
+                                 int4* __restrict__ sorted) {
+    const int64_t n = min(static_cast<int64_t>(*n_dev), cap);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int k = cost_bucket(cost[i]);
+        sorted[hist[kBuckets + k] + atomicAdd(&hist[2 * kBuckets + k], 1)] = raw[i];
+    }
+}
+
+// The persistent sweep's queue counter: the first real item, or the capacity when the setup
+// exceeded a capacity (the sweep then runs nothing and the solve is redone on the host path).
+__global__ void k_counter_start(unsigned int* counter, const int32_t* __restrict__ start,
+                                const int32_t* __restrict__ stop, int64_t cap) {
+    *counter = *stop ? static_cast<unsigned int>(cap) : static_cast<unsigned int>(*start);
+}
+
 }  // namespace
+
+static void build_plan_sized(Context* ctx, Lists* L, PlanArgs a, DBuf<int32_t>& item_off,
+                             DBuf<int64_t>& words, int degree) {
+    cudaStream_t s = ctx->stream;
+    const Caps* caps = L->caps;
+    Plan& pl = L->plan;
+    const int64_t cap = a.item_cap;
+    pl.n_items = cap;
+    pl.partial_len = std::max<int64_t>(1, caps->partial_len);
+    pl.dwords = std::move(words);
+    pl.dstart = DBuf<int32_t>(ctx, 1);
+    DBuf<int4> raw(ctx, cap);
+    DBuf<int64_t> icost(ctx, cap);
+    DBuf<int32_t> hist(ctx, 3 * kBuckets);
+    pl.items = DBuf<int4>(ctx, cap);
+    const int32_t* n_dev = reinterpret_cast<const int32_t*>(pl.dwords.p + 1);
+    a.item_off = item_off.p;
+    a.items = raw.p;
+    k_chunks<true><<<grid_for(L->n_batches, 128), 128, 0, s>>>(a); ++ctx->launches;
+    k_item_costs<<<grid_for(cap, 256), 256, 0, s>>>(a, raw.p, cap, icost.p, n_dev); ++ctx->launches;
+    BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * kBuckets, s));
+    const unsigned g = grid_for(cap, 256, 4 * std::max(1, ctx->sm_count));
+    k_bucket_hist<<<g, 256, 0, s>>>(icost.p, n_dev, cap, hist.p); ++ctx->launches;
+    k_bucket_offsets<<<1, 32, 0, s>>>(hist.p, pl.dwords.p, cap, pl.partial_len,
+                                      pl.mutual ? pl.mpart_len : INT64_MAX, pl.dstart.p, caps->flag); ++ctx->launches;
+    k_bucket_scatter<<<g, 256, 0, s>>>(raw.p, icost.p, n_dev, cap, hist.p, pl.items.p); ++ctx->launches;
+    BLTC_LAUNCH_CHECK("plan items (sized on the device)");
+    pl.h_cost.clear();
+    pl.degree = degree;
+    pl.valid = true;
+}
 
 void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
     cudaStream_t s = ctx->stream;
     const int64_t nb = L->n_batches;
     const int64_t np1 = degree + 1;
+    const Caps* caps = L->caps;
     Plan& pl = L->plan;
     pl.valid = false;
     PlanArgs a{};
@@ -420,6 +555,12 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
     a.dir_ids = L->dir_ids.p;
     a.n_batches = nb;
     a.P = np1 * np1 * np1;
+    a.item_cap = INT64_MAX;
+    if (caps) {
+        a.n_dir_dev = L->dcount.p + 1;
+        a.cap_flag = caps->flag;
+        a.item_cap = std::max<int64_t>(1, caps->items);
+    }
     // per direct entry: the self-pair and close-pair flags, then the mutual pairs
     pl.dir_sel = DBuf<uint8_t>(ctx, L->n_dir);
     pl.dir_tau2 = DBuf<float>(ctx, L->n_dir);
@@ -446,6 +587,7 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
         DBuf<int64_t> mlen(ctx, L->n_dir), moff_e(ctx, L->n_dir);
         pl.dir_moff = DBuf<int64_t>(ctx, L->n_dir);
         BLTC_CUDA(cudaMemsetAsync(lidx.p, 0xff, sizeof(int32_t) * m, s));
+        if (caps) BLTC_CUDA(cudaMemsetAsync(mlen.p, 0, sizeof(int64_t) * L->n_dir, s));
         a.s_nch = L->st->nch.p;
         a.lidx = lidx.p;
         a.partner = partner.p;
@@ -464,11 +606,18 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
     a.total = reinterpret_cast<unsigned long long*>(words.p);
     k_batch_cost<<<grid_for(nb, 128), 128, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("plan cost");
-    const int64_t* w0 = ctx->read_words(words.p, 4);
-    const int64_t total = w0[0];
-    if (pl.mutual) pl.mpart_len = w0[3];
     const int64_t blocks = kMinBlocks * static_cast<int64_t>(std::max(1, ctx->sm_count));
-    a.cut = std::max<int64_t>(total / (blocks * kItemsPerBlock), int64_t(1) << 20);
+    if (caps) {
+        // the cut follows from the total cost in device memory
+        a.total_dev = reinterpret_cast<const unsigned long long*>(words.p);
+        a.cut_div = blocks * kItemsPerBlock;
+        pl.mpart_len = pl.mutual ? std::max<int64_t>(1, caps->mpart_len) : 0;
+    } else {
+        const int64_t* w0 = ctx->read_words(words.p, 4);
+        const int64_t total = w0[0];
+        if (pl.mutual) pl.mpart_len = w0[3];
+        a.cut = std::max<int64_t>(total / (blocks * kItemsPerBlock), int64_t(1) << 20);
+    }
     pl.n_chunks = DBuf<int32_t>(ctx, nb);
     pl.part_off = DBuf<int64_t>(ctx, nb);
     DBuf<int32_t> item_off(ctx, nb);
@@ -478,6 +627,10 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
     BLTC_LAUNCH_CHECK("plan chunks");
     exclusive_scan_i32(ctx, pl.n_chunks.p, item_off.p, nb, reinterpret_cast<int32_t*>(words.p + 1));
     exclusive_scan_i64(ctx, part_len.p, pl.part_off.p, nb, words.p + 2);
+    if (caps) {
+        build_plan_sized(ctx, L, a, item_off, words, degree);
+        return;
+    }
     const int64_t* w = ctx->read_words(words.p, 3);
     pl.n_items = *reinterpret_cast<const int32_t*>(w + 1);
     pl.partial_len = w[2];
@@ -491,7 +644,7 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual) {
     // writes its own partials); ties keep batch order (stable sort).
     if (pl.n_items > 1) {
         DBuf<int64_t> icost(ctx, pl.n_items);
-        k_item_costs<<<grid_for(pl.n_items, 256), 256, 0, s>>>(a, pl.items.p, pl.n_items, icost.p); ++ctx->launches;
+        k_item_costs<<<grid_for(pl.n_items, 256), 256, 0, s>>>(a, pl.items.p, pl.n_items, icost.p, nullptr); ++ctx->launches;
         BLTC_LAUNCH_CHECK("plan costs");
         std::vector<int4> h_items(static_cast<size_t>(pl.n_items));
         std::vector<int64_t> h_cost(static_cast<size_t>(pl.n_items));
@@ -603,7 +756,11 @@ void run_sweep(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const blt
                double* phi, const SweepBuffers& b) {
     cudaStream_t s = ctx->stream;
     const Plan& pl = L->plan;
-    BLTC_CUDA(cudaMemsetAsync(b.counter.p, 0, sizeof(unsigned int), s));
+    if (L->caps) {
+        k_counter_start<<<1, 1, 0, s>>>(b.counter.p, pl.dstart.p, L->caps->flag, pl.n_items); ++ctx->launches;
+    } else {
+        BLTC_CUDA(cudaMemsetAsync(b.counter.p, 0, sizeof(unsigned int), s));
+    }
     SweepArgs a = make_args(ctx, L, bt, st, p, b.partials.p, b.counter.p);
     a.mpart = pl.mutual ? b.mpart.p : nullptr;
     const int per_sm = p.precision == BLTC_PRECISION_MIXED ? kMinBlocks : 2;
@@ -641,7 +798,8 @@ void run_sweep(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const blt
     ctx->mark(Context::kSweepEnd);
     k_finalize<<<static_cast<unsigned>(L->n_batches), 256, 0, s>>>(
         bt->leaves.p, bt->begin.p, bt->count.p, bt->perm.p, pl.n_chunks.p, pl.part_off.p,
-        b.partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi); ++ctx->launches;
+        b.partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi,
+        L->caps ? L->caps->flag : nullptr); ++ctx->launches;
     BLTC_LAUNCH_CHECK("finalize");
     ctx->mark(Context::kEnd);
 }
@@ -691,7 +849,7 @@ void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, co
     ctx->mark(Context::kSweepEnd);
     k_finalize<<<static_cast<unsigned>(L->n_batches), 256, 0, s>>>(
         bt->leaves.p, bt->begin.p, bt->count.p, bt->perm.p, pl.n_chunks.p, pl.part_off.p,
-        partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi); ++ctx->launches;
+        partials.p, L->dir_off.p, pl.dir_sel.p, a.dir_moff, a.mpart, phi, nullptr); ++ctx->launches;
     BLTC_LAUNCH_CHECK("finalize hermite");
     ctx->mark(Context::kEnd);
 }
@@ -861,7 +1019,7 @@ int MultiSweep::run_slice(int64_t budget, int max_requests, std::vector<void*>* 
         k_finalize<<<static_cast<unsigned>(jb->j.L->n_batches), 256, 0, s>>>(
             jb->j.bt->leaves.p, jb->j.bt->begin.p, jb->j.bt->count.p, jb->j.bt->perm.p, pl.n_chunks.p,
             pl.part_off.p, jb->partials.p, jb->j.L->dir_off.p, pl.dir_sel.p,
-            pl.mutual ? pl.dir_moff.p : nullptr, pl.mutual ? jb->mpart.p : nullptr, jb->j.phi);
+            pl.mutual ? pl.dir_moff.p : nullptr, pl.mutual ? jb->mpart.p : nullptr, jb->j.phi, nullptr);
         ++ctx_->launches;
         BLTC_LAUNCH_CHECK("finalize multi");
         finished->push_back(jb->tag);

@@ -39,6 +39,8 @@ struct UpArgs {
     const int4* items;                // {slot, first particle, end particle, -}
     double* partial;                  // [n_items * P]
     int np1;
+    const int32_t* n_items_dev;       // sized on the device: the item count, else null
+    const int32_t* stop;              // sized on the device: the overflow flag
 };
 
 // Chebyshev point k of [lo, hi] (Eq. 6 mapped linearly; s_0 = hi and s_n = lo exactly).
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
     F* fac2 = reinterpret_cast<F*>(smem_raw);
     F* fac0 = fac2 + kTile * np4;
     F* fac1 = fac0 + np1 * stride;
+    if (a.n_items_dev && (static_cast<int>(blockIdx.x) >= *a.n_items_dev || *a.stop)) return;
     const int4 it = a.items[blockIdx.x];
     const int node = a.slot_node[it.x];
     const int tid = threadIdx.x;
@@ -255,9 +258,11 @@ __global__ void __launch_bounds__(kThreads) k_upward_partial(UpArgs a) {
 
 __global__ void k_upward_reduce(const double* __restrict__ partial,
                                 const int32_t* __restrict__ item0, int P, double* qhat64,
-                                float* qhat32) {
+                                float* qhat32, const int32_t* n_slots_dev, const int32_t* stop,
+                                int32_t item_cap) {
     const int slot = blockIdx.x;
-    const int i0 = item0[slot], i1 = item0[slot + 1];
+    if (n_slots_dev && (slot >= *n_slots_dev || *stop)) return;
+    const int i0 = item0[slot], i1 = min(item0[slot + 1], item_cap);
     for (int k = threadIdx.x; k < P; k += blockDim.x) {
         double s = 0.0;
         for (int i = i0; i < i1; ++i) s += partial[static_cast<int64_t>(i) * P + k];
@@ -267,7 +272,8 @@ __global__ void k_upward_reduce(const double* __restrict__ partial,
 }
 
 __global__ void k_mark_from_lists(const int32_t* __restrict__ app_ids, int64_t n,
-                                  int32_t* flag) {
+                                  int32_t* flag, const int32_t* n_dev) {
+    if (n_dev && *n_dev < n) n = *n_dev;
     int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < n) flag[app_ids[i]] = 1;
 }
@@ -280,10 +286,15 @@ __global__ void k_mark_by_size(const int32_t* __restrict__ count, int64_t m, int
 
 __global__ void k_slots(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
                         const int32_t* __restrict__ count, const int32_t* __restrict__ nch,
-                        int64_t m, int32_t* qslot, int32_t* slot_node, int32_t* slot_items) {
+                        int64_t m, int32_t* qslot, int32_t* slot_node, int32_t* slot_items,
+                        int32_t slot_cap, int32_t* cap_flag) {
     int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (v >= m) return;
-    if (flag[v]) {
+    if (flag[v] && pos[v] >= slot_cap) {
+        // sized on the device and past the capacity: a valid slot keeps every index in range
+        atomicOr(cap_flag, 1);
+        qslot[v] = slot_cap - 1;
+    } else if (flag[v]) {
         qslot[v] = pos[v];
         slot_node[pos[v]] = static_cast<int32_t>(v);
         // particles are summed only at the leaves; parents come from their children (M2M)
@@ -295,15 +306,34 @@ __global__ void k_slots(const int32_t* __restrict__ flag, const int32_t* __restr
 
 __global__ void k_items(const int32_t* __restrict__ slot_node,
                         const int32_t* __restrict__ item0, const int32_t* __restrict__ begin,
-                        const int32_t* __restrict__ count, int64_t n_slots, int4* items) {
+                        const int32_t* __restrict__ count, int64_t n_slots, int4* items,
+                        const int32_t* n_slots_dev, int32_t item_cap, int32_t* cap_flag) {
+    if (n_slots_dev && *n_slots_dev < n_slots) n_slots = *n_slots_dev;
     int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
     const int v = slot_node[s];
     const int b = begin[v], c = count[v];
     // a slot owns items item0[s] .. item0[s+1]-1: none for internal nodes (built by M2M)
     const int i1 = item0[s + 1];
+    if (i1 > item_cap) {
+        atomicOr(cap_flag, 1);
+        return;
+    }
     for (int i = item0[s], p0 = b; i < i1; ++i, p0 += kItem)
         items[i] = make_int4(static_cast<int>(s), p0, min(b + c, p0 + kItem), 0);
+}
+
+// Sized on the device: the offsets of the levels' marked internal nodes (lev[nl + L]) from
+// their counts (lev[L]), zero cursors (lev[2 nl + L]), and the flag when a level holds more
+// than the capacity.
+__global__ void k_level_offsets(int32_t* lev, int nl, int32_t cap, int32_t* cap_flag) {
+    int32_t o = 0;
+    for (int L = 0; L < nl; ++L) {
+        lev[nl + L] = o;
+        lev[2 * nl + L] = 0;
+        o += lev[L];
+        if (lev[L] > cap) atomicOr(cap_flag, 1);
+    }
 }
 
 __global__ void k_append_total(int32_t* off, int64_t n, const int32_t* total) { off[n] = *total; }
@@ -343,7 +373,23 @@ struct M2MArgs {
     double* qhat64;
     float* qhat32;
     int np1;
+    // sized on the device: per level the count (lev[L]) and the offset in the list
+    // (lev[nl + L]) of the marked internal nodes, the capacity per level, and the overflow flag
+    const int32_t* lev;
+    int nl;
+    int32_t cap;
+    const int32_t* stop;
 };
+
+// The parent of block group j of a launch: nodes[j] (host-driven) or, sized on the device,
+// entry p0 + j of level L's part of the list; -1 when beyond the level's count.
+__device__ __forceinline__ int m2m_parent(const M2MArgs& a, const int32_t* nodes, int L, int p0, int j) {
+    if (!a.lev) return nodes[j];
+    if (*a.stop) return -1;
+    const int k = p0 + j;
+    if (k >= min(a.lev[L], a.cap)) return -1;
+    return nodes[a.lev[a.nl + L] + k];
+}
 
 // Exact transfer of the children's modified charges to their parent (the parent's Lagrange
 // polynomials L^P_k have degree n in each variable, so a child's tensor interpolant (Eq. 4-8)
@@ -354,10 +400,11 @@ struct M2MArgs {
 // hits as in Sec. II-C), then three mode products into the pair's scratch row.  A second
 // kernel adds a parent's rows in child order.  FP64 throughout.
 __global__ void __launch_bounds__(256) k_m2m_child(M2MArgs a, const int32_t* __restrict__ nodes,
-                                                   double* __restrict__ scratch) {
+                                                   double* __restrict__ scratch, int L, int p0) {
     extern __shared__ __align__(16) double m2m_smem[];
-    const int v = nodes[blockIdx.x >> 3], ci = static_cast<int>(blockIdx.x & 7);
-    if (ci >= a.nch[v]) return;
+    const int v = m2m_parent(a, nodes, L, p0, static_cast<int>(blockIdx.x >> 3)),
+              ci = static_cast<int>(blockIdx.x & 7);
+    if (v < 0 || ci >= a.nch[v]) return;
     const int c = a.child[8 * v + ci];
     const int np1 = a.np1, n = np1 - 1, P = np1 * np1 * np1, n2 = np1 * np1;
     double* A = m2m_smem;            // child charges, then the second mode product
@@ -424,8 +471,10 @@ __global__ void __launch_bounds__(256) k_m2m_child(M2MArgs a, const int32_t* __r
 
 // qhat of each parent: its children's rows added in child order.
 __global__ void k_m2m_sum(M2MArgs a, const int32_t* __restrict__ nodes,
-                          const double* __restrict__ scratch) {
-    const int v = nodes[blockIdx.x], nc = a.nch[v];
+                          const double* __restrict__ scratch, int L, int p0) {
+    const int v = m2m_parent(a, nodes, L, p0, static_cast<int>(blockIdx.x));
+    if (v < 0) return;
+    const int nc = a.nch[v];
     const int P = a.np1 * a.np1 * a.np1;
     const double* rows = scratch + static_cast<int64_t>(blockIdx.x) * 8 * P;
     double* q = a.qhat64 + static_cast<int64_t>(a.qslot[v]) * P;
@@ -479,19 +528,25 @@ void prepare_upward(Context* ctx, Tree* st, const Lists* lists, int degree, int 
     if (!st->has_q) throw Error(BLTC_ERR_STATE, "modified charges: source tree has no charges");
     if (lists && lists->st != st)
         throw Error(BLTC_ERR_STATE, "modified charges: lists were built for another source tree");
+    const Caps* caps = st->caps;
+    require(!caps || (lists && lists->caps == caps), "modified charges: lists sized differently");
     cudaStream_t s = ctx->stream;
     const int np1 = degree + 1;
     const int P = np1 * np1 * np1;
     const int64_t m = st->n_nodes;
     up->degree = degree;
     up->precision = precision;
+    up->caps = caps;
 
-    DBuf<int32_t> flag(ctx, m), pos(ctx, m), tot(ctx, 2);
+    DBuf<int32_t> flag(ctx, m), pos(ctx, m);
+    up->dcount = DBuf<int32_t>(ctx, 2);           // {slots, items}
+    int32_t* tot = up->dcount.p;
+    int32_t* cap_flag = caps ? caps->flag : nullptr;
     if (lists) {
         BLTC_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int32_t) * m, s));
         if (lists->n_app > 0) {
-            k_mark_from_lists<<<grid_for(lists->n_app, 256), 256, 0, s>>>(lists->app_ids.p,
-                                                                           lists->n_app, flag.p); ++ctx->launches;
+            k_mark_from_lists<<<grid_for(lists->n_app, 256), 256, 0, s>>>(
+                lists->app_ids.p, lists->n_app, flag.p, caps ? lists->dcount.p : nullptr); ++ctx->launches;
         }
     } else {
         k_mark_by_size<<<grid_for(m, 256), 256, 0, s>>>(st->count.p, m, P, flag.p); ++ctx->launches;
@@ -501,8 +556,9 @@ void prepare_upward(Context* ctx, Tree* st, const Lists* lists, int degree, int 
         k_propagate<<<grid_for(m, 256), 256, 0, s>>>(st->level.p, st->parent.p, m, L, flag.p); ++ctx->launches;
     }
     BLTC_LAUNCH_CHECK("upward propagate");
-    exclusive_scan_i32(ctx, flag.p, pos.p, m, tot.p);
-    const int32_t n_slots = *reinterpret_cast<const int32_t*>(ctx->read_words(tot.p, 1));
+    exclusive_scan_i32(ctx, flag.p, pos.p, m, tot);
+    const int32_t n_slots = caps ? std::max<int32_t>(1, caps->slots)
+                                 : *reinterpret_cast<const int32_t*>(ctx->read_words(tot, 1));
 
     st->qslot = DBuf<int32_t>(ctx, m);
     st->q_slots = n_slots;
@@ -517,24 +573,44 @@ void prepare_upward(Context* ctx, Tree* st, const Lists* lists, int degree, int 
     up->slot_node = DBuf<int32_t>(ctx, n_slots);
     up->item0 = DBuf<int32_t>(ctx, n_slots + 1);
     DBuf<int32_t> slot_items(ctx, n_slots);
+    if (caps) BLTC_CUDA(cudaMemsetAsync(slot_items.p, 0, sizeof(int32_t) * n_slots, s));
     k_slots<<<grid_for(m, 256), 256, 0, s>>>(flag.p, pos.p, st->count.p, st->nch.p, m, st->qslot.p,
-                                             up->slot_node.p, slot_items.p); ++ctx->launches;
+                                             up->slot_node.p, slot_items.p, n_slots, cap_flag); ++ctx->launches;
     BLTC_LAUNCH_CHECK("upward slots");
-    if (n_slots == 0) return;
-    exclusive_scan_i32(ctx, slot_items.p, up->item0.p, n_slots, tot.p + 1);
-    k_append_total<<<1, 1, 0, s>>>(up->item0.p, n_slots, tot.p + 1); ++ctx->launches;
-    const int32_t n_items = reinterpret_cast<const int32_t*>(ctx->read_words(tot.p, 1))[1];
+    if (!caps && n_slots == 0) return;
+    exclusive_scan_i32(ctx, slot_items.p, up->item0.p, n_slots, tot + 1);
+    k_append_total<<<1, 1, 0, s>>>(up->item0.p, n_slots, tot + 1); ++ctx->launches;
+    const int32_t n_items = caps ? std::max<int32_t>(1, caps->up_items)
+                                 : reinterpret_cast<const int32_t*>(ctx->read_words(tot, 1))[1];
     up->n_items = n_items;
     up->items = DBuf<int4>(ctx, std::max<int32_t>(n_items, 1));
     k_items<<<grid_for(n_slots, 128), 128, 0, s>>>(up->slot_node.p, up->item0.p, st->begin.p,
-                                                   st->count.p, n_slots, up->items.p); ++ctx->launches;
+                                                   st->count.p, n_slots, up->items.p,
+                                                   caps ? tot : nullptr, caps ? n_items : INT32_MAX,
+                                                   cap_flag); ++ctx->launches;
     up->partial = DBuf<double>(ctx, static_cast<int64_t>(n_items) * P);
     ctx->cheb_table(degree);
     // M2M: marked internal nodes per level, deepest level first
     const int nl = st->n_levels;
     up->h.assign(static_cast<size_t>(nl), 0);
     up->off.assign(static_cast<size_t>(nl) + 1, 0);
-    if (nl > 1) {
+    if (nl > 1 && caps) {
+        // counts, offsets and cursors stay in device memory; the launches cover the capacity
+        up->lev = DBuf<int32_t>(ctx, 3 * nl);
+        up->list = DBuf<int32_t>(ctx, m);
+        BLTC_CUDA(cudaMemsetAsync(up->lev.p, 0, sizeof(int32_t) * 3 * nl, s));
+        k_level_hist<<<grid_for(m, 256), 256, 0, s>>>(flag.p, st->nch.p, st->level.p, m, up->lev.p); ++ctx->launches;
+        k_level_offsets<<<1, 1, 0, s>>>(up->lev.p, nl, std::max<int32_t>(1, caps->m2m), caps->flag); ++ctx->launches;
+        k_level_fill<<<grid_for(m, 256), 256, 0, s>>>(flag.p, st->nch.p, st->level.p, m, up->lev.p + nl,
+                                                      up->lev.p + 2 * nl, up->list.p); ++ctx->launches;
+        BLTC_LAUNCH_CHECK("upward levels");
+        const int32_t hmax = std::max<int32_t>(1, caps->m2m);
+        for (int L = 0; L < nl; ++L) up->h[L] = hmax;
+        up->chunk = static_cast<int32_t>(std::max<int64_t>(
+            1, std::min<int64_t>(hmax, (int64_t(32) << 20) / (8 * static_cast<int64_t>(P) * 8))));
+        up->scratch = DBuf<double>(ctx, static_cast<int64_t>(up->chunk) * 8 * P);
+        up->off[nl] = 1;
+    } else if (nl > 1) {
         DBuf<int32_t> hist(ctx, 2 * nl + 1);
         up->list = DBuf<int32_t>(ctx, m);
         BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * (2 * nl + 1), s));
@@ -564,6 +640,7 @@ void run_upward(Context* ctx, Tree* st, const UpwardPlan& up) {
     const int degree = up.degree, precision = up.precision;
     const int np1 = degree + 1;
     const int P = np1 * np1 * np1;
+    const Caps* caps = up.caps;
     UpArgs a{};
     a.px = st->px.p;
     a.py = st->py.p;
@@ -578,6 +655,8 @@ void run_upward(Context* ctx, Tree* st, const UpwardPlan& up) {
     a.items = up.items.p;
     a.partial = up.partial.p;
     a.np1 = np1;
+    a.n_items_dev = caps ? up.dcount.p + 1 : nullptr;
+    a.stop = caps ? caps->flag : nullptr;
     if (up.n_items > 0) {
         if (precision == BLTC_PRECISION_MIXED) {
             const size_t sm = upward_smem<float>(np1);
@@ -592,22 +671,25 @@ void run_upward(Context* ctx, Tree* st, const UpwardPlan& up) {
         BLTC_LAUNCH_CHECK("upward partial");
     }
     k_upward_reduce<<<up.n_slots, 256, 0, s>>>(up.partial.p, up.item0.p, P, st->qhat64.p,
-                                                precision == BLTC_PRECISION_MIXED ? st->qhat32.p
-                                                                                  : nullptr); ++ctx->launches;
+                                                precision == BLTC_PRECISION_MIXED ? st->qhat32.p : nullptr,
+                                                caps ? up.dcount.p : nullptr, a.stop,
+                                                caps ? up.n_items : INT32_MAX); ++ctx->launches;
     BLTC_LAUNCH_CHECK("upward reduce");
     const int nl = static_cast<int>(up.h.size());
     if (nl > 1 && up.off[nl] > 0) {
         M2MArgs ma{st->nch.p, st->child.p, st->qslot.p, st->lo.p, st->hi.p, a.cheb_t, st->qhat64.p,
-                   precision == BLTC_PRECISION_MIXED ? st->qhat32.p : nullptr, np1};
+                   precision == BLTC_PRECISION_MIXED ? st->qhat32.p : nullptr, np1,
+                   caps ? up.lev.p : nullptr, nl, caps ? std::max<int32_t>(1, caps->m2m) : 0, a.stop};
         const size_t sm = m2m_smem_bytes(np1);
         BLTC_CUDA(cudaFuncSetAttribute(k_m2m_child, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(m2m_smem_bytes(BLTC_MAX_DEGREE + 1))));
         for (int L = nl - 1; L >= 0; --L) {
             for (int32_t p0 = 0; p0 < up.h[L]; p0 += up.chunk) {
                 const int32_t np = std::min(up.chunk, up.h[L] - p0);
-                const int32_t* nodes = up.list.p + up.off[L] + p0;
-                k_m2m_child<<<8 * np, 256, sm, s>>>(ma, nodes, up.scratch.p); ++ctx->launches;
-                k_m2m_sum<<<np, 256, 0, s>>>(ma, nodes, up.scratch.p); ++ctx->launches;
+                // host-driven: the chunk's parents; sized on the device: the list, read by level
+                const int32_t* nodes = caps ? up.list.p : up.list.p + up.off[L] + p0;
+                k_m2m_child<<<8 * np, 256, sm, s>>>(ma, nodes, up.scratch.p, L, p0); ++ctx->launches;
+                k_m2m_sum<<<np, 256, 0, s>>>(ma, nodes, up.scratch.p, L, p0); ++ctx->launches;
             }
         }
         BLTC_LAUNCH_CHECK("upward m2m");
