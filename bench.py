@@ -3,8 +3,11 @@
 
 Workload: 1e6 particles uniform in [-1,1]^3 with charges uniform in [-1,1] (Sec. IV test
 systems), Coulomb kernel, theta = 0.7, degree n = 8, N_L = N_B = 2000, mixed precision.
-A step is one pass of the whole path on resident device inputs: source tree (= target
-batches), MAC lists, modified charges, far- and near-field sweep, finalize.
+A step is one pass of the whole path for new positions on resident device inputs: source
+tree (= target batches), MAC lists, modified charges, far- and near-field sweep, finalize,
+run as one CUDA graph sized on the device (bltc_graph_create_positions); the steps alternate
+two seeded draws of the workload.  The host-driven bltc_solve of the first draw is timed
+beside it and gives the per-phase times and the sweep's roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -296,23 +299,64 @@ def run_ours(args, dist: Dist):
         w["theta"] = args.theta
     x, y, z, q = inputs.system(w["kind"], w["n"], w["seed"] + dist.rank)
     X = [torch.from_numpy(a).to(f"cuda:{dev}") for a in (x, y, z, q)]
+    # a second seeded draw of the workload: the graph's steps alternate the two systems, so
+    # that every step solves positions other than the previous step's
+    X2 = [torch.from_numpy(a).to(f"cuda:{dev}")
+          for a in inputs.system(w["kind"], w["n"], w["seed"] + dist.rank + 1000)]
+    systems = (X, X2)
     phi = torch.empty_like(X[0])
     ctx = b.Context(dev)
     p = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
                  b.BLTC_PRECISION_MIXED)
-    b.bltc_context_set_timing(ctx.h, True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
 
-    for _ in range(args.warmup):
-        ctx.solve(*X, p, phi)
+    # The step: the whole solve for new positions as one CUDA graph (bltc_graph_create_positions:
+    # tree, lists, upward pass, plan, sweep and finalize sized on the device).  A step copies
+    # the step's positions and charges into the graph's bound tensors and launches it.
+    B = [t.clone() for t in X]
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = b.Graph(ctx, *B[:3], B[3], p, positions=True)
+    torch.cuda.synchronize()
+    graph_setup_ms = 1e3 * (time.perf_counter() - t0)
 
+    def load(k):
+        for t, src in zip(B, systems[k]):
+            t.copy_(src)
+
+    for i in range(args.warmup):
+        load(i % 2)
+        g.launch()
+    torch.cuda.synchronize()
     sampler = ClockSampler(dev)
-    step_ms, phases = [], []
+    step_ms = []
     launches0 = b.bltc_context_launch_count(ctx.h)
     dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    for i in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        load(i % 2)
+        g.launch()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    dist.barrier()
+    launches = b.bltc_context_launch_count(ctx.h) - launches0
+    mean_ms = sum(step_ms) / len(step_ms)
+    agg = aggregate(mean_ms, w["n"], dist)
+    graph_info = g.info
+
+    # The host-driven solve (bltc_solve) of the first system, with phase events: the sweep's
+    # time for the roofline (the same kernel the graph runs) and the per-phase split.
+    b.bltc_context_set_timing(ctx.h, True)
+    for _ in range(args.warmup):
+        ctx.solve(*X, p, phi)
+    torch.cuda.synchronize()
+    host_ms, phases = [], []
     for _ in range(args.steps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -320,14 +364,14 @@ def run_ours(args, dist: Dist):
         ctx.solve(*X, p, phi)
         e1.record()
         e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+        host_ms.append(e0.elapsed_time(e1))
         phases.append(b.bltc_last_timings(ctx.h))
     torch.cuda.synchronize()
-    dist.barrier()
     clocks = sampler.stop()
-    launches = b.bltc_context_launch_count(ctx.h) - launches0
-    mean_ms = sum(step_ms) / len(step_ms)
-    agg = aggregate(mean_ms, w["n"], dist)
+    b.bltc_context_set_timing(ctx.h, False)
+    load(0)
+    g.launch()
+    graph_bits_equal = bool(torch.equal(g.phi, phi))
 
     # evaluated interactions of one step (same lists every step)
     st = b.bltc_tree_build(ctx.h, X[0], X[1], X[2], X[3], w["leaf"])
@@ -372,12 +416,22 @@ def run_ours(args, dist: Dist):
                           "p99": float(np.percentile(step_ms, 99)),
                           "min": min(step_ms), "max": max(step_ms)},
            "phases_ms": ph, "clocks": clocks, "gpu_launches": int(launches),
-           "roofline": roofline}
+           "roofline": roofline,
+           "step": {"api": "bltc_graph_create_positions + bltc_graph_launch (whole solve, one CUDA graph)",
+                    "systems": "two seeded draws of the workload, alternating",
+                    "kernels_per_launch": graph_info["kernels"], "redone": graph_info["redone"],
+                    "graph_setup_ms": graph_setup_ms, "bits_equal_to_bltc_solve": graph_bits_equal},
+           "host_driven": {"api": "bltc_solve (host reads each count back)",
+                           "ms_per_step": statistics.mean(host_ms),
+                           "p50": float(np.percentile(host_ms, 50)),
+                           "p99": float(np.percentile(host_ms, 99)),
+                           "note": "phases_ms and the roofline come from these solves"}}
 
     if not args.no_check:
-        out["error"] = check_errors(ctx, b, X, p, w, phi)
+        out["error"] = check_errors(ctx, b, X, p, w, g.phi)
     if not args.no_e2e:
-        out["e2e"] = run_e2e(ctx, b, x, y, z, q, p, args, dist, w)
+        out["e2e"] = run_e2e(ctx, b, x, y, z, q, g, B, args, dist, w)
+    g.close()
     # the sub-records run on one GPU only: under torchrun every rank is a replica of the main
     # workload, and N copies of the 2.56e8 system or the request stream would crowd the host
     if dist.world == 1 and not args.no_serving:
@@ -658,28 +712,36 @@ def direct_roofline(ctx, n, seconds):
             "frac": evals / seconds / peak}
 
 
-def run_e2e(ctx, b, x, y, z, q, p, args, dist, w):
-    """The same metric through bltc_solve_host: pinned host inputs copied in and phi copied
-    back inside every timed step."""
+def run_e2e(ctx, b, x, y, z, q, g, B, args, dist, w):
+    """The same metric end to end through the graph's public API: every timed step copies the
+    step's positions and charges from pinned host memory into the graph's bound tensors,
+    launches the graph (which synchronizes) and copies phi back to pinned host memory."""
     import torch
     H = [torch.from_numpy(a).pin_memory() for a in (x, y, z, q)]
     out = torch.empty(w["n"], dtype=torch.float64).pin_memory()
-    Hn = [t.numpy() for t in H]
-    on = out.numpy()
+
+    def step():
+        for t, h in zip(B, H):
+            t.copy_(h, non_blocking=True)
+        g.launch()
+        out.copy_(g.phi, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
     for _ in range(max(1, min(args.warmup, 2))):
-        b.bltc_solve_host(ctx.h, *Hn, p, on)
+        step()
     k = max(1, min(args.steps, 5))
     dist.barrier()
     times = []
     for _ in range(k):
         t0 = time.perf_counter()
-        b.bltc_solve_host(ctx.h, *Hn, p, on)   # synchronizes
+        step()
         times.append(time.perf_counter() - t0)
     dist.barrier()
     t = dist.max(sum(times) / len(times))
     total = dist.sum(w["n"])
     return {"value": total / t, "unit": "targets/s", "h2d_bytes_per_step": 4 * 8 * w["n"],
-            "d2h_bytes_per_step": 8 * w["n"], "steps": k, "ms_per_step": t * 1e3}
+            "d2h_bytes_per_step": 8 * w["n"], "steps": k, "ms_per_step": t * 1e3,
+            "api": "pinned host -> bound device tensors, bltc_graph_launch, phi -> pinned host"}
 
 
 # ---- serving: continuous batching of a request stream --------------------------------------
@@ -1007,6 +1069,103 @@ def run_graph(args, dist: Dist):
     return out
 
 
+def run_graph_positions(args, dist: Dist):
+    """New positions at every step: the whole solve (tree, lists, upward pass, plan, sweep,
+    finalize) sized on the device and captured as one CUDA graph.  A step copies the step's
+    positions and charges into the bound tensors (two seeded systems of the workload,
+    alternating) and launches the graph (one cudaGraphLaunch, one read of the overflow flag)."""
+    import torch
+
+    import paper_2003_01836_gb300 as b
+    from paper_2003_01836_gb300 import build, inputs
+    build.build()
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+    if args.theta >= 0:
+        w["theta"] = args.theta
+    systems = [[torch.from_numpy(a).to(f"cuda:{dev}") for a in inputs.system(w["kind"], w["n"], w["seed"] + dist.rank + 1000 * k)]
+               for k in range(2)]
+    X = [t.clone() for t in systems[0]]
+    ctx = b.Context(dev)
+    p = b.params(w["degree"], w["theta"], w["leaf"], w["batch"], w["kernel"], w["kappa"],
+                 b.BLTC_PRECISION_MIXED)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = b.Graph(ctx, *X[:3], X[3], p, positions=True)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+
+    def load(k):
+        for t, src in zip(X, systems[k]):
+            t.copy_(src)
+
+    for i in range(args.warmup):
+        load(i % 2)
+        g.launch()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    step_ms = []
+    launches0 = b.bltc_context_launch_count(ctx.h)
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        load(i % 2)
+        g.launch()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    launches = b.bltc_context_launch_count(ctx.h) - launches0
+    agg = aggregate(sum(step_ms) / len(step_ms), w["n"], dist)
+    # the host-driven solve of the same systems, for comparison
+    solve_ms = []
+    ref = torch.empty_like(X[0])
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.solve(*systems[i % 2], p, ref)
+        e1.record()
+        e1.synchronize()
+        if i >= args.warmup:
+            solve_ms.append(e0.elapsed_time(e1))
+    info = g.info
+    out = {"metric": "graph_positions variant: new positions every step, whole solve as one CUDA graph, targets/s",
+           "value": agg["targets_per_s"], "unit": "targets/s", "n_gpus": dist.world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": agg["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 (f64 accumulation)", "data": "synthetic",
+           "config": {"workload": "whole solve sized on the device, one CUDA graph, on " + workload_name(w),
+                      "n_particles": w["n"], "theta": w["theta"], "degree": w["degree"],
+                      "leaf_size": w["leaf"], "batch_size": w["batch"], "kernel": "coulomb",
+                      "precision": "mixed", "systems": "two seeded draws, alternating",
+                      "l2": "flushed before every timed step (256 MiB device write)"},
+           "setup_ms": setup_ms, "kernels_per_launch": info["kernels"], "redone": info["redone"],
+           "captures": info["captures"],
+           "host_driven_solve_ms": float(np.median(solve_ms)), "step_ms": [round(t, 3) for t in step_ms],
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+           "clocks": clocks, "gpu_launches": int(launches)}
+    if not args.no_check:
+        load(1)
+        g.launch()
+        ctx.solve(*systems[1], p, ref)
+        torch.cuda.synchronize()
+        out["bits_equal_to_solve"] = bool(torch.equal(g.phi, ref))
+    g.close()
+    ctx.close()
+    return out
+
+
 # ---- reference arm: the oracle --------------------------------------------------------------
 
 def run_reference(args, dist: Dist):
@@ -1090,7 +1249,7 @@ def main(argv=None):
                     help="targets of the 2.56e8 configuration's error sample (default 2048)")
     ap.add_argument("--serving", action="store_true",
                     help="time the serving runtime on the request stream instead")
-    ap.add_argument("--variant", choices=("treecode", "cp", "cc", "hermite", "graph"), default="treecode",
+    ap.add_argument("--variant", choices=("treecode", "cp", "cc", "hermite", "graph", "graph_positions"), default="treecode",
                     help="cp / cc / hermite: time the cluster-particle, cluster-cluster or "
                          "barycentric Hermite (n = 4) variant on the same workload instead; "
                          "graph: replays with fixed positions and new charges")
@@ -1113,6 +1272,8 @@ def main(argv=None):
             out = run_serving(args, dist)
         elif args.variant == "graph":
             out = run_graph(args, dist)
+        elif args.variant == "graph_positions":
+            out = run_graph_positions(args, dist)
         elif args.variant in ("cp", "cc", "hermite"):
             out = run_variant(args, dist)
         else:

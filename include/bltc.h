@@ -80,7 +80,14 @@ typedef struct bltc_params {
     int32_t batch_size;  /* N_B >= 1, target batches hold at most N_B particles */
     int32_t kernel;      /* BLTC_KERNEL_COULOMB, BLTC_KERNEL_YUKAWA or a registered user id */
     int32_t precision;   /* BLTC_PRECISION_FP64 or BLTC_PRECISION_MIXED */
-    int32_t reserved;    /* must be 0 */
+    int32_t tile;        /* the mixed sweep's tile shape, 0 for the defaults (bltc_autotune_tile
+                          * chooses one): bits 0-3 cap the source groups of a batch (0: 8;
+                          * else 1, 2, 4 or 8 thread groups of 256/G threads that split a
+                          * batch's sources, each covering the batch in passes of 2048/G
+                          * targets), bits 4-11 the work items per resident block of the
+                          * persistent sweep (0: 16; else 1..255; the item size follows), the
+                          * other bits 0.  The shape fixes the summation order, not the
+                          * arithmetic: results differ by rounding only. */
     double theta;        /* MAC parameter, 0 <= theta < 1 (theta = 0: all direct) */
     double kappa;        /* Yukawa inverse Debye length, >= 0 (ignored for Coulomb); the
                           * parameter of a user kernel */
@@ -364,6 +371,20 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
                           const double* q, int64_t n, const bltc_params* params,
                           const int32_t* leaf, const int32_t* batch, int32_t n_candidates,
                           int32_t repeats, int32_t use_cache, bltc_params* best, float* ms);
+
+/* Chooses the mixed sweep's tile shape (params->tile) for the given system at the leaf and
+ * batch sizes of *params, among candidates tiles[n_tiles] (0 included for the defaults).  Not
+ * in the paper.  Each candidate is timed with bltc_solve (one warm-up, then `repeats` runs, the
+ * fastest counts); the fastest wins.  Writes *params with that tile into *best and every
+ * candidate's time into ms[n_tiles] (may be NULL).  Cached in the context under
+ * (floor(log2 n), degree, kernel, precision, theta to 1e-3, mean batch size in quarter
+ * octaves, leaf and batch size): a later call with that key and use_cache != 0 returns the
+ * choice untimed if it is among its candidates.  Device pointers as bltc_solve.  Synchronizes.
+ * Errors: ARG (a malformed tile, no candidates), OOM, CUDA. */
+bltc_status bltc_autotune_tile(bltc_context* ctx, const double* x, const double* y, const double* z,
+                               const double* q, int64_t n, const bltc_params* params,
+                               const int32_t* tiles, int32_t n_tiles, int32_t repeats,
+                               int32_t use_cache, bltc_params* best, float* ms);
 
 /* ---- user kernels: a hook for any smooth, non-oscillatory radial G ---------------- */
 /* The treecode needs only evaluations of G (Sec. I; Sec. V names other kernels as the

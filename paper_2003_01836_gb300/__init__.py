@@ -48,16 +48,23 @@ class BltcError(RuntimeError):
 class bltc_params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("batch_size", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("theta", ctypes.c_double), ("kappa", ctypes.c_double)]
 
 
 def params(degree=8, theta=0.7, leaf_size=2000, batch_size=None, kernel=BLTC_KERNEL_COULOMB,
-           kappa=0.0, precision=BLTC_PRECISION_MIXED) -> bltc_params:
-    """Treecode parameters (theta, n, N_L, N_B of Algorithm 1) plus kernel and precision."""
+           kappa=0.0, precision=BLTC_PRECISION_MIXED, tile=0) -> bltc_params:
+    """Treecode parameters (theta, n, N_L, N_B of Algorithm 1) plus kernel, precision and the
+    sweep's tile shape (0: the defaults; see tile())."""
     return bltc_params(int(degree), int(leaf_size),
                        int(leaf_size if batch_size is None else batch_size), int(kernel),
-                       int(precision), 0, float(theta), float(kappa))
+                       int(precision), int(tile), float(theta), float(kappa))
+
+
+def tile(group_cap=0, items_per_block=0):
+    """bltc_params.tile from its fields: the cap on a batch's source groups (0: 8; else 1, 2, 4
+    or 8) and the persistent sweep's work items per resident block (0: 16; else 1..255)."""
+    return int(group_cap) | (int(items_per_block) << 4)
 
 
 class bltc_server_config(ctypes.Structure):
@@ -130,6 +137,8 @@ _SIGNATURES = {
     "bltc_graph_create_positions": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, ctypes.c_double, _pp],
                                     ctypes.c_int),
     "bltc_graph_info": ([_vp, _vp], ctypes.c_int),
+    "bltc_autotune_tile": ([_vp, _vp, _vp, _vp, _vp, _i64, _P, _vp, _i32, _i32, _i32, _P, _vp],
+                           ctypes.c_int),
     "bltc_dual_lists": ([_vp, _vp, _vp, _P, _vp, _vp, _vp], ctypes.c_int),
     "bltc_solve_targets": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _P, _vp],
                            ctypes.c_int),
@@ -532,6 +541,18 @@ def bltc_autotune(ctx, x, y, z, q, p: bltc_params, leaf=(500, 1000, 2000, 3000, 
                                     1 if use_cache else 0, ctypes.byref(best), ms.ctypes.data))
     keys = [(int(l), int(bb)) for l, bb in zip(L, L if B is None else B)]
     return best, {k: float(v) for k, v in zip(keys, ms)}
+
+
+def bltc_autotune_tile(ctx, x, y, z, q, p: bltc_params, tiles, repeats=1, use_cache=True):
+    """Returns (params with the fastest tile, {tile: fastest ms}) at p's leaf and batch sizes."""
+    _stream(ctx)
+    T = np.ascontiguousarray(tiles, dtype=np.int32)
+    ms = np.full(len(T), np.nan, dtype=np.float32)
+    best = bltc_params()
+    _check(ctx, lib().bltc_autotune_tile(ctx, _ptr(x), _ptr(y), _ptr(z), _ptr(q), x.numel(),
+                                         ctypes.byref(p), T.ctypes.data, len(T), int(repeats),
+                                         1 if use_cache else 0, ctypes.byref(best), ms.ctypes.data))
+    return best, {int(t): float(v) for t, v in zip(T, ms)}
 
 
 # ---- serving -------------------------------------------------------------------------

@@ -18,6 +18,8 @@ struct bltc_context {
     // autotuner cache: (log2 n, degree, kernel, precision, theta * 1000, distribution shape)
     // -> (leaf, batch)
     std::map<std::tuple<int, int, int, int, int, int>, std::pair<int32_t, int32_t>> tuned;
+    // tile cache: the same key plus (leaf, batch) -> params.tile
+    std::map<std::tuple<int, int, int, int, int, int, int32_t, int32_t>, int32_t> tuned_tile;
 };
 struct bltc_tree {
     bltc::Tree t;
@@ -118,7 +120,7 @@ static void check_params(const bltc_params* p) {
             "a user kernel's parameter (kappa) must be finite");
     require(p->precision == BLTC_PRECISION_FP64 || p->precision == BLTC_PRECISION_MIXED,
             "unknown precision");
-    require(p->reserved == 0, "params.reserved must be 0");
+    require(tile_valid(p->tile), "params.tile: group cap 0, 1, 2, 4 or 8 (bits 0-3), items per block 0..255 (bits 4-11), other bits 0");
 }
 
 template <typename F>
@@ -162,7 +164,7 @@ static void upward_beside_plan(Context* c, Tree* st, Lists* L, const bltc_params
     }
     c->stream = main_stream;
     try {
-        prepare_plan(c, L, p.degree, p.precision);
+        prepare_plan(c, L, p.degree, p.precision, p.tile);
     } catch (...) {
         c->join();
         throw;
@@ -452,7 +454,7 @@ bltc_status bltc_evaluations(bltc_context* ctx, bltc_lists* lists, const bltc_pa
     if (!ctx || !lists || !n_evaluations) return BLTC_ERR_ARG;
     return guarded(ctx, [&] {
         check_params(params);
-        *n_evaluations = plan_evaluations(&ctx->c, &lists->l, params->degree, params->precision);
+        *n_evaluations = plan_evaluations(&ctx->c, &lists->l, params->degree, params->precision, params->tile);
     });
 }
 
@@ -690,7 +692,7 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
             k.s_nodes = st.n_nodes;
             k.b_nodes = bt->n_nodes;
             k.b_leaves = bt->n_leaves;
-            k.cost = plan_slot_cost(c, &L, p.degree, p.precision);
+            k.cost = plan_slot_cost(c, &L, p.degree, p.precision, p.tile);
             for (int j = 0; j < i; ++j) {
                 const Cand& o = cs[static_cast<size_t>(j)];
                 if (o.same < 0 && o.s_nodes == k.s_nodes && o.b_nodes == k.b_nodes && o.cost == k.cost) {
@@ -782,6 +784,85 @@ bltc_status bltc_autotune(bltc_context* ctx, const double* x, const double* y, c
         best->leaf_size = leaf[win];
         best->batch_size = batch ? batch[win] : leaf[win];
         ctx->tuned[key] = {best->leaf_size, best->batch_size};
+    });
+}
+
+bltc_status bltc_autotune_tile(bltc_context* ctx, const double* x, const double* y, const double* z,
+                               const double* q, int64_t n, const bltc_params* params,
+                               const int32_t* tiles, int32_t n_tiles, int32_t repeats,
+                               int32_t use_cache, bltc_params* best, float* ms) {
+    if (!ctx || !best) return BLTC_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_params(params);
+        require(x && y && z && q, "autotune_tile: NULL pointer");
+        require(n >= 1 && n < (int64_t(1) << 31), "autotune_tile: n must be in [1, 2^31)");
+        require(tiles && n_tiles >= 1 && repeats >= 1, "autotune_tile: need candidates and repeats");
+        for (int i = 0; i < n_tiles; ++i) require(tile_valid(tiles[i]), "autotune_tile: malformed tile");
+        Context* c = &ctx->c;
+        if (ms)
+            for (int i = 0; i < n_tiles; ++i) ms[i] = std::nanf("");
+        // the key of bltc_autotune (the distribution as the mean batch size) plus the sizes
+        int64_t n_batches = 0;
+        {
+            Tree bt;
+            build_tree(c, x, y, z, nullptr, n, params->batch_size, &bt);
+            n_batches = bt.n_leaves;
+        }
+        int lg = 0;
+        while ((int64_t(1) << (lg + 1)) <= n) ++lg;
+        const int shape = static_cast<int>(std::lround(4.0 * std::log2(static_cast<double>(n) /
+                                                                           static_cast<double>(n_batches))));
+        const auto key = std::make_tuple(lg, params->degree, params->kernel, params->precision,
+                                         static_cast<int>(std::lround(params->theta * 1000.0)), shape,
+                                         params->leaf_size, params->batch_size);
+        *best = *params;
+        if (use_cache) {
+            auto it = ctx->tuned_tile.find(key);
+            if (it != ctx->tuned_tile.end()) {
+                for (int i = 0; i < n_tiles; ++i) {
+                    if (tiles[i] == it->second) {
+                        best->tile = it->second;
+                        return;
+                    }
+                }
+            }
+        }
+        DBuf<double> phi(c, n);
+        cudaEvent_t e0, e1;
+        BLTC_CUDA(cudaEventCreate(&e0));
+        BLTC_CUDA(cudaEventCreate(&e1));
+        float best_ms = 3.0e38f;
+        int win = 0;
+        try {
+            for (int i = 0; i < n_tiles; ++i) {
+                bltc_params p = *params;
+                p.tile = tiles[i];
+                solve_device(c, x, y, z, q, n, p, phi.p);     // warm-up
+                float t_min = 3.0e38f;
+                for (int r = 0; r < repeats; ++r) {
+                    BLTC_CUDA(cudaEventRecord(e0, c->stream));
+                    solve_device(c, x, y, z, q, n, p, phi.p);
+                    BLTC_CUDA(cudaEventRecord(e1, c->stream));
+                    BLTC_CUDA(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    BLTC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                    t_min = std::min(t_min, t);
+                }
+                if (ms) ms[i] = t_min;
+                if (t_min < best_ms) {
+                    best_ms = t_min;
+                    win = i;
+                }
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        best->tile = tiles[win];
+        ctx->tuned_tile[key] = tiles[win];
     });
 }
 

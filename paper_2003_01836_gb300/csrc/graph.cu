@@ -134,9 +134,27 @@ void run_sized(GraphSolve* g, SolveObjects* o) {
     }
     build_lists(c, o->bt, &o->st, p.theta, p.degree, &o->L, &g->caps_s);
     prepare_upward(c, &o->st, &o->L, p.degree, p.precision, &o->up);
-    run_upward(c, &o->st, o->up);
-    prepare_plan(c, &o->L, p.degree, p.precision);
-    alloc_sweep_buffers(c, &o->L, &o->sb);
+    // the upward pass's kernels on a second branch, beside the work plan (both follow the
+    // lists and are independent); captured, the fork and the join become graph edges
+    c->fork();
+    cudaStream_t main_stream = c->stream;
+    c->stream = c->side;
+    try {
+        run_upward(c, &o->st, o->up);
+    } catch (...) {
+        c->stream = main_stream;
+        c->join();
+        throw;
+    }
+    c->stream = main_stream;
+    try {
+        prepare_plan(c, &o->L, p.degree, p.precision, p.tile);
+        alloc_sweep_buffers(c, &o->L, &o->sb);
+    } catch (...) {
+        c->join();
+        throw;
+    }
+    c->join();
     run_sweep(c, &o->L, o->bt, &o->st, p, g->phi, o->sb);
 }
 

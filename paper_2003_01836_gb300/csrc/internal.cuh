@@ -199,6 +199,7 @@ struct Tree {
 struct Plan {
     bool valid = false;
     int degree = -1;
+    int tile = 0;                     // bltc_params.tile the plan was built for
     bool mutual = false;              // mutual leaf pairs evaluated once (mixed, batches = sources)
     int64_t mpart_len = 0;            // doubles of mutual rows
     DBuf<int64_t> dir_moff;           // per direct entry: its mutual row in mpart, or -1
@@ -294,14 +295,22 @@ void run_sweep(Context* ctx, Lists* lists, const Tree* bt, const Tree* st, const
                double* phi, const SweepBuffers& b);
 void interaction_counts(Context* ctx, const Lists* lists, int64_t* n_dir, int64_t* n_app);
 // Work plan of a list set (items, partial layout, self-pair flags); built once per degree.
-void build_plan(Context* ctx, Lists* L, int degree, bool mutual);
-// The plan for an evaluation in `precision` (mutual pairs for MIXED with batches = sources).
-void prepare_plan(Context* ctx, Lists* L, int degree, int precision);
+void build_plan(Context* ctx, Lists* L, int degree, bool mutual, int tile = 0);
+// The plan for an evaluation in `precision` (mutual pairs for MIXED with batches = sources)
+// with the sweep's tile shape `tile` (bltc_params.tile).
+void prepare_plan(Context* ctx, Lists* L, int degree, int precision, int tile = 0);
 // Kernel evaluations the sweep performs for that plan (mutual pairs counted once).
-int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision);
+int64_t plan_evaluations(Context* ctx, Lists* L, int degree, int precision, int tile = 0);
 // The sweep's cost model for that plan: evaluations with every batch padded to the target
 // slots its source groups run (the autotuner's screen).
-int64_t plan_slot_cost(Context* ctx, Lists* L, int degree, int precision);
+int64_t plan_slot_cost(Context* ctx, Lists* L, int degree, int precision, int tile = 0);
+// The fields of bltc_params.tile (0: the defaults).
+inline int tile_group_cap(int tile) { return (tile & 15) ? (tile & 15) : 8; }
+inline int tile_items_per_block(int tile) { return ((tile >> 4) & 255) ? ((tile >> 4) & 255) : 16; }
+inline bool tile_valid(int tile) {
+    const int g = tile & 15;
+    return (tile >> 12) == 0 && (g == 0 || g == 1 || g == 2 || g == 4 || g == 8);
+}
 // The Hermite treecode's sweep (sweep.cu) and the whole solve (hermite.cu).
 void evaluate_hermite(Context* ctx, Lists* L, const Tree* bt, const Tree* st, const bltc_params& p,
                       const double* qh64, const float* qh32, const int32_t* qslot, double* phi);

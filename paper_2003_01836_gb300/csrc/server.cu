@@ -188,7 +188,7 @@ static void prepare(Context* c, ServerRequest* r) {
     r->L.reset(new Lists());
     build_lists(c, bt, r->st.get(), r->p.theta, r->p.degree, r->L.get());
     compute_modified_charges(c, r->st.get(), r->L.get(), r->p.degree, r->p.precision);
-    prepare_plan(c, r->L.get(), r->p.degree, r->p.precision);
+    prepare_plan(c, r->L.get(), r->p.degree, r->p.precision, r->p.tile);
     BLTC_CUDA(cudaEventCreateWithFlags(&r->ready_ev, cudaEventDisableTiming));
     BLTC_CUDA(cudaEventRecord(r->ready_ev, c->stream));
 }
@@ -429,7 +429,7 @@ bltc_status bltc_server_submit(bltc_server* h, const double* x, const double* y,
     if (!h || !x || !y || !z || !q || !phi || !p || !ticket) return BLTC_ERR_ARG;
     if (n < 1 || n >= (int64_t(1) << 31)) return BLTC_ERR_ARG;
     if (p->degree < 1 || p->degree > BLTC_MAX_DEGREE || !(p->theta >= 0.0 && p->theta < 1.0) ||
-        p->leaf_size < 1 || p->batch_size < 1 || p->reserved != 0 ||
+        p->leaf_size < 1 || p->batch_size < 1 || !tile_valid(p->tile) ||
         (p->kernel != BLTC_KERNEL_COULOMB && p->kernel != BLTC_KERNEL_YUKAWA) ||
         (p->kernel == BLTC_KERNEL_YUKAWA && !(p->kappa >= 0.0 && p->kappa < 1e300)) ||
         p->precision != BLTC_PRECISION_MIXED)

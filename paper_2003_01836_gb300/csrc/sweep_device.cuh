@@ -60,6 +60,7 @@ struct SweepArgs {
     double kappa;
     float neg_kappa_log2e;
     float param32;             // kappa in FP32, the parameter of a user kernel
+    int g_max;                 // cap on the source groups of a batch (1, 2, 4 or 8)
 };
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
@@ -173,11 +174,13 @@ struct Targets {
 // keeps its own partial potentials; they are added in group order at the end of the item, so
 // the result is fixed by the batch alone.  The last pass runs its padding slots like targets,
 // so G is the one with the fewest target slots, ceil(nb / (2048/G)) * 2048/G, the smallest G
-// on a tie: a batch of 1100 targets runs 1280 slots with G = 8 instead of 2048 with G = 1.
-__device__ __forceinline__ int groups_for(int nb) {
+// on a tie, up to the tile's cap g_max: a batch of 1100 targets runs 1280 slots with G = 8
+// instead of 2048 with G = 1.
+__device__ __forceinline__ int groups_for(int nb, int g_max) {
     int best = 1, best_slots = (nb + kThreads * kT - 1) / (kThreads * kT) * (kThreads * kT);
 #pragma unroll
     for (int G = 2; G <= 8; G *= 2) {
+        if (G > g_max) break;
         const int w = kThreads / G * kT;
         const int slots = (nb + w - 1) / w * w;
         if (slots < best_slots) {
@@ -682,7 +685,7 @@ __device__ void item_mixed(const SweepArgs& a, int4 it, float4* sm) {
     const double cb[3] = {a.b_center[3 * B], a.b_center[3 * B + 1], a.b_center[3 * B + 2]};
     const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
     double* out = a.partials + a.part_off[b] + static_cast<int64_t>(it.w) * nb;
-    const int G = groups_for(nb);
+    const int G = groups_for(nb, a.g_max);
     const int tpg = kThreads / G;                       // threads per group
     const int g = static_cast<int>(threadIdx.x) / tpg, l = static_cast<int>(threadIdx.x) - g * tpg;
     for (int t0 = 0; t0 < nb; t0 += tpg * kT) {

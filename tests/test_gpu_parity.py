@@ -414,6 +414,54 @@ def test_autotune_screen_and_never_slower(gpu):
     assert oracle.rel_err(ref, got) <= MIXED_REL2
 
 
+TILES = (0, b.tile(group_cap=4), b.tile(group_cap=2), b.tile(items_per_block=8), b.tile(items_per_block=32))
+
+
+@pytest.mark.parametrize("deg", [4, 8])
+def test_autotune_tile_per_degree(gpu, deg):
+    # The tile tuner times every candidate shape at the given sizes and keeps the fastest, per
+    # degree; each shape changes only the summation order: every candidate's potentials stay
+    # within the mixed bars of the FP64 solve, and the choice is never slower than the default.
+    import torch
+    x, y, z, q = system("plummer", 300000, 20031906 + deg)
+    X = dev(x, y, z, q)
+    p = b.params(deg, 0.8, 1000, 1000, b.BLTC_KERNEL_YUKAWA, 0.5, b.BLTC_PRECISION_MIXED)
+    best, ms = b.bltc_autotune_tile(gpu.h, *X, p, TILES, repeats=2, use_cache=False)
+    assert best.tile in TILES and best.leaf_size == 1000 and best.degree == deg
+    assert all(v == v for v in ms.values()) and ms[best.tile] == min(ms.values())
+    again, ms2 = b.bltc_autotune_tile(gpu.h, *X, p, TILES, repeats=2, use_cache=True)
+    assert again.tile in TILES
+    ref = gpu_solve(gpu, x, y, z, q, b.params(deg, 0.8, 1000, 1000, b.BLTC_KERNEL_YUKAWA, 0.5,
+                                              b.BLTC_PRECISION_FP64))
+    # per target, relative to its own potential (or the rms, where the potential cancels)
+    ref_abs = np.maximum(np.abs(ref), np.sqrt(np.mean(ref ** 2)))
+    for t in TILES:
+        pt = b.params(deg, 0.8, 1000, 1000, b.BLTC_KERNEL_YUKAWA, 0.5, b.BLTC_PRECISION_MIXED, tile=t)
+        got = gpu_solve(gpu, x, y, z, q, pt)
+        assert oracle.rel_err(ref, got) <= MIXED_REL2, (t, oracle.rel_err(ref, got))
+        assert np.max(np.abs(got - ref) / ref_abs) <= MIXED_ELEM, t
+    phi = torch.empty_like(X[0])
+
+    def fastest(pp):
+        ts = []
+        for _ in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.bltc_solve(gpu.h, *X, pp, phi)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts[1:])
+    assert fastest(best) <= 1.05 * fastest(p), (best.tile, ms)
+
+
+def test_malformed_tile_rejected(gpu):
+    x, y, z, q = system("cube", 2000, 20031907)
+    for t in (3, 5, 1 << 12, -1):
+        with pytest.raises(b.BltcError):
+            gpu_solve(gpu, x, y, z, q, b.params(4, 0.7, 200, tile=t))
+
+
 def test_solve_host_matches_device(gpu):
     x, y, z, q = system("cube", 20000, 6)
     p = b.params(6, 0.7, 1000)
