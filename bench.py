@@ -470,15 +470,24 @@ def run_ours(args, dist: Dist):
 
 CONFIGS = {
     "3": dict(kind="plummer", n=8_000_000, theta=0.8, degree=8, kernel=1, kappa=0.5, seed=20031839,
-              fp32_storage=False, steps=3, warmup=1, error_targets=10_000,
+              fp32_storage=False, steps=3, warmup=1, error_targets=10_000, tiles=True,
               name=("truncated Plummer sphere N=8e6 (a=1, r<=10), q in [-1,1], Yukawa kappa=0.5, "
-                    "theta=0.8, n=8, leaf=batch autotuned over {500,1000,2000,3000,4000}, mixed")),
+                    "theta=0.8, n=8, leaf=batch autotuned over {500,1000,2000,3000,4000}, then the "
+                    "sweep's tile shape autotuned, mixed")),
     "5": dict(kind="cube", n=256_000_000, theta=0.8, degree=10, kernel=0, kappa=0.0, seed=20031841,
               fp32_storage=True, steps=2, warmup=1, error_targets=2048,
               name=("uniform cube N=2.56e8, xyzq stored in FP32 (read as FP64), Coulomb, theta=0.8, "
                     "n=10, leaf=batch autotuned over {500,1000,2000,3000,4000}, mixed")),
 }
 CANDIDATES = (500, 1000, 2000, 3000, 4000)
+# tile shapes tried after the sizes (bltc_params.tile): the default, caps of 4 and 2 source
+# groups per batch, and 8 or 32 work items per resident block
+TILE_CANDIDATES = (0, 4, 2, 8 << 4, 32 << 4)
+
+
+def tile_name(t):
+    g, ipb = t & 15, (t >> 4) & 255
+    return f"groups<={g or 8},items/block={ipb or 16}"
 
 
 def xu_peak(sm_count, kernel):
@@ -523,6 +532,14 @@ def run_config(ctx, b, key, args, dist):
     t0 = time.perf_counter()
     best, tune_ms = b.bltc_autotune(ctx.h, *X, p, leaf=CANDIDATES, repeats=1, use_cache=False)
     tune_s = time.perf_counter() - t0
+    tile_rec = {"searched": False, "reason": "one solve of this configuration takes seconds; "
+                                             "the default tile is kept"}
+    if c.get("tiles"):
+        t0 = time.perf_counter()
+        best, tile_ms = b.bltc_autotune_tile(ctx.h, *X, best, TILE_CANDIDATES, repeats=1, use_cache=False)
+        tile_rec = {"searched": True, "seconds": time.perf_counter() - t0,
+                    "candidates": {tile_name(t): v for t, v in tile_ms.items()},
+                    "chosen": tile_name(best.tile)}
     phi = torch.empty_like(X[0])
     for _ in range(c["warmup"]):
         ctx.solve(*X, best, phi)
@@ -582,7 +599,8 @@ def run_config(ctx, b, key, args, dist):
     out = {"workload": c["name"], "n_particles": c["n"], "leaf_size": best.leaf_size,
            "batch_size": best.batch_size, "batches": n_batches,
            "autotune": {"seconds": tune_s, "candidates": list(CANDIDATES),
-                        "timed_ms": {str(k[0]): v for k, v in tune_ms.items() if v == v}},
+                        "timed_ms": {str(k[0]): v for k, v in tune_ms.items() if v == v},
+                        "tile": tile_rec},
            "input_generation_s": gen_s, "steps": c["steps"], "warmup": c["warmup"],
            "ms_per_step": mean_ms, "targets_per_s": c["n"] / (mean_ms / 1e3),
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "max": max(step_ms)},
