@@ -541,6 +541,7 @@ def run_config(ctx, b, key, args, dist):
                     "candidates": {tile_name(t): v for t, v in tile_ms.items()},
                     "chosen": tile_name(best.tile)}
     phi = torch.empty_like(X[0])
+    b.bltc_context_set_timing(ctx.h, True)          # phase events for the sweep's roofline
     for _ in range(c["warmup"]):
         ctx.solve(*X, best, phi)
     torch.cuda.synchronize()
@@ -558,6 +559,7 @@ def run_config(ctx, b, key, args, dist):
         step_ms.append(e0.elapsed_time(e1))
         phases.append(b.bltc_last_timings(ctx.h))
     clocks = sampler.stop()
+    b.bltc_context_set_timing(ctx.h, False)
     del flush
     ph = {k: statistics.mean(d[k] for d in phases) for k in phases[0]}
     mean_ms = statistics.mean(step_ms)

@@ -32,6 +32,7 @@ struct PlanArgs {
     int64_t* part_len;           // per batch: n_chunks * nb
     const int32_t* item_off;     // pass 2
     int4* items;
+    int64_t* icost;              // pass 2: per item its interaction count (the queue order)
     // boxes for the self-pair test
     const double* b_lo;
     const double* b_hi;
@@ -204,41 +205,29 @@ __global__ void k_chunks(PlanArgs a) {
     int chunk = 0, start = 0;
     int64_t acc = 0;
     int4* out = kFill ? a.items + a.item_off[b] : nullptr;
+    int64_t* oc = kFill ? a.icost + a.item_off[b] : nullptr;
     for (int e = 0; e < ne; ++e) {
         const int64_t c = e < na ? nb * a.P : dir_cost(a, d0 + e - na, nb);
         if (acc > 0 && acc + c > a.cut) {
-            if (kFill) out[chunk] = make_int4(static_cast<int>(b), start, e, chunk);
+            if (kFill) {
+                out[chunk] = make_int4(static_cast<int>(b), start, e, chunk);
+                oc[chunk] = acc;
+            }
             ++chunk;
             start = e;
             acc = 0;
         }
         acc += c;
     }
-    if (kFill) out[chunk] = make_int4(static_cast<int>(b), start, ne, chunk);
+    if (kFill) {
+        out[chunk] = make_int4(static_cast<int>(b), start, ne, chunk);
+        oc[chunk] = acc;
+    }
     ++chunk;
     if (!kFill) {
         a.n_chunks[b] = chunk;
         a.part_len[b] = chunk * nb;
     }
-}
-
-// Interaction count of each item (for longest-first ordering).
-__global__ void k_item_costs(PlanArgs a, const int4* __restrict__ items, int64_t n_items,
-                             int64_t* cost, const int32_t* n_items_dev) {
-    if (n_items_dev) {
-        // sized on the device: unwritten items follow an exceeded capacity (nothing runs then)
-        if (*a.cap_flag) return;
-        if (*n_items_dev < n_items) n_items = *n_items_dev;
-    }
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n_items) return;
-    const int4 it = items[i];
-    const int b = it.x;
-    const int64_t nb = a.b_count[a.b_leaves[b]];
-    const int a0 = a.app_off[b], na = a.app_off[b + 1] - a0, d0 = a.dir_off[b];
-    int64_t c = 0;
-    for (int e = it.y; e < it.z; ++e) c += e < na ? nb * a.P : dir_cost(a, d0 + e - na, nb);
-    cost[i] = c;
 }
 
 // out[0]: direct interactions, out[1]: approximation interactions, out[2]: direct kernel
@@ -346,8 +335,8 @@ static void build_plan_sized(Context* ctx, Lists* L, PlanArgs a, DBuf<int32_t>& 
     const int32_t* n_dev = reinterpret_cast<const int32_t*>(pl.dwords.p + 1);
     a.item_off = item_off.p;
     a.items = raw.p;
+    a.icost = icost.p;
     k_chunks<true><<<grid_for(L->n_batches, 128), 128, 0, s>>>(a); ++ctx->launches;
-    k_item_costs<<<grid_for(cap, 256), 256, 0, s>>>(a, raw.p, cap, icost.p, n_dev); ++ctx->launches;
     BLTC_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * kBuckets, s));
     const unsigned g = grid_for(cap, 256, 4 * std::max(1, ctx->sm_count));
     k_bucket_hist<<<g, 256, 0, s>>>(icost.p, n_dev, cap, hist.p); ++ctx->launches;
@@ -458,17 +447,16 @@ void build_plan(Context* ctx, Lists* L, int degree, bool mutual, int tile) {
     pl.n_items = *reinterpret_cast<const int32_t*>(w + 1);
     pl.partial_len = w[2];
     pl.items = DBuf<int4>(ctx, pl.n_items);
+    DBuf<int64_t> icost(ctx, pl.n_items);
     a.item_off = item_off.p;
     a.items = pl.items.p;
+    a.icost = icost.p;
     k_chunks<true><<<grid_for(nb, 128), 128, 0, s>>>(a); ++ctx->launches;
     BLTC_LAUNCH_CHECK("plan items");
     // Longest-first order (LPT): the persistent sweep takes items in queue order, so the
     // short ones fill the gaps at the end.  The order does not change any result (each item
     // writes its own partials); ties keep batch order (stable sort).
     if (pl.n_items > 1) {
-        DBuf<int64_t> icost(ctx, pl.n_items);
-        k_item_costs<<<grid_for(pl.n_items, 256), 256, 0, s>>>(a, pl.items.p, pl.n_items, icost.p, nullptr); ++ctx->launches;
-        BLTC_LAUNCH_CHECK("plan costs");
         std::vector<int4> h_items(static_cast<size_t>(pl.n_items));
         std::vector<int64_t> h_cost(static_cast<size_t>(pl.n_items));
         BLTC_CUDA(cudaMemcpyAsync(h_items.data(), pl.items.p, sizeof(int4) * pl.n_items, cudaMemcpyDeviceToHost, s));
