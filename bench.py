@@ -436,9 +436,11 @@ def run_ours(args, dist: Dist):
     # workload, and N copies of the 2.56e8 system or the request stream would crowd the host
     if dist.world == 1 and not args.no_serving:
         sv = serve_measure(args.serve_record_requests, (0.5,), args.serve_workers, dist,
-                           args.serve_slice_us)
+                           args.serve_slice_us, args.serve_setup_blocks, args.serve_slices_in_flight)
         out["serving"] = {"requests": sv["config"]["requests"], "total_targets": sv["config"]["total_targets"],
-                          "mix": sv["config"]["mix"], "slice_us": sv["config"]["slice_us"], "levels": sv["levels"], "solo": sv["solo"],
+                          "mix": sv["config"]["mix"], "slice_us": sv["config"]["slice_us"],
+                          "setup_blocks": sv["config"]["setup_blocks"],
+                          "slices_in_flight": sv["config"]["slices_in_flight"], "levels": sv["levels"], "solo": sv["solo"],
                           "served_vs_solo": sv["served_vs_solo"]}
     if dist.world == 1 and not args.no_configs:
         out["configs"] = {}
@@ -817,10 +819,10 @@ def run_serving(args, dist: Dist):
     from paper_2003_01836_gb300 import build
     build.build()
     return serve_measure(args.serve_requests, (0.5, 0.8, 1.0), args.serve_workers, dist,
-                         args.serve_slice_us)
+                         args.serve_slice_us, args.serve_setup_blocks, args.serve_slices_in_flight)
 
 
-def serve_measure(count, fractions, workers, dist, slice_us=10000):
+def serve_measure(count, fractions, workers, dist, slice_us=15000, setup_blocks=0, slices_in_flight=0):
     """The serving runtime on the first `count` requests of the stream: all at once
     (saturated), then Poisson arrivals at each fraction of that rate; every request is also
     solved alone for the comparison."""
@@ -838,7 +840,8 @@ def serve_measure(count, fractions, workers, dist, slice_us=10000):
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         data = list(ex.map(make, reqs))
     total_targets = sum(r[1] for r in reqs)
-    srv = b.Server(dist.local_rank, setup_workers=workers, max_batch=64, slice_us=slice_us)
+    srv = b.Server(dist.local_rank, setup_workers=workers, max_batch=64, slice_us=slice_us,
+                   setup_blocks=setup_blocks, slices_in_flight=slices_in_flight)
     try:
         # warm-up: a few requests
         for i in range(min(8, len(reqs))):
@@ -862,7 +865,7 @@ def serve_measure(count, fractions, workers, dist, slice_us=10000):
                     tickets[i] = srv.submit(*data[i], reqs[i][3])
             th = threading.Thread(target=submitter)
             th.start()
-            lat = []
+            lat, parts = [], []
             for i in range(len(reqs)):
                 while tickets[i] is None:
                     time.sleep(0.0002)
@@ -870,26 +873,39 @@ def serve_measure(count, fractions, workers, dist, slice_us=10000):
                 if st != b.BLTC_OK:
                     raise RuntimeError(f"request {i} failed with status {st}: {srv.last_error()}")
                 lat.append((info["t_done"] - info["t_submit"]) * 1e3)
+                parts.append(((info["t_admit"] - info["t_submit"]) * 1e3, (info["t_ready"] - info["t_admit"]) * 1e3,
+                              (info["t_done"] - info["t_ready"]) * 1e3, (info["t_swept"] - info["t_ready"]) * 1e3,
+                              (info["t_copy"] - info["t_swept"]) * 1e3, (info["t_done"] - info["t_copy"]) * 1e3))
             th.join()
-            return time.perf_counter() - t0, np.array(lat)
+            return time.perf_counter() - t0, np.array(lat), np.array(parts)
 
-        wall, lat = run_load(None)
+        wall, lat, parts = run_load(None)
         x_req = len(reqs) / wall
-        runs = [("saturated (all submitted at t=0)", None, wall, lat)]
+        runs = [("saturated (all submitted at t=0)", None, wall, lat, parts)]
         for frac in fractions:
-            wall_f, lat_f = run_load(frac * x_req)
-            runs.append((f"Poisson at {frac:.1f} x saturated rate", frac * x_req, wall_f, lat_f))
+            wall_f, lat_f, parts_f = run_load(frac * x_req)
+            runs.append((f"Poisson at {frac:.1f} x saturated rate", frac * x_req, wall_f, lat_f, parts_f))
         stats = srv.stats()
     finally:
         srv.close()
     solo_each = serve_solo_time(reqs, data, dist)
     solo = float(solo_each.sum())
     levels = []
-    for name, offered, wall_f, lat_f in runs:
+    for name, offered, wall_f, lat_f, parts_f in runs:
         slow = lat_f / (1e3 * solo_each)          # latency over the request's solo solve time
+        tail = slow >= np.percentile(slow, 99)
         lv = {"load": name, "requests_per_s": len(reqs) / wall_f, "targets_per_s": total_targets / wall_f,
               "p50_ms": float(np.percentile(lat_f, 50)), "p99_ms": float(np.percentile(lat_f, 99)),
-              "slowdown_p50": float(np.percentile(slow, 50)), "slowdown_p99": float(np.percentile(slow, 99))}
+              "slowdown_p50": float(np.percentile(slow, 50)), "slowdown_p99": float(np.percentile(slow, 99)),
+              # where the slowest 1% (by slowdown) spent their time: waiting for admission, in
+              # setup (copy-in, tree, lists, charges, plan), and from ready to copied out
+              "tail_ms": {"requests": int(tail.sum()), "n_mean": float(np.mean([reqs[i][1] for i in np.flatnonzero(tail)])),
+                          "queued": float(parts_f[tail, 0].mean()), "setup": float(parts_f[tail, 1].mean()),
+                          "sweep_and_copy_out": float(parts_f[tail, 2].mean()),
+                          "ready_to_enqueued": float(parts_f[tail, 3].mean()),
+                          "enqueued_to_complete": float(parts_f[tail, 4].mean()),
+                          "copy_out": float(parts_f[tail, 5].mean()),
+                          "solo": float(1e3 * solo_each[tail].mean())}}
         if offered is not None:
             lv["offered_requests_per_s"] = offered
         levels.append(lv)
@@ -900,7 +916,8 @@ def serve_measure(count, fractions, workers, dist, slice_us=10000):
                        "total_targets": total_targets,
                        "mix": "N log-uniform [1e3,1e6]; cube|Plummer; Coulomb|Yukawa kappa U[0.1,1]; "
                               "theta U[0.5,0.8]; n in {4,6,8,10}; N_L=N_B=2000; mixed",
-                       "setup_workers": workers, "max_batch": 64, "slice_us": slice_us},
+                       "setup_workers": workers, "max_batch": 64, "slice_us": slice_us,
+                       "setup_blocks": setup_blocks, "slices_in_flight": slices_in_flight or 1},
             "levels": levels,
             "solo": {"seconds": solo, "targets_per_s": total_targets / solo,
                      "p50_ms": float(np.percentile(solo_each, 50) * 1e3),
@@ -1274,8 +1291,12 @@ def main(argv=None):
                          "barycentric Hermite (n = 4) variant on the same workload instead; "
                          "graph: replays with fixed positions and new charges")
     ap.add_argument("--serve-requests", type=int, default=4096)
-    ap.add_argument("--serve-slice-us", type=int, default=10000,
+    ap.add_argument("--serve-slice-us", type=int, default=15000,
                     help="serving engine slice length in microseconds (0: all ready work at once)")
+    ap.add_argument("--serve-setup-blocks", type=int, default=0,
+                    help="block slots the serving sweeps leave to requests in preparation (0: none)")
+    ap.add_argument("--serve-slices-in-flight", type=int, default=0, choices=(0, 1, 2),
+                    help="slices the serving engine keeps enqueued (0: the library's default)")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving sub-record of the default run")
     ap.add_argument("--serve-record-requests", type=int, default=1024,

@@ -464,10 +464,21 @@ typedef struct bltc_server_config {
                                * launches (0: launch at once) */
     int64_t hbm_budget_bytes; /* device bytes admitted requests may reserve; 0 = 80% of free */
     int32_t slice_us;         /* >= 0: the engine runs the ready work in slices of about this
-                               * many microseconds, the requests with the least remaining work
-                               * first, so a request that arrives during a large sweep starts
-                               * at the next slice; 0: all ready work in one slice */
-    int32_t reserved;         /* must be 0 */
+                               * many microseconds of device time (converted to work by the
+                               * rate its earlier launches ran at), the requests with the least
+                               * remaining work first, so a request that arrives during a large
+                               * sweep starts at the next slice; 0: all ready work in one slice */
+    int32_t setup_blocks;     /* >= 0: block slots (of 2 per SM) the slices' sweeps leave free
+                               * for the kernels of requests in preparation, which otherwise
+                               * wait for a slice to end; setup workers' streams also take the
+                               * device's greatest stream priority (0: the sweeps fill every
+                               * slot) */
+    int32_t slices_in_flight; /* 0, 1 or 2: slices enqueued on the device at a time (0: 1).  The
+                               * engine takes the requests that became ready just before it
+                               * assembles a slice, after the slice before has run (1) or while
+                               * it runs (2): with 1 a new request waits about one slice less,
+                               * at the cost of the host time between slices.  Slices are sized
+                               * by the rate the engine's launches have measured */
 } bltc_server_config;
 
 typedef struct bltc_request_info {
@@ -475,6 +486,8 @@ typedef struct bltc_request_info {
     int32_t batch;            /* requests in the last slice it ran in */
     int64_t bytes_reserved;   /* device bytes reserved for it at admission */
     double t_submit, t_admit, t_ready, t_done;   /* host monotonic clock, seconds */
+    double t_swept;           /* when the engine enqueued its last items and its finalize */
+    double t_copy;            /* when its finalize had completed and the copy-out began */
 } bltc_request_info;
 
 typedef struct bltc_server_stats {

@@ -71,14 +71,15 @@ class bltc_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("setup_workers", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("linger_us", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("slice_us", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("setup_blocks", ctypes.c_int32), ("slices_in_flight", ctypes.c_int32)]
 
 
 class bltc_request_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("bytes_reserved", ctypes.c_int64), ("t_submit", ctypes.c_double),
                 ("t_admit", ctypes.c_double), ("t_ready", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("t_swept", ctypes.c_double),
+                ("t_copy", ctypes.c_double)]
 
 
 class bltc_server_counters(ctypes.Structure):
@@ -558,9 +559,10 @@ def bltc_autotune_tile(ctx, x, y, z, q, p: bltc_params, tiles, repeats=1, use_ca
 # ---- serving -------------------------------------------------------------------------
 
 def bltc_server_create(device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0, linger_us=0,
-                       slice_us=10000):
+                       slice_us=15000, setup_blocks=0, slices_in_flight=0):
     cfg = bltc_server_config(int(device), int(setup_workers), int(max_batch), int(linger_us),
-                             int(hbm_budget_bytes), int(slice_us), 0)
+                             int(hbm_budget_bytes), int(slice_us), int(setup_blocks),
+                             int(slices_in_flight))
     h = ctypes.c_void_p()
     st = lib().bltc_server_create(ctypes.byref(cfg), ctypes.byref(h))
     if st != BLTC_OK:
@@ -614,9 +616,9 @@ class Server:
     """Owns a serving runtime; keeps each request's host arrays alive until it is waited."""
 
     def __init__(self, device=0, setup_workers=2, max_batch=32, hbm_budget_bytes=0, linger_us=0,
-                 slice_us=10000):
+                 slice_us=15000, setup_blocks=0, slices_in_flight=0):
         self.h = bltc_server_create(device, setup_workers, max_batch, hbm_budget_bytes, linger_us,
-                                    slice_us)
+                                    slice_us, setup_blocks, slices_in_flight)
         self._keep = {}
 
     def submit(self, x, y, z, q, p, phi=None):

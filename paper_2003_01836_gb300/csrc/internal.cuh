@@ -354,6 +354,12 @@ public:
     MultiSweep(const MultiSweep&) = delete;
     MultiSweep& operator=(const MultiSweep&) = delete;
     void add(const SweepJob& job, void* tag);      // checks the job, allocates its partials
+    // block slots the persistent launches leave free (for other streams' kernels)
+    void set_free_blocks(int n) { free_blocks_ = n > 0 ? n : 0; }
+    // waits until at most `keep` (0 or 1) enqueued launch groups may still be running
+    void wait_in_flight(int keep);
+    // weighted interactions per microsecond the launches have run at (0 before any measure)
+    double rate() const { return rate_; }
     bool idle() const { return jobs_.empty(); }
     std::vector<void*> tags() const;                // requests with work still to run
     void clear();                                   // drops every request (after a failure)
@@ -368,6 +374,9 @@ private:
     std::vector<std::unique_ptr<Slot>> slots_;      // staging of the item order, two in flight
     int next_slot_ = 0;
     uint64_t seq_ = 0;
+    int free_blocks_ = 0;
+    double rate_ = 0.0;
+    void measure(Slot& sl);
 };
 void direct_sum(Context* ctx, const double* tx, const double* ty, const double* tz,
                 int64_t nt, const double* sx, const double* sy, const double* sz,

@@ -58,7 +58,7 @@ struct ServerRequest {
     bltc_status status = BLTC_OK;
     std::string err;
     int64_t bytes = 0;
-    double t_submit = 0, t_admit = 0, t_ready = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_ready = 0, t_done = 0, t_swept = 0, t_copy = 0;
     int batch = 0;
     // device state, allocated through the preparing worker's context
     std::vector<DBuf<double>> X;
@@ -112,12 +112,17 @@ static void server_free(void* ptr, size_t bytes, void* stream, void* user) {
     s->live.fetch_sub(static_cast<int64_t>(bytes));
 }
 
-static std::unique_ptr<Context> make_context(Server* s) {
+// A context on its own stream: the setup workers' streams take the greatest priority, so
+// their kernels get the block slots the sweeps leave free, and free slots between slices,
+// before the next slice's blocks.
+static std::unique_ptr<Context> make_context(Server* s, bool urgent) {
     std::unique_ptr<Context> c(new Context());
     c->device = s->cfg.device;
     BLTC_CUDA(cudaSetDevice(c->device));
     BLTC_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
-    BLTC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    int least = 0, greatest = 0;
+    BLTC_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    BLTC_CUDA(cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, urgent ? greatest : least));
     BLTC_CUDA(cudaMallocHost(&c->pinned, sizeof(int64_t) * Context::kPinnedWords));
     c->alloc_fn = server_alloc;
     c->free_fn = server_free;
@@ -241,18 +246,17 @@ static void worker_loop(Server* s, Context* c) {
     }
 }
 
-// Interactions the sweep runs per microsecond, about (1e6 cube, Coulomb): converts the slice
-// duration asked for into a work budget.
+// Weighted interactions the sweep runs per microsecond, about (1e6 cube, Coulomb): converts the
+// slice duration asked for into a work budget until the engine has measured its own rate.
 constexpr double kInteractionsPerUs = 3.5e6;
 
 static void engine_loop(Server* s) {
     Context* c = s->engine_ctx.get();
     cudaSetDevice(s->cfg.device);
-    const int64_t budget = s->cfg.slice_us > 0
-                               ? static_cast<int64_t>(kInteractionsPerUs * s->cfg.slice_us) : 0;
     std::unique_ptr<MultiSweep> ms;
     try {
         ms.reset(new MultiSweep(c));
+        ms->set_free_blocks(s->cfg.setup_blocks);
     } catch (const std::exception& e) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->last_err = e.what();
@@ -275,6 +279,16 @@ static void engine_loop(Server* s) {
                            (s->preparing == 0 && s->queued.empty());
                 });
             }
+        }
+        // At most slices_in_flight - 1 earlier slices stay enqueued; the requests that became
+        // ready meanwhile join the slice assembled next.
+        try {
+            ms->wait_in_flight(s->cfg.slices_in_flight == 2 ? 1 : 0);
+        } catch (const std::exception&) {
+            // a failed slice is reported by the launch that follows
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
             while (!s->ready.empty()) {
                 add.push_back(s->ready.front());
                 s->ready.pop_front();
@@ -289,6 +303,10 @@ static void engine_loop(Server* s) {
                 BLTC_CUDA(cudaStreamWaitEvent(c->stream, r->ready_ev, 0));
                 ms->add(SweepJob{r->L.get(), r->bt ? r->bt.get() : r->st.get(), r->st.get(), r->p, r->phi.p}, r);
             }
+            // the slice's work from the rate its launches have run at (the request mix's cost per
+            // interaction varies with theta, the degree and the kernel)
+            const double rate = ms->rate() > 0.0 ? ms->rate() : kInteractionsPerUs;
+            const int64_t budget = s->cfg.slice_us > 0 ? static_cast<int64_t>(rate * s->cfg.slice_us) : 0;
             took = ms->run_slice(budget, s->cfg.max_batch, &fin);
         } catch (const Error& e) {
             st = e.status;
@@ -329,9 +347,11 @@ static void engine_loop(Server* s) {
         s->max_batch_seen = std::max<int64_t>(s->max_batch_seen, static_cast<int64_t>(took));
         if (!fin.empty()) {
             std::vector<ServerRequest*> batch;
-            for (void* t : fin) {
-                ServerRequest* r = static_cast<ServerRequest*>(t);
+            const double t = now_s();
+            for (void* f : fin) {
+                ServerRequest* r = static_cast<ServerRequest*>(f);
                 r->batch = took;
+                r->t_swept = t;
                 batch.push_back(r);
             }
             s->inflight.emplace_back(std::move(batch), done);
@@ -359,7 +379,9 @@ static void completer_loop(Server* s) {
             cudaEventSynchronize(job.second);
             cudaEventDestroy(job.second);
         }
+        const double t_copy = now_s();
         for (ServerRequest* r : job.first) {
+            r->t_copy = t_copy;
             cudaError_t e = cudaMemcpyAsync(r->hphi, r->phi.p, sizeof(double) * static_cast<size_t>(r->n),
                                             cudaMemcpyDeviceToHost, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -385,7 +407,8 @@ bltc_status bltc_server_create(const bltc_server_config* cfg, bltc_server** out)
     if (!cfg || !out) return BLTC_ERR_ARG;
     *out = nullptr;
     if (cfg->setup_workers < 1 || cfg->setup_workers > 64 || cfg->max_batch < 1 || cfg->hbm_budget_bytes < 0 ||
-        cfg->linger_us < 0 || cfg->slice_us < 0 || cfg->reserved != 0)
+        cfg->linger_us < 0 || cfg->slice_us < 0 || cfg->setup_blocks < 0 || cfg->slices_in_flight < 0 ||
+        cfg->slices_in_flight > 2)
         return BLTC_ERR_ARG;
     std::unique_ptr<bltc_server> h(new bltc_server());
     Server& s = h->s;
@@ -406,9 +429,10 @@ bltc_status bltc_server_create(const bltc_server_config* cfg, bltc_server** out)
         BLTC_CUDA(cudaMemPoolCreate(&s.pool, &props));
         uint64_t keep = ~0ULL;
         cudaMemPoolSetAttribute(s.pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        for (int w = 0; w < cfg->setup_workers; ++w) s.worker_ctx.push_back(make_context(&s));
-        s.engine_ctx = make_context(&s);
-        s.completer_ctx = make_context(&s);
+        const bool urgent = cfg->setup_blocks > 0;
+        for (int w = 0; w < cfg->setup_workers; ++w) s.worker_ctx.push_back(make_context(&s, urgent));
+        s.engine_ctx = make_context(&s, false);
+        s.completer_ctx = make_context(&s, urgent);
     } catch (const Error& e) {
         for (auto& c : s.worker_ctx) release_context(c.get());
         release_context(s.engine_ctx.get());
@@ -478,6 +502,8 @@ bltc_status bltc_server_wait(bltc_server* h, uint64_t ticket, double timeout_s, 
         info->t_admit = r->t_admit;
         info->t_ready = r->t_ready;
         info->t_done = r->t_done;
+        info->t_swept = r->t_swept;
+        info->t_copy = r->t_copy;
     }
     const bltc_status st = r->status;
     s.reqs.erase(it);

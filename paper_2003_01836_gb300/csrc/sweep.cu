@@ -393,14 +393,17 @@ struct MultiSweep::Slot {
     int64_t cap = 0;
     DBuf<int2> dev;
     DBuf<unsigned int> counters;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;   // around the launch group, timed
     bool used = false;
+    int64_t cost = 0, budget = 0;                   // its weighted work and the slice's budget
+    bool measured = true;
 };
 
 MultiSweep::MultiSweep(Context* ctx) : ctx_(ctx) {
     for (int i = 0; i < 2; ++i) {
         slots_.emplace_back(new Slot());
-        BLTC_CUDA(cudaEventCreateWithFlags(&slots_.back()->done, cudaEventDisableTiming));
+        BLTC_CUDA(cudaEventCreate(&slots_.back()->start));
+        BLTC_CUDA(cudaEventCreate(&slots_.back()->done));
     }
 }
 
@@ -410,6 +413,7 @@ MultiSweep::~MultiSweep() {
             cudaEventSynchronize(sl->done);
             cudaEventDestroy(sl->done);
         }
+        if (sl->start) cudaEventDestroy(sl->start);
         if (sl->host) cudaFreeHost(sl->host);
     }
 }
@@ -434,6 +438,38 @@ void MultiSweep::add(const SweepJob& job, void* tag) {
     jb->mpart = DBuf<float>(ctx_, pl.mutual ? pl.mpart_len : 0);
     for (int64_t c : pl.h_cost) jb->remaining += weighted_cost(c, job.p);
     jobs_.push_back(std::move(jb));
+}
+
+// After a launch group has run: its weighted work over its device time updates the engine's
+// rate (an exponential average over the groups that filled at least half of their slice's
+// budget, so that short tails do not count as slow work).
+void MultiSweep::measure(Slot& sl) {
+    if (!sl.used || sl.measured) return;
+    sl.measured = true;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, sl.start, sl.done) != cudaSuccess || ms <= 0.f) {
+        cudaGetLastError();
+        return;
+    }
+    if (sl.budget > 0 && 2 * sl.cost < sl.budget) return;
+    const double r = static_cast<double>(sl.cost) / (1e3 * static_cast<double>(ms));
+    rate_ = rate_ > 0.0 ? 0.7 * rate_ + 0.3 * r : r;
+}
+
+void MultiSweep::wait_in_flight(int keep) {
+    // slots alternate: next_slot_ is the older one, next_slot_ ^ 1 the most recent
+    Slot& older = *slots_[static_cast<size_t>(next_slot_)];
+    if (older.used) {
+        BLTC_CUDA(cudaEventSynchronize(older.done));
+        measure(older);
+    }
+    if (keep == 0) {
+        Slot& recent = *slots_[static_cast<size_t>(next_slot_ ^ 1)];
+        if (recent.used) {
+            BLTC_CUDA(cudaEventSynchronize(recent.done));
+            measure(recent);
+        }
+    }
 }
 
 std::vector<void*> MultiSweep::tags() const {
@@ -477,7 +513,8 @@ int MultiSweep::run_slice(int64_t budget, int max_requests, std::vector<void*>* 
         if (i > jb->next) take.push_back(Take{jb, jb->next, i});
         jb->next = i;
     }
-    const int64_t cap = kMinBlocks * static_cast<int64_t>(std::max(1, ctx_->sm_count));
+    const int64_t cap = std::max<int64_t>(
+        1, kMinBlocks * static_cast<int64_t>(std::max(1, ctx_->sm_count)) - free_blocks_);
     BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_COULOMB>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kMixedSmem));
     BLTC_CUDA(cudaFuncSetAttribute(k_sweep_multi<BLTC_KERNEL_YUKAWA>,
@@ -500,7 +537,14 @@ int MultiSweep::run_slice(int64_t budget, int max_requests, std::vector<void*>* 
                                                     const std::pair<int64_t, int2>& y) { return x.first > y.first; });
         Slot& sl = *slots_[static_cast<size_t>(next_slot_)];
         next_slot_ ^= 1;
-        if (sl.used) BLTC_CUDA(cudaEventSynchronize(sl.done));     // its previous slice has run
+        if (sl.used) {
+            BLTC_CUDA(cudaEventSynchronize(sl.done));     // its previous slice has run
+            measure(sl);
+        }
+        sl.cost = 0;
+        for (const auto& pr : all) sl.cost += weighted_cost(pr.first, take[t0 + pr.second.x].jb->j.p);
+        sl.budget = budget;
+        sl.measured = false;
         const int64_t total = static_cast<int64_t>(all.size());
         if (total > sl.cap) {
             if (sl.host) cudaFreeHost(sl.host);
@@ -516,6 +560,7 @@ int MultiSweep::run_slice(int64_t budget, int max_requests, std::vector<void*>* 
         int64_t ny = nc;
         for (const auto& pr : all)
             if (take[t0 + pr.second.x].jb->j.p.kernel == BLTC_KERNEL_YUKAWA) sl.host[ny++] = pr.second;
+        BLTC_CUDA(cudaEventRecord(sl.start, s));
         BLTC_CUDA(cudaMemsetAsync(sl.counters.p, 0, 2 * sizeof(unsigned int), s));
         BLTC_CUDA(cudaMemcpyAsync(sl.dev.p, sl.host, sizeof(int2) * total, cudaMemcpyHostToDevice, s));
         if (nc > 0) {

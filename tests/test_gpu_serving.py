@@ -39,7 +39,8 @@ def test_served_results_equal_solo(gpu):
         for i, ((st, phi, info), ref) in enumerate(zip(outs, solo)):
             assert st == b.BLTC_OK, (i, st)
             assert np.array_equal(phi, ref), f"request {i} differs from its solo solve"
-            assert info["t_submit"] <= info["t_admit"] <= info["t_ready"] <= info["t_done"]
+            assert info["t_submit"] <= info["t_admit"] <= info["t_ready"] <= info["t_swept"]
+            assert info["t_swept"] <= info["t_copy"] <= info["t_done"]
         s = srv.stats()
         assert s["completed"] == 24 and s["failed"] == 0
         assert s["max_batch"] > 1, "requests were never swept together"
@@ -65,14 +66,18 @@ def test_more_requests_in_a_sweep_than_one_launch_holds(gpu):
         srv.close()
 
 
-def test_sliced_sweeps_let_small_requests_pass_a_large_one(gpu):
+@pytest.mark.parametrize("in_flight,setup_blocks", [(1, 0), (2, 0), (1, 8)],
+                         ids=["one-slice", "two-slices", "one-slice-free-blocks"])
+def test_sliced_sweeps_let_small_requests_pass_a_large_one(gpu, in_flight, setup_blocks):
     # With slices of 2 ms, small requests that become ready while a large sweep runs are
     # swept at the next slice (least remaining work first) and finish before the large one;
-    # every result is still its solo solve's bits.
+    # every result is still its solo solve's bits, with one or two slices enqueued at a time
+    # and with block slots left free for the setup workers' kernels.
     big = system("cube", 600000, 20031911) + (b.params(10, 0.5, 2000),)
     small = [system("plummer", 3000, 20031912 + i) + (b.params(6, 0.7, 500),) for i in range(6)]
     solo = [gpu_solve(gpu, *r) for r in [big] + small]
-    srv = b.Server(0, setup_workers=2, max_batch=16, slice_us=2000)
+    srv = b.Server(0, setup_workers=2, max_batch=16, slice_us=2000, setup_blocks=setup_blocks,
+                   slices_in_flight=in_flight)
     try:
         tb = srv.submit(*big)
         import time
