@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbltc.so")
 
-SOURCES = ["api.cu", "scan.cu", "tree.cu", "lists.cu", "upward.cu", "plan.cu", "sweep.cu", "direct.cu",
+SOURCES = ["api.cu", "scan.cu", "tree.cu", "lists.cu", "upward.cu", "plan.cu", "sweep.cu", "multisweep.cu", "direct.cu",
            "server.cu", "user_kernel.cu", "cp.cu", "hermite.cu", "graph.cu"]
 # the sweep device code, embedded as text for run-time compilation of user kernels
 EMBED = ("sweep_device.cuh", "kSweepDeviceSource")
