@@ -142,3 +142,28 @@ def test_positions_graph_single_particle_and_headroom(gpu):
     X = dev(x, y, z, q)
     with pytest.raises(b.BltcError):
         b.Graph(gpu, *X[:3], X[3], b.params(4, 0.7, 100, 100), positions=True, headroom=0.5)
+
+
+SOFT = """
+__device__ float bltc_user_g32(float r2, float r, float eps) { return rsqrtf(r2 + eps * eps); }
+__device__ double bltc_user_g64(double r2, double r, double eps) { return 1.0 / sqrt(r2 + eps * eps); }
+"""
+
+
+def test_positions_graph_with_registered_kernel(gpu):
+    # a kernel compiled at run time is launched inside the capture like the built-in ones
+    st, log = b.bltc_kernel_check(SOFT, 103)
+    if st == b.BLTC_ERR_STATE:
+        pytest.skip("NVRTC not available: " + log)
+    kid = b.bltc_kernel_register(gpu.h, SOFT)
+    x, y, z, q = system("plummer", 20000, 20031974)
+    p = b.params(6, 0.7, 600, 600, kid, 0.05, b.BLTC_PRECISION_MIXED)
+    X = dev(x, y, z, q)
+    g = b.Graph(gpu, *X[:3], X[3], p, positions=True)
+    try:
+        x1, y1, z1, q1 = system("plummer", 20000, 20031975)
+        _load(X, x1, y1, z1, q1)
+        g.launch()
+        assert np.array_equal(host(g.phi), _solve(gpu, x1, y1, z1, q1, p))
+    finally:
+        g.close()
